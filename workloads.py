@@ -1,0 +1,234 @@
+"""Seeded synthetic inputs shared by the tests, the smoke check and the benchmark.
+
+This module generates INPUTS only.  It holds none of the sorting method's
+arithmetic: no comparison, no key transform, no sort.  Sorted inputs are built
+from cumulative exponential spacings (the order statistics of n uniforms are
+the normalised partial sums of n+1 exponentials), so they are non-decreasing
+by construction.
+
+Distributions follow the paper's data sets (Sec. 4: random keys in
+[0, 10^6], distinct = a shuffle of 1..n, 0-1, and defined duplicates = k copies
+of n/k keys) plus the large-sort workload family: uniform, Gaussian, sorted,
+reverse sorted, 16 distinct values and Zipf(1.1) over 2^20 symbols, for u32,
+u64 and f32 keys.  Payloads are the u32 row index.  Every generator takes an
+explicit seed; the recipe of each is stated in its docstring.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+DTYPES = {"u32": np.uint32, "u64": np.uint64, "f32": np.float32}
+DISTRIBUTIONS = ("uniform", "gaussian", "sorted", "reverse", "distinct16", "zipf")
+PAPER_SETS = ("random1e6", "distinct", "zero_one", "dup2", "dup16", "dup2250")
+
+_GOLDEN32 = 0x9E3779B1
+_GOLDEN64 = 0x9E3779B97F4A7C15
+
+
+def rng(seed: int) -> np.random.Generator:
+    """PCG64 generator for ``seed``."""
+    return np.random.default_rng(seed)
+
+
+def large_sort_seed(dist: str, dtype: str, n: int) -> int:
+    """Seed of the large-sort workload: 1000*dist_id + 10*dtype_id + log2(n)."""
+    dist_id = DISTRIBUTIONS.index(dist)
+    dtype_id = list(DTYPES).index(dtype)
+    return 1000 * dist_id + 10 * dtype_id + int(round(math.log2(max(n, 1))))
+
+
+def _uniform_bits(g, n, dtype):
+    if dtype == "u64":
+        return g.integers(0, 2**64, size=n, dtype=np.uint64, endpoint=False)
+    u = g.integers(0, 2**32, size=n, dtype=np.uint64).astype(np.uint32)
+    return u.view(np.float32) if dtype == "f32" else u
+
+
+def sorted_uniform_u64(g, n: int, hi: float) -> np.ndarray:
+    """n non-decreasing integers distributed as sorted uniforms on [0, hi).
+
+    Built from exponential spacings: S_i = E_1 + ... + E_i, U_(i) = S_i / S_{n+1}.
+    """
+    if n == 0:
+        return np.zeros(0, dtype=np.uint64)
+    e = g.exponential(1.0, size=n + 1)
+    s = np.cumsum(e)
+    u = s[:-1] / s[-1]
+    x = np.floor(u * hi)
+    x = np.minimum(x, np.nextafter(hi, 0))
+    # float64 keeps the sequence monotone; the conversion is exact below 2^53
+    # and monotone (round-toward-zero of a monotone sequence) above.
+    out = x.astype(np.uint64)
+    return np.maximum.accumulate(out)
+
+
+def sorted_keys(g, n: int, dtype: str) -> np.ndarray:
+    """Non-decreasing keys of ``dtype`` (f32: float32 of sorted u32 values)."""
+    if dtype == "u64":
+        return sorted_uniform_u64(g, n, 2.0**64)
+    u = sorted_uniform_u64(g, n, 2.0**32).astype(np.uint32)
+    if dtype == "f32":
+        return u.astype(np.float32)
+    return u
+
+
+def gaussian_u32(g, n: int) -> np.ndarray:
+    """rint(N(2^31, 2^28)) clamped to [0, 2^32 - 1]."""
+    x = np.rint(g.normal(2.0**31, 2.0**28, size=n))
+    return np.clip(x, 0, 2.0**32 - 1).astype(np.uint64).astype(np.uint32)
+
+
+def zipf_ranks(g, n: int, s: float = 1.1, symbols: int = 1 << 20) -> np.ndarray:
+    """Ranks r in [1, symbols] with P(r) proportional to r^-s (inverse CDF)."""
+    w = np.arange(1, symbols + 1, dtype=np.float64) ** (-s)
+    cdf = np.cumsum(w)
+    cdf /= cdf[-1]
+    u = g.random(n)
+    return np.minimum(np.searchsorted(cdf, u, side="left"), symbols - 1).astype(np.uint64) + 1
+
+
+def keys(dist: str, dtype: str, n: int, seed: int | None = None) -> np.ndarray:
+    """Keys of the large-sort workload family (``dist`` in DISTRIBUTIONS).
+
+    uniform   : u32 / u64 uniform over the full range; f32 = uniform random
+                32-bit patterns (NaNs, infinities, subnormals and both zeros
+                included, to exercise the total order).
+    gaussian  : u32 = rint(N(2^31, 2^28)) clamped; u64 = the same values
+                widened; f32 = float32 of the same values (many ties).
+    sorted    : non-decreasing by construction (exponential spacings); f32 =
+                float32 of sorted u32 values.
+    reverse   : ``sorted`` read backwards.
+    distinct16: 16 values drawn from the uniform law, each element picks one.
+    zipf      : rank r ~ Zipf(1.1) over 2^20 symbols, key = (r-1)*golden mod
+                2^32 (u32) or 2^64 (u64); f32 = float32 of the u32 key.
+    """
+    if seed is None:
+        seed = large_sort_seed(dist, dtype, n)
+    g = rng(seed)
+    if dist == "uniform":
+        return _uniform_bits(g, n, dtype)
+    if dist == "gaussian":
+        u = gaussian_u32(g, n)
+        if dtype == "u64":
+            return u.astype(np.uint64)
+        return u.astype(np.float32) if dtype == "f32" else u
+    if dist == "sorted":
+        return sorted_keys(g, n, dtype)
+    if dist == "reverse":
+        return np.ascontiguousarray(sorted_keys(g, n, dtype)[::-1])
+    if dist == "distinct16":
+        pool = _uniform_bits(g, 16, dtype)
+        return pool[g.integers(0, 16, size=n)]
+    if dist == "zipf":
+        r = zipf_ranks(g, n) - 1
+        if dtype == "u64":
+            return r * np.uint64(_GOLDEN64)  # wraps mod 2^64
+        u = ((r * np.uint64(_GOLDEN32)) & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+        return u.astype(np.float32) if dtype == "f32" else u
+    raise ValueError(f"unknown distribution {dist!r}")
+
+
+def paper_keys(name: str, n: int, seed: int = 7) -> np.ndarray:
+    """The paper's correctness data sets (Sec. 4), as u32 keys.
+
+    random1e6: uniform in [0, 10^6]; distinct: a shuffle of 1..n; zero_one:
+    uniform 0/1; dupK: K copies of each of n/K distinct keys, shuffled.
+    """
+    g = rng(seed)
+    if name == "random1e6":
+        return g.integers(0, 10**6 + 1, size=n).astype(np.uint32)
+    if name == "distinct":
+        return g.permutation(np.arange(1, n + 1, dtype=np.uint32))
+    if name == "zero_one":
+        return g.integers(0, 2, size=n).astype(np.uint32)
+    if name.startswith("dup"):
+        k = int(name[3:])
+        distinct = max(1, -(-n // k))  # ceil(n / k); the last key may have fewer copies
+        # distinct by construction: an odd multiplier is a bijection mod 2^32
+        off = np.uint64(g.integers(0, 2**32))
+        base = ((np.arange(distinct, dtype=np.uint64) * np.uint64(_GOLDEN32) + off)
+                & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+        return g.permutation(np.repeat(base, k)[:n])
+    raise ValueError(f"unknown paper data set {name!r}")
+
+
+def row_index(n: int) -> np.ndarray:
+    """Payload v[i] = i (u32)."""
+    return np.arange(n, dtype=np.uint32)
+
+
+def log_uniform_sizes(g, count: int, lo: float, hi: float) -> np.ndarray:
+    """floor(exp(U(ln lo, ln(hi + 1)))) clamped to [lo, hi]."""
+    x = np.floor(np.exp(g.uniform(math.log(lo), math.log(hi + 1), size=count)))
+    return np.clip(x, lo, hi).astype(np.int64)
+
+
+def run_lengths(k: int, total: int, seed: int | None = None,
+                lo: int = 1 << 10, hi: int = 1 << 24) -> np.ndarray:
+    """k run lengths drawn log-uniform in [lo, hi], rescaled to sum to ``total``.
+
+    Rescaling uses cumulative rounding (lengths are the differences of the
+    rounded partial sums of the scaled draws), so the lengths sum to ``total``
+    exactly; every length is >= lo when k * lo <= total, else >= 1.  (For k = 2
+    and 16 a total of 2^27 forces lengths above 2^24; that is unavoidable and
+    reported by callers.)
+    """
+    if seed is None:
+        seed = 3000 + k
+    g = rng(seed)
+    w = np.exp(g.uniform(math.log(lo), math.log(hi), size=k))
+    floor_min = lo if k * lo <= total else 1
+    spare = total - k * floor_min
+    bounds = np.rint(np.cumsum(w) / w.sum() * spare).astype(np.int64)
+    bounds[-1] = spare
+    lens = np.diff(np.concatenate([[0], bounds]))
+    return lens + floor_min
+
+
+def sorted_runs(k: int, total: int, dtype: str = "u32", seed: int | None = None):
+    """k sorted runs (lengths from :func:`run_lengths`) concatenated.
+
+    Returns ``(keys, offsets)`` with offsets of length k+1.
+    """
+    if seed is None:
+        seed = 3000 + k
+    lens = run_lengths(k, total, seed)
+    g = rng(seed + 1)
+    parts = [sorted_keys(g, int(m), dtype) for m in lens]
+    offs = np.zeros(k + 1, dtype=np.uint64)
+    offs[1:] = np.cumsum(lens)
+    return np.concatenate(parts) if parts else np.zeros(0, DTYPES[dtype]), offs
+
+
+def segment_sizes(count: int = 100_000, hi: int = 1 << 18, seed: int = 4000) -> np.ndarray:
+    """Segment sizes clamp(floor(exp(U(ln 1, ln(hi + 1)))), 1, hi)."""
+    return log_uniform_sizes(rng(seed), count, 1, hi)
+
+
+def segments(count: int, hi: int, dtype: str = "u32", seed: int = 4000):
+    """Uniform keys in ``count`` segments of log-uniform size in [1, hi].
+
+    Returns ``(keys, offsets)``.
+    """
+    sizes = segment_sizes(count, hi, seed)
+    offs = np.zeros(count + 1, dtype=np.uint64)
+    offs[1:] = np.cumsum(sizes)
+    return _uniform_bits(rng(seed + 1), int(offs[-1]), dtype), offs
+
+
+def request_trace(rate_hz: float = 2000.0, duration_s: float = 10.0, lo: int = 1 << 8,
+                  hi: int = 1 << 24, pairs_fraction: float = 0.3, seed: int = 5000):
+    """Open-loop request trace: Poisson arrivals, log-uniform sizes, 30 % pairs.
+
+    Returns a dict of numpy arrays: ``t`` (arrival seconds), ``n`` (keys),
+    ``pairs`` (bool).
+    """
+    g = rng(seed)
+    gaps = g.exponential(1.0 / rate_hz, size=int(rate_hz * duration_s * 1.5) + 16)
+    t = np.cumsum(gaps)
+    t = t[t < duration_s]
+    n = log_uniform_sizes(g, t.size, lo, hi)
+    pairs = g.random(t.size) < pairs_fraction
+    return {"t": t, "n": n, "pairs": pairs}
