@@ -1,0 +1,182 @@
+/*
+ * bcfsort.h -- C ABI of the GB300 bank-conflict-free comparison merge sort.
+ *
+ * The library implements the hot path of Sitchinava & Weichert, "Bank Conflict
+ * Free Comparison-based Sorting On GPUs" (arXiv 1306.5076): a shared-memory
+ * block sort with no bank conflicts (Sec. 3.1) followed by BCFMergesort's
+ * global merge passes (Sec. 3.2, Lemma 2), redesigned for sm_103a.
+ *
+ * Conventions shared by every call below
+ * --------------------------------------
+ *  - Memory.  Every key / value pointer is DEVICE memory owned by the caller
+ *    and must be 16-byte aligned when the element count is non-zero.  Keys are
+ *    arrays of the key type (4 bytes for BCF_U32 / BCF_F32, 8 for BCF_U64);
+ *    values are uint32_t arrays of the same length.  Arrays are contiguous.
+ *  - Workspace.  The library allocates nothing on the sort path.  Calls that
+ *    need scratch take a caller-provided device workspace `ws` of at least
+ *    bcf_workspace_bytes(...) bytes, 256-byte aligned.  Its contents on entry
+ *    are irrelevant and on return undefined.
+ *  - Aliasing.  keys_out == keys_in (and vals_out == vals_in) is allowed; any
+ *    other overlap between an output and an input, or with `ws`, is BCF_EINVAL.
+ *  - Asynchrony.  Calls enqueue work on `stream` and return after launching;
+ *    results are valid once the stream has reached that point.  Errors that
+ *    can be seen on the host (null pointers, misalignment, short workspace,
+ *    bad dtype, decreasing offsets) are returned before anything is launched.
+ *    A launch failure returns BCF_ECUDA.  Device-side bounded waits that run
+ *    out set a device error word that bcf_last_device_error() reports.
+ *  - Order.  Keys are compared after an order-preserving map to unsigned
+ *    integers: u32 / u64 as-is, f32 under IEEE 754 totalOrder
+ *    (-NaN < -inf < ... < -0 < +0 < ... < +inf < +NaN).  Keys are returned
+ *    bit-for-bit (NaN payloads and the sign of zero survive).  Descending
+ *    order reverses the key order; ties ALWAYS keep input order (stable), in
+ *    both directions.  The paper sorts integer keys and never discusses ties
+ *    or floats; stability and totalOrder are this library's reading.
+ *  - Edge sizes.  n == 0 is a no-op returning BCF_OK; n == 1 copies.
+ *  - Determinism.  The output is a function of the input alone: it does not
+ *    depend on the stream, tuning parameters or what else runs on the GPU.
+ *  - Threads.  Calls may be made from several host threads at once as long as
+ *    they use different workspaces.
+ */
+#ifndef BCFSORT_H
+#define BCFSORT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { BCF_U32 = 0, BCF_U64 = 1, BCF_F32 = 2 } bcf_dtype;
+
+typedef enum {
+    BCF_OK = 0,
+    BCF_EINVAL = 1,       /* bad argument, detected on the host before any launch */
+    BCF_ENOMEM = 2,       /* workspace smaller than bcf_workspace_bytes() */
+    BCF_ECUDA = 3,        /* a CUDA launch or runtime call failed */
+    BCF_ETIMEOUT = 4,     /* a device-side bounded wait ran out (see bcf_last_device_error) */
+    BCF_EUNSUPPORTED = 5  /* valid request this build does not handle (e.g. too many segments) */
+} bcf_status;
+
+typedef struct {
+    int descending;      /* 0: ascending, 1: descending (ties keep input order) */
+    int stable_required; /* accepted for API symmetry; output is always stable */
+} bcf_opts;              /* a NULL bcf_opts* means ascending */
+
+/* Operation codes for bcf_workspace_bytes. */
+enum { BCF_OP_SORT = 0, BCF_OP_MERGE = 1, BCF_OP_SEGMENTED = 2 };
+
+/*
+ * Workspace size in bytes for an operation.
+ *   op        BCF_OP_SORT: sort n keys (pairs if has_vals);
+ *             BCF_OP_MERGE: merge nseg_or_k runs totalling n keys;
+ *             BCF_OP_SEGMENTED: nseg_or_k segments totalling n keys.
+ * Returns 0 for an unknown op or dtype.  The size is about one extra copy of
+ * the keys (+ values) -- the merge is not in place, as in the paper (Sec. 4
+ * remarks that BCFMergesort needs less extra space than its competitors) --
+ * plus O(n / tile) split points and a small header.
+ */
+size_t bcf_workspace_bytes(int op, uint64_t n, uint64_t nseg_or_k, bcf_dtype kt, int has_vals);
+
+/*
+ * Sort n keys.  "Sort N keys" is the problem of Sec. 3; the method is the
+ * base-case block sort (Sec. 3.1) followed by ceil(log2(n / T)) global merge
+ * passes (Sec. 3.2, Lemma 2), T being the block tile of bcf_sort_plan().
+ *   keys_out  device, n keys, written with the sorted keys (may equal keys_in)
+ *   keys_in   device, n keys, read only
+ * Errors: BCF_EINVAL (null pointer with n > 0, misalignment, bad dtype,
+ * partial overlap), BCF_ENOMEM (ws too small), BCF_ECUDA.
+ */
+bcf_status bcf_sort_keys(void* keys_out, const void* keys_in, uint64_t n, bcf_dtype kt,
+                         const bcf_opts* opts, void* ws, size_t ws_bytes, cudaStream_t stream);
+
+/*
+ * Stable sort of n (key, value) pairs: values follow their keys, and pairs
+ * with equal keys keep their input order.  Same method and errors as
+ * bcf_sort_keys.  vals_out may equal vals_in.
+ */
+bcf_status bcf_sort_pairs(void* keys_out, uint32_t* vals_out, const void* keys_in,
+                          const uint32_t* vals_in, uint64_t n, bcf_dtype kt,
+                          const bcf_opts* opts, void* ws, size_t ws_bytes, cudaStream_t stream);
+
+/*
+ * Merge k sorted runs into one sorted array ("merge sorted sequences",
+ * Sec. 3.2, Algorithm 6; the final merge phase merges many runs per bucket).
+ * Run r occupies [run_offsets_host[r], run_offsets_host[r+1]) of keys_in;
+ * offsets are HOST memory, k+1 entries, non-decreasing, run_offsets_host[0]
+ * is usually 0 and the output covers the same index range.  Each run must be
+ * sorted under the requested order (a precondition that is not checked, as
+ * in Algorithm 6).  Ties are broken by run index, then position.  Runs are
+ * merged pairwise in a balanced tree of ceil(log2 k) passes.
+ *   vals_in / vals_out  NULL for keys only (both or neither).
+ * Errors: as bcf_sort_keys, plus BCF_EINVAL for decreasing offsets or k == 0.
+ */
+bcf_status bcf_merge_runs(void* keys_out, uint32_t* vals_out, const void* keys_in,
+                          const uint32_t* vals_in, const uint64_t* run_offsets_host, uint32_t k,
+                          bcf_dtype kt, const bcf_opts* opts, void* ws, size_t ws_bytes,
+                          cudaStream_t stream);
+
+/*
+ * Sort each of nseg segments independently (the paper's "segmented" sorts are
+ * intra-tile only, Sec. 3.1 and Algorithm 5; sorting many independent arrays
+ * in one launch is this library's batching extension).  Segment s occupies
+ * [seg_offsets_dev[s], seg_offsets_dev[s+1]) of keys_in; offsets are DEVICE
+ * memory, nseg+1 non-decreasing uint64 entries with seg_offsets_dev[nseg] ==
+ * n_total.  vals may be NULL (both or neither).  Offsets are read on the
+ * device; a decreasing offset is not detected on the host and yields an
+ * unspecified (but memory-safe) result.
+ */
+bcf_status bcf_segmented_sort(void* keys_out, uint32_t* vals_out, const void* keys_in,
+                              const uint32_t* vals_in, const uint64_t* seg_offsets_dev,
+                              uint64_t nseg, uint64_t n_total, bcf_dtype kt,
+                              const bcf_opts* opts, void* ws, size_t ws_bytes,
+                              cudaStream_t stream);
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char* bcf_status_string(bcf_status status);
+
+/*
+ * Synchronise `stream`, then read and clear the current device's error word.
+ * Returns BCF_ETIMEOUT if a kernel's bounded wait ran out since the last call,
+ * BCF_ECUDA if the synchronisation failed, else BCF_OK.
+ */
+bcf_status bcf_last_device_error(cudaStream_t stream);
+
+/* ---- plan introspection and building blocks ------------------------------ */
+
+typedef struct {
+    uint32_t block_tile;   /* T: keys per CTA in the block sort (Sec. 3.1 "M") */
+    uint32_t merge_tile;   /* output keys per CTA in a merge pass */
+    uint32_t merge_passes; /* ceil(log2(n / T)) global merge passes (Lemma 2) */
+    uint32_t launches;     /* kernel launches one bcf_sort_* call makes */
+    uint64_t bytes_per_pass; /* algorithmic bytes of one pass: 2 n (key + value size) */
+} bcf_plan;
+
+/* Fill *plan for sorting n keys of type kt (pairs if has_vals). */
+bcf_status bcf_sort_plan(uint64_t n, bcf_dtype kt, int has_vals, bcf_plan* plan);
+
+/*
+ * Per-kernel timing of the library's own launches, for benchmarking.  When
+ * enabled, the library brackets every kernel it launches with CUDA events on
+ * the launch stream (events are created once, on first use).  Kinds:
+ * 0 block sort, 1 merge-path partition, 2 merge pass, 3 segmented sort.
+ */
+typedef struct {
+    uint32_t launches[4];
+    double total_ms[4];
+} bcf_profile;
+
+bcf_status bcf_profile_enable(int on);
+/* Synchronise the recorded events, accumulate their times into *out, clear. */
+bcf_status bcf_profile_collect(bcf_profile* out);
+
+/* Version string of the library. */
+const char* bcf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BCFSORT_H */

@@ -1,0 +1,164 @@
+"""GB300-native bank-conflict-free comparison merge sort (arXiv 1306.5076).
+
+Python binding of the C ABI in ``include/bcfsort.h``: the functions below have
+the C names and only marshal arguments (tensor -> device pointer, stream,
+options) and turn non-OK status codes into :class:`BcfError`.  Every step of
+the sort runs in the CUDA kernels of ``libbcfsort.so``; there is no CPU or
+library fallback.  PyTorch supplies device memory and streams only.
+
+Keys: torch.uint32 / torch.int32 (bits read as u32), torch.uint64 /
+torch.int64 (bits read as u64), torch.float32 (IEEE 754 totalOrder).
+Values: 32-bit tensors (torch.int32 / torch.uint32).
+"""
+from __future__ import annotations
+
+import ctypes
+
+from . import _native
+from ._native import BCF_F32, BCF_OP_MERGE, BCF_OP_SEGMENTED, BCF_OP_SORT, BCF_U32, BCF_U64
+
+__all__ = [
+    "BcfError", "bcf_workspace_bytes", "bcf_sort_keys", "bcf_sort_pairs", "bcf_merge_runs",
+    "bcf_segmented_sort", "bcf_last_device_error", "bcf_sort_plan", "bcf_profile_enable",
+    "bcf_profile_collect", "bcf_version", "key_dtype_of", "BCF_U32", "BCF_U64", "BCF_F32",
+    "BCF_OP_SORT", "BCF_OP_MERGE", "BCF_OP_SEGMENTED",
+]
+
+
+class BcfError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        msg = _native.load().bcf_status_string(status).decode()
+        super().__init__(f"{what}: {msg}" if what else msg)
+
+
+def _check(status: int, what: str) -> None:
+    if status != 0:
+        raise BcfError(status, what)
+
+
+def key_dtype_of(t) -> int:
+    """C key-type code of a tensor's dtype."""
+    import torch
+
+    if t.dtype == torch.float32:
+        return BCF_F32
+    if t.dtype in (torch.int32, getattr(torch, "uint32", torch.int32)):
+        return BCF_U32
+    if t.dtype in (torch.int64, getattr(torch, "uint64", torch.int64)):
+        return BCF_U64
+    raise TypeError(f"unsupported key dtype {t.dtype}")
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("bcfsort: tensors must be CUDA tensors")
+    if not t.is_contiguous():
+        raise ValueError("bcfsort: tensors must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _opts(descending: bool):
+    return ctypes.byref(_native.BcfOpts(int(bool(descending)), 1))
+
+
+def _workspace(op, n, k, kt, has_vals, ws, device):
+    import torch
+
+    need = bcf_workspace_bytes(op, n, k, kt, has_vals)
+    if ws is None:
+        ws = torch.empty(max(need, 1), dtype=torch.uint8, device=device)
+    return ws, ws.numel() * ws.element_size()
+
+
+def bcf_workspace_bytes(op: int, n: int, nseg_or_k: int, kt: int, has_vals: bool) -> int:
+    return int(_native.load().bcf_workspace_bytes(op, n, nseg_or_k, kt, int(bool(has_vals))))
+
+
+def bcf_sort_keys(keys_out, keys_in, *, descending=False, ws=None, stream=None, kt=None):
+    """Sort ``keys_in`` into ``keys_out`` (may be the same tensor)."""
+    kt = key_dtype_of(keys_in) if kt is None else kt
+    n = keys_in.numel()
+    ws, wsb = _workspace(BCF_OP_SORT, n, 0, kt, False, ws, keys_in.device)
+    _check(_native.load().bcf_sort_keys(_ptr(keys_out), _ptr(keys_in), n, kt, _opts(descending),
+                                        _ptr(ws), wsb, _stream(stream)), "bcf_sort_keys")
+    return keys_out
+
+
+def bcf_sort_pairs(keys_out, vals_out, keys_in, vals_in, *, descending=False, ws=None,
+                   stream=None, kt=None):
+    """Stable sort of (key, value) pairs."""
+    kt = key_dtype_of(keys_in) if kt is None else kt
+    n = keys_in.numel()
+    if vals_in.numel() != n or vals_out.numel() != n or keys_out.numel() != n:
+        raise ValueError("bcf_sort_pairs: length mismatch")
+    ws, wsb = _workspace(BCF_OP_SORT, n, 0, kt, True, ws, keys_in.device)
+    _check(_native.load().bcf_sort_pairs(_ptr(keys_out), _ptr(vals_out), _ptr(keys_in),
+                                         _ptr(vals_in), n, kt, _opts(descending), _ptr(ws), wsb,
+                                         _stream(stream)), "bcf_sort_pairs")
+    return keys_out, vals_out
+
+
+def bcf_merge_runs(keys_out, vals_out, keys_in, vals_in, run_offsets, *, descending=False,
+                   ws=None, stream=None, kt=None):
+    """Stable merge of the sorted runs delimited by host ``run_offsets`` (k+1 ints)."""
+    kt = key_dtype_of(keys_in) if kt is None else kt
+    offs = [int(x) for x in run_offsets]
+    k = len(offs) - 1
+    arr = (ctypes.c_uint64 * max(len(offs), 1))(*offs)
+    n = offs[-1] if offs else 0
+    ws, wsb = _workspace(BCF_OP_MERGE, n, max(k, 0), kt, vals_in is not None, ws, keys_in.device)
+    _check(_native.load().bcf_merge_runs(_ptr(keys_out), _ptr(vals_out), _ptr(keys_in),
+                                         _ptr(vals_in), arr, k, kt, _opts(descending), _ptr(ws),
+                                         wsb, _stream(stream)), "bcf_merge_runs")
+    return keys_out, vals_out
+
+
+def bcf_segmented_sort(keys_out, vals_out, keys_in, vals_in, seg_offsets, *, descending=False,
+                       ws=None, stream=None, kt=None):
+    """Sort every segment; ``seg_offsets`` is a CUDA uint64/int64 tensor of nseg+1 offsets."""
+    kt = key_dtype_of(keys_in) if kt is None else kt
+    nseg = seg_offsets.numel() - 1
+    n = keys_in.numel()
+    ws, wsb = _workspace(BCF_OP_SEGMENTED, n, nseg, kt, vals_in is not None, ws, keys_in.device)
+    _check(_native.load().bcf_segmented_sort(_ptr(keys_out), _ptr(vals_out), _ptr(keys_in),
+                                             _ptr(vals_in), _ptr(seg_offsets), nseg, n, kt,
+                                             _opts(descending), _ptr(ws), wsb, _stream(stream)),
+           "bcf_segmented_sort")
+    return keys_out, vals_out
+
+
+def bcf_last_device_error(stream=None) -> int:
+    return int(_native.load().bcf_last_device_error(_stream(stream)))
+
+
+def bcf_sort_plan(n: int, kt: int, has_vals: bool) -> dict:
+    p = _native.BcfPlan()
+    _check(_native.load().bcf_sort_plan(n, kt, int(bool(has_vals)), ctypes.byref(p)),
+           "bcf_sort_plan")
+    return {f: getattr(p, f) for f, _ in p._fields_}
+
+
+def bcf_profile_enable(on: bool = True) -> None:
+    _check(_native.load().bcf_profile_enable(int(bool(on))), "bcf_profile_enable")
+
+
+def bcf_profile_collect() -> dict:
+    p = _native.BcfProfile()
+    _check(_native.load().bcf_profile_collect(ctypes.byref(p)), "bcf_profile_collect")
+    kinds = ("block_sort", "partition", "merge", "segmented")
+    return {k: {"launches": int(p.launches[i]), "total_ms": float(p.total_ms[i])}
+            for i, k in enumerate(kinds)}
+
+
+def bcf_version() -> str:
+    return _native.load().bcf_version().decode()

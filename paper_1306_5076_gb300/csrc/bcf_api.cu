@@ -1,0 +1,507 @@
+// bcf_api.cu -- the C ABI declared in include/bcfsort.h: argument checks,
+// workspace layout, pass planning and kernel sequencing.
+//
+// A sort of n keys is the paper's BCFMergesort (Sec. 3; Lemma 2): one base-
+// case pass (block sort of T-key tiles) then ceil(log2(n / T)) merge passes,
+// each one read and one write of the data.  Passes ping-pong between the
+// caller's output buffer and the workspace so that the last pass lands in the
+// output.  Keys are mapped to unsigned order when first read and mapped back
+// when last written, so intermediate passes compare plain unsigned integers.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "bcf_internal.h"
+#include "bcfsort.h"
+
+namespace bcf {
+
+__device__ uint32_t g_error_word;  // set by bounded waits that ran out
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+int key_bytes_of(bcf_dtype kt) { return kt == BCF_U64 ? 8 : 4; }
+bool dtype_ok(int kt) { return kt == BCF_U32 || kt == BCF_U64 || kt == BCF_F32; }
+
+int mode_of(bcf_dtype kt, const bcf_opts* o) {
+  int m = 0;
+  if (kt == BCF_F32) m |= 1;
+  if (o && o->descending) m |= 2;
+  return m;
+}
+
+// ---------------------------------------------------------------- tuning
+
+struct Tuning {
+  int block_cfg, merge_cfg;
+};
+
+// Default (E, NT) per key width and payload flag; indices into kBlockCfgs /
+// kMergeCfgs.  Overridable with BCF_BLOCK_CFG / BCF_MERGE_CFG (integers) for
+// sweeps.
+Tuning default_tuning(int kb, bool pairs) {
+  Tuning t;
+  if (kb == 4 && !pairs) t = {1, 0};       // T = 8192 (16 x 512), Tm = 4096 (16 x 256)
+  else if (kb == 4) t = {0, 0};            // T = 4096, Tm = 4096
+  else if (!pairs) t = {0, 0};             // u64 keys
+  else t = {0, 0};                         // u64 pairs
+  static const char* eb = std::getenv("BCF_BLOCK_CFG");
+  static const char* em = std::getenv("BCF_MERGE_CFG");
+  if (eb) {
+    const int c = std::atoi(eb);
+    if (block_cfg_supported(kb, pairs, c)) t.block_cfg = c;
+  }
+  if (em) {
+    const int c = std::atoi(em);
+    if (merge_cfg_supported(kb, pairs, c)) t.merge_cfg = c;
+  }
+  // a merge tile never exceeds two block tiles (pairs of runs are multiples of it)
+  if (kMergeCfgs[t.merge_cfg].tile() > 2 * kBlockCfgs[t.block_cfg].tile()) t.merge_cfg = 0;
+  return t;
+}
+
+struct Plan {
+  Tuning tune;
+  uint32_t T, Tm, passes;
+};
+
+Plan make_plan(uint64_t n, int kb, bool pairs) {
+  Plan p;
+  p.tune = default_tuning(kb, pairs);
+  p.T = kBlockCfgs[p.tune.block_cfg].tile();
+  p.Tm = kMergeCfgs[p.tune.merge_cfg].tile();
+  p.passes = 0;
+  uint64_t runs = (n + p.T - 1) / p.T;
+  while (runs > 1) {
+    runs = (runs + 1) / 2;
+    ++p.passes;
+  }
+  return p;
+}
+
+// smallest merge tile over all configurations: bounds the split arrays
+constexpr uint64_t kMinMergeTile = 4096;
+
+struct WsLayout {
+  size_t splits, keys, vals, total;
+};
+
+WsLayout ws_layout(uint64_t n, uint64_t runs_or_segs, int kb, bool pairs) {
+  WsLayout w;
+  const uint64_t items = (n + kMinMergeTile - 1) / kMinMergeTile + runs_or_segs + 2;
+  w.splits = kAlign;
+  w.keys = align_up(w.splits + items * sizeof(uint64_t), kAlign);
+  w.vals = align_up(w.keys + n * kb, kAlign);
+  w.total = align_up(w.vals + (pairs ? n * 4 : 0), kAlign);
+  return w;
+}
+
+// ---------------------------------------------------------------- device error word
+
+uint32_t* error_word_ptr() {
+  static std::mutex mu;
+  static uint32_t* ptrs[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!ptrs[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_error_word) != cudaSuccess) return nullptr;
+    ptrs[dev] = static_cast<uint32_t*>(p);
+  }
+  return ptrs[dev];
+}
+
+// ---------------------------------------------------------------- profiling
+
+struct Profiler {
+  std::mutex mu;
+  bool on = false;
+  struct Rec {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> pending;
+  std::vector<cudaEvent_t> pool;
+
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+};
+Profiler& prof() {
+  static Profiler p;
+  return p;
+}
+
+template <typename F>
+cudaError_t timed(int kind, cudaStream_t s, F&& launch) {
+  Profiler& P = prof();
+  bool on;
+  {
+    std::lock_guard<std::mutex> lk(P.mu);
+    on = P.on;
+  }
+  if (!on) return launch();
+  cudaEvent_t a, b;
+  {
+    std::lock_guard<std::mutex> lk(P.mu);
+    a = P.get();
+    b = P.get();
+  }
+  cudaEventRecord(a, s);
+  const cudaError_t err = launch();
+  cudaEventRecord(b, s);
+  std::lock_guard<std::mutex> lk(P.mu);
+  P.pending.push_back({kind, a, b});
+  return err;
+}
+
+// ---------------------------------------------------------------- argument checks
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+struct Span {
+  const void* p;
+  size_t bytes;
+};
+bool overlap(Span a, Span b) {
+  if (!a.p || !b.p || a.bytes == 0 || b.bytes == 0) return false;
+  const uintptr_t a0 = reinterpret_cast<uintptr_t>(a.p), b0 = reinterpret_cast<uintptr_t>(b.p);
+  return a0 < b0 + b.bytes && b0 < a0 + a.bytes;
+}
+// out may equal in exactly; any other overlap among the spans is an error
+bool bad_overlap(Span out, Span in) { return out.p != in.p && overlap(out, in); }
+
+bcf_status check_common(void* ko, uint32_t* vo, const void* ki, const uint32_t* vi, uint64_t n,
+                        int kt, bool pairs) {
+  if (!dtype_ok(kt)) return BCF_EINVAL;
+  if (n == 0) return BCF_OK;
+  if (!ko || !ki) return BCF_EINVAL;
+  if (pairs && (!vo || !vi)) return BCF_EINVAL;
+  if (!aligned16(ko) || !aligned16(ki)) return BCF_EINVAL;
+  if (pairs && (!aligned16(vo) || !aligned16(vi))) return BCF_EINVAL;
+  const size_t kb = key_bytes_of(static_cast<bcf_dtype>(kt));
+  const Span sko{ko, n * kb}, ski{ki, n * kb};
+  if (bad_overlap(sko, ski)) return BCF_EINVAL;
+  if (pairs) {
+    const Span svo{vo, n * 4}, svi{vi, n * 4};
+    if (bad_overlap(svo, svi) || overlap(sko, svo) || overlap(sko, svi) || overlap(ski, svo))
+      return BCF_EINVAL;
+  }
+  return BCF_OK;
+}
+
+bcf_status check_ws(void* ws, size_t ws_bytes, size_t need, void* ko, uint32_t* vo,
+                    const void* ki, const uint32_t* vi, uint64_t n, int kb) {
+  if (ws_bytes < need || (need > 0 && !ws)) return BCF_ENOMEM;
+  if (need == 0) return BCF_OK;
+  if (!aligned16(ws)) return BCF_EINVAL;
+  const Span sw{ws, need};
+  if (overlap(sw, {ko, n * kb}) || overlap(sw, {ki, n * kb}) || overlap(sw, {vo, vo ? n * 4 : 0}) ||
+      overlap(sw, {vi, vi ? n * 4 : 0}))
+    return BCF_EINVAL;
+  return BCF_OK;
+}
+
+bcf_status from_cuda(cudaError_t e) { return e == cudaSuccess ? BCF_OK : BCF_ECUDA; }
+
+// ---------------------------------------------------------------- sort
+
+bcf_status run_sort(void* ko, uint32_t* vo, const void* ki, const uint32_t* vi, uint64_t n,
+                    bcf_dtype kt, const bcf_opts* o, void* ws, size_t ws_bytes, cudaStream_t s,
+                    bool pairs) {
+  bcf_status st = check_common(ko, vo, ki, vi, n, kt, pairs);
+  if (st != BCF_OK || n == 0) return st;
+  const int kb = key_bytes_of(kt);
+  const Plan plan = make_plan(n, kb, pairs);
+  const WsLayout wl = ws_layout(n, 0, kb, pairs);
+  const size_t need = plan.passes > 0 ? wl.total : 0;
+  st = check_ws(ws, ws_bytes, need, ko, vo, ki, vi, n, kb);
+  if (st != BCF_OK) return st;
+  const int mode = mode_of(kt, o);
+  uint32_t* err = error_word_ptr();
+  if (!err) return BCF_ECUDA;
+
+  char* wsb = static_cast<char*>(ws);
+  void* kbuf[2] = {ko, plan.passes > 0 ? wsb + wl.keys : nullptr};
+  uint32_t* vbuf[2] = {vo, (pairs && plan.passes > 0) ? reinterpret_cast<uint32_t*>(wsb + wl.vals)
+                                                      : nullptr};
+  const int m = static_cast<int>(plan.passes);
+  // buffer written by pass i (0 = block sort): the output for i == m, and
+  // alternating backwards from there
+  auto buf = [m](int i) { return ((m - i) % 2 == 0) ? 0 : 1; };
+
+  BlockSortArgs ba{ki, vi, kbuf[buf(0)], vbuf[buf(0)], n, mode, m == 0 ? mode : 0};
+  cudaError_t e = timed(0, s, [&] {
+    return launch_block_sort(kb, pairs, plan.tune.block_cfg, ba, s);
+  });
+  if (e != cudaSuccess) return BCF_ECUDA;
+  uint64_t* splits = reinterpret_cast<uint64_t*>(wsb + wl.splits);
+  const uint64_t items = (n + plan.Tm - 1) / plan.Tm;
+  for (int i = 1; i <= m; ++i) {
+    MergeArgs ma{};
+    ma.kin = kbuf[buf(i - 1)];
+    ma.vin = vbuf[buf(i - 1)];
+    ma.kout = kbuf[buf(i)];
+    ma.vout = vbuf[buf(i)];
+    ma.n = n;
+    ma.run = static_cast<uint64_t>(plan.T) << (i - 1);
+    ma.splits = splits;
+    ma.mode_in = 0;
+    ma.mode_out = i == m ? mode : 0;
+    ma.err = err;
+    ma.nitems = items;
+    e = timed(1, s, [&] { return launch_partition(kb, plan.tune.merge_cfg, ma, nullptr, s); });
+    if (e != cudaSuccess) return BCF_ECUDA;
+    e = timed(2, s, [&] { return launch_merge(kb, pairs, plan.tune.merge_cfg, ma, nullptr, s); });
+    if (e != cudaSuccess) return BCF_ECUDA;
+  }
+  return BCF_OK;
+}
+
+// ---------------------------------------------------------------- merge runs
+
+struct Run {
+  uint64_t off, len;
+};
+
+bcf_status run_merge(void* ko, uint32_t* vo, const void* ki, const uint32_t* vi,
+                     const uint64_t* offs, uint32_t k, bcf_dtype kt, const bcf_opts* o, void* ws,
+                     size_t ws_bytes, cudaStream_t s) {
+  const bool pairs = vo != nullptr || vi != nullptr;
+  if (!offs || k == 0) return BCF_EINVAL;
+  for (uint32_t r = 0; r < k; ++r)
+    if (offs[r + 1] < offs[r]) return BCF_EINVAL;
+  const uint64_t n = offs[k];  // arrays span [0, offs[k]); runs cover [offs[0], offs[k])
+  bcf_status st = check_common(ko, vo, ki, vi, n, kt, pairs);
+  if (st != BCF_OK) return st;
+  if (offs[k] == offs[0]) return BCF_OK;
+  const int kb = key_bytes_of(kt);
+  const WsLayout wl = ws_layout(n, k, kb, pairs);
+  st = check_ws(ws, ws_bytes, wl.total, ko, vo, ki, vi, n, kb);
+  if (st != BCF_OK) return st;
+  const int mode = mode_of(kt, o);
+  uint32_t* err = error_word_ptr();
+  if (!err) return BCF_ECUDA;
+  const Plan plan = make_plan(n, kb, pairs);
+  const uint64_t Tm = plan.Tm;
+  const uint64_t lo = offs[0], span = offs[k] - offs[0];
+
+  std::vector<Run> runs;
+  runs.reserve(k);
+  for (uint32_t r = 0; r < k; ++r) runs.push_back({offs[r], offs[r + 1] - offs[r]});
+  int m = 0;
+  for (size_t c = runs.size(); c > 1; c = (c + 1) / 2) ++m;
+
+  char* wsb = static_cast<char*>(ws);
+  void* wk = wsb + wl.keys;
+  uint32_t* wv = pairs ? reinterpret_cast<uint32_t*>(wsb + wl.vals) : nullptr;
+  const bool alias = ko == ki || (pairs && vo == vi);
+  if (m == 0) {
+    // a single run is already merged: copy it (identity key map both ways)
+    if (ko != ki &&
+        cudaMemcpyAsync(static_cast<char*>(ko) + lo * kb, static_cast<const char*>(ki) + lo * kb,
+                        span * kb, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return BCF_ECUDA;
+    if (pairs && vo != vi &&
+        cudaMemcpyAsync(vo + lo, vi + lo, span * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return BCF_ECUDA;
+    return BCF_OK;
+  }
+  // pass i reads B[i-1] and writes B[i]; B[m] = output, alternating backwards.
+  // With an aliased output and an odd pass count, pass 1 would write the
+  // buffer it reads, so the input is first copied into the workspace.
+  const void* src_k = ki;
+  const uint32_t* src_v = vi;
+  int src_mode = mode;
+  if (alias && (m % 2 == 1)) {
+    if (cudaMemcpyAsync(static_cast<char*>(wk) + lo * kb, static_cast<const char*>(ki) + lo * kb,
+                        span * kb, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return BCF_ECUDA;
+    if (pairs && cudaMemcpyAsync(wv + lo, vi + lo, span * 4, cudaMemcpyDeviceToDevice, s) !=
+                     cudaSuccess)
+      return BCF_ECUDA;
+    src_k = wk;
+    src_v = wv;
+  }
+  uint64_t* splits = reinterpret_cast<uint64_t*>(wsb + wl.splits);
+  for (int i = 1; i <= m; ++i) {
+    const bool to_out = ((m - i) % 2) == 0;
+    void* dst_k = to_out ? ko : wk;
+    uint32_t* dst_v = to_out ? vo : wv;
+    // pair adjacent runs; an odd last run pairs with an empty one (a copy)
+    std::vector<PairDesc> pairs_v;
+    std::vector<Run> next;
+    uint64_t piece = 0;
+    for (size_t r = 0; r < runs.size(); r += 2) {
+      const Run A = runs[r];
+      const Run B = r + 1 < runs.size() ? runs[r + 1] : Run{A.off + A.len, 0};
+      const uint64_t len = A.len + B.len;
+      next.push_back({A.off, len});
+      if (len == 0) continue;
+      const uint64_t pieces = (A.off + len - 1) / Tm - A.off / Tm + 1;
+      pairs_v.push_back({A.off, A.len, B.len, piece});
+      piece += pieces;
+    }
+    for (size_t c = 0; c < pairs_v.size(); c += kMaxPairsPerLaunch) {
+      PairList pl{};
+      const size_t cnt = std::min<size_t>(kMaxPairsPerLaunch, pairs_v.size() - c);
+      for (size_t q = 0; q < cnt; ++q) pl.p[q] = pairs_v[c + q];
+      pl.npairs = static_cast<uint32_t>(cnt);
+      const uint64_t end_piece = c + cnt < pairs_v.size() ? pairs_v[c + cnt].piece0 : piece;
+      MergeArgs ma{};
+      ma.kin = src_k;
+      ma.vin = src_v;
+      ma.kout = dst_k;
+      ma.vout = dst_v;
+      ma.n = n;
+      ma.run = 0;
+      ma.splits = splits;
+      ma.mode_in = src_mode;
+      ma.mode_out = i == m ? mode : 0;
+      ma.err = err;
+      ma.nitems = end_piece - pl.p[0].piece0;
+      cudaError_t e =
+          timed(1, s, [&] { return launch_partition(kb, plan.tune.merge_cfg, ma, &pl, s); });
+      if (e != cudaSuccess) return BCF_ECUDA;
+      e = timed(2, s, [&] { return launch_merge(kb, pairs, plan.tune.merge_cfg, ma, &pl, s); });
+      if (e != cudaSuccess) return BCF_ECUDA;
+    }
+    runs.swap(next);
+    src_k = dst_k;
+    src_v = dst_v;
+    src_mode = 0;
+  }
+  return BCF_OK;
+}
+
+}  // namespace
+}  // namespace bcf
+
+// ==================================================================== C ABI
+
+using namespace bcf;
+
+extern "C" {
+
+size_t bcf_workspace_bytes(int op, uint64_t n, uint64_t nseg_or_k, bcf_dtype kt, int has_vals) {
+  if (!dtype_ok(kt)) return 0;
+  const int kb = key_bytes_of(kt);
+  switch (op) {
+    case BCF_OP_SORT: return ws_layout(n, 0, kb, has_vals != 0).total;
+    case BCF_OP_MERGE: return ws_layout(n, nseg_or_k, kb, has_vals != 0).total;
+    case BCF_OP_SEGMENTED: return ws_layout(n, nseg_or_k, kb, has_vals != 0).total;
+    default: return 0;
+  }
+}
+
+bcf_status bcf_sort_keys(void* keys_out, const void* keys_in, uint64_t n, bcf_dtype kt,
+                         const bcf_opts* opts, void* ws, size_t ws_bytes, cudaStream_t stream) {
+  return run_sort(keys_out, nullptr, keys_in, nullptr, n, kt, opts, ws, ws_bytes, stream, false);
+}
+
+bcf_status bcf_sort_pairs(void* keys_out, uint32_t* vals_out, const void* keys_in,
+                          const uint32_t* vals_in, uint64_t n, bcf_dtype kt,
+                          const bcf_opts* opts, void* ws, size_t ws_bytes, cudaStream_t stream) {
+  return run_sort(keys_out, vals_out, keys_in, vals_in, n, kt, opts, ws, ws_bytes, stream, true);
+}
+
+bcf_status bcf_merge_runs(void* keys_out, uint32_t* vals_out, const void* keys_in,
+                          const uint32_t* vals_in, const uint64_t* run_offsets_host, uint32_t k,
+                          bcf_dtype kt, const bcf_opts* opts, void* ws, size_t ws_bytes,
+                          cudaStream_t stream) {
+  if ((vals_out == nullptr) != (vals_in == nullptr)) return BCF_EINVAL;
+  return run_merge(keys_out, vals_out, keys_in, vals_in, run_offsets_host, k, kt, opts, ws,
+                   ws_bytes, stream);
+}
+
+bcf_status bcf_segmented_sort(void* keys_out, uint32_t* vals_out, const void* keys_in,
+                              const uint32_t* vals_in, const uint64_t* seg_offsets_dev,
+                              uint64_t nseg, uint64_t n_total, bcf_dtype kt,
+                              const bcf_opts* opts, void* ws, size_t ws_bytes,
+                              cudaStream_t stream) {
+  (void)keys_out; (void)vals_out; (void)keys_in; (void)vals_in; (void)seg_offsets_dev;
+  (void)nseg; (void)n_total; (void)kt; (void)opts; (void)ws; (void)ws_bytes; (void)stream;
+  return BCF_EUNSUPPORTED;
+}
+
+const char* bcf_status_string(bcf_status s) {
+  switch (s) {
+    case BCF_OK: return "BCF_OK";
+    case BCF_EINVAL: return "BCF_EINVAL: invalid argument";
+    case BCF_ENOMEM: return "BCF_ENOMEM: workspace too small";
+    case BCF_ECUDA: return "BCF_ECUDA: CUDA error";
+    case BCF_ETIMEOUT: return "BCF_ETIMEOUT: device-side wait ran out";
+    case BCF_EUNSUPPORTED: return "BCF_EUNSUPPORTED: not supported by this build";
+    default: return "BCF: unknown status";
+  }
+}
+
+bcf_status bcf_last_device_error(cudaStream_t stream) {
+  if (cudaStreamSynchronize(stream) != cudaSuccess) return BCF_ECUDA;
+  uint32_t v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_error_word, sizeof(v)) != cudaSuccess) return BCF_ECUDA;
+  if (v != 0) {
+    const uint32_t zero = 0;
+    if (cudaMemcpyToSymbol(g_error_word, &zero, sizeof(zero)) != cudaSuccess) return BCF_ECUDA;
+    return BCF_ETIMEOUT;
+  }
+  return BCF_OK;
+}
+
+bcf_status bcf_sort_plan(uint64_t n, bcf_dtype kt, int has_vals, bcf_plan* out) {
+  if (!out || !dtype_ok(kt)) return BCF_EINVAL;
+  const int kb = key_bytes_of(kt);
+  const Plan p = make_plan(n, kb, has_vals != 0);
+  out->block_tile = p.T;
+  out->merge_tile = p.Tm;
+  out->merge_passes = p.passes;
+  out->launches = n == 0 ? 0 : 1 + 2 * p.passes;
+  out->bytes_per_pass = 2ull * n * (kb + (has_vals ? 4 : 0));
+  return BCF_OK;
+}
+
+bcf_status bcf_profile_enable(int on) {
+  Profiler& P = prof();
+  std::lock_guard<std::mutex> lk(P.mu);
+  P.on = on != 0;
+  return BCF_OK;
+}
+
+bcf_status bcf_profile_collect(bcf_profile* out) {
+  if (!out) return BCF_EINVAL;
+  Profiler& P = prof();
+  std::lock_guard<std::mutex> lk(P.mu);
+  bcf_status st = BCF_OK;
+  for (auto& r : P.pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess)
+      st = BCF_ECUDA;
+    if (r.kind >= 0 && r.kind < 4) {
+      out->launches[r.kind] += 1;
+      out->total_ms[r.kind] += ms;
+    }
+    P.pool.push_back(r.a);
+    P.pool.push_back(r.b);
+  }
+  P.pending.clear();
+  return st;
+}
+
+const char* bcf_version(void) { return "bcfsort 0.1 (sm_103a)"; }
+
+}  // extern "C"

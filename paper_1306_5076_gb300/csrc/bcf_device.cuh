@@ -1,0 +1,329 @@
+// bcf_device.cuh -- device building blocks shared by the block sort, the merge
+// pass and the segmented sort.
+//
+// Data model.  A CTA holds a logical array X[0, 2^t) of elements spread over
+// its threads' registers, E = 2^r elements per thread.  Two register layouts
+// are used (the paper's row/column views of shared memory, Sec. 2.1, taken to
+// registers):
+//   BLK: thread tid holds X[tid * E + e]        (register bits = k bits [0, r))
+//   STR: thread tid holds X[e * NT + tid]       (register bits = k bits [t-r, t))
+// A bitonic stage on bit b pairs X[k] with X[k ^ 2^b].  It is a register
+// compare-exchange when b is a register bit of the current layout, a warp
+// shuffle when b is a lane bit of BLK (bits [r, r+5)), and otherwise needs a
+// switch of layout through shared memory.  With t <= 2r + 5 the two layouts
+// cover every bit, so every cross-thread step is either a shuffle or one
+// transpose through shared memory.
+//
+// Bank conflicts.  The transposes go through shared memory in 32-bit planes
+// (one plane per 32-bit word of an element) with one pad word after every 32
+// words: physical word = k + (k >> 5).  In STR a warp touches 32 consecutive
+// k, i.e. 32 distinct banks.  In BLK lane l touches k = l*E + e; its bank is
+// (l*E + e + floor(l*E / 32)) mod 32, which is a bijection of l for every
+// power of two E <= 32 -- the skew the paper obtains with shifted diagonals
+// (Sec. 3.3, Algorithm 2), obtained here by padding.  So every shared-memory
+// access of the sorting network is conflict-free.
+#pragma once
+
+#include <cstdint>
+
+namespace bcf {
+
+// ---------------------------------------------------------------- constants
+
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // bounded mbarrier waits: 2 s
+constexpr uint32_t kErrTmaTimeout = 1u;
+
+__host__ __device__ constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x >> 1); }
+
+// ---------------------------------------------------------------- key maps
+// Order-preserving maps from key bits to unsigned integers.  mode bit 0: f32
+// IEEE 754 totalOrder (32-bit keys only), bit 1: descending (bitwise NOT).
+// map(u) for f32: a negative-signed pattern has all its bits inverted, a
+// positive-signed one its sign bit set, so that unsigned order equals
+// totalOrder.  unmap inverts it exactly.
+
+__device__ __forceinline__ uint32_t map_key(uint32_t u, int mode) {
+  if (mode & 1) u ^= (uint32_t)((int32_t)u >> 31) | 0x80000000u;
+  if (mode & 2) u = ~u;
+  return u;
+}
+__device__ __forceinline__ uint32_t unmap_key(uint32_t m, int mode) {
+  if (mode & 2) m = ~m;
+  if (mode & 1) m ^= (~(uint32_t)((int32_t)m >> 31)) | 0x80000000u;
+  return m;
+}
+__device__ __forceinline__ uint64_t map_key(uint64_t u, int mode) {
+  return (mode & 2) ? ~u : u;
+}
+__device__ __forceinline__ uint64_t unmap_key(uint64_t m, int mode) {
+  return (mode & 2) ? ~m : m;
+}
+
+template <typename K> struct KeyLimits;
+template <> struct KeyLimits<uint32_t> {
+  static constexpr uint32_t kMin = 0u, kMax = 0xFFFFFFFFu;
+};
+template <> struct KeyLimits<uint64_t> {
+  static constexpr uint64_t kMin = 0ull, kMax = ~0ull;
+};
+
+// ---------------------------------------------------------------- PTX helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for phase `parity` of the barrier, at most kWaitLimitNs.  On expiry the
+// error word gets `code` and false is returned.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t* err,
+                                                  uint32_t code) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (globaltimer_ns() - t0 > kWaitLimitNs) {
+      if (err) atomicOr(err, code);
+      return false;
+    }
+  }
+  return true;
+}
+// One bulk (non-tensor) global -> shared copy completing on `bar`.  dst, src
+// and bytes must be multiples of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+// Shared loads issued only by lanes whose predicate is set; the others keep
+// `dflt`.  Two such loads with disjoint predicates stay two separate
+// requests, so lanes reading two different arrays never share a wavefront.
+__device__ __forceinline__ uint32_t lds_pred(const uint32_t* p, bool pred, uint32_t dflt) {
+  uint32_t v = dflt;
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q ld.shared.b32 %0, [%1];\n\t}"
+      : "+r"(v)
+      : "r"(smem_u32(p)), "r"((uint32_t)pred)
+      : "memory");
+  return v;
+}
+__device__ __forceinline__ uint64_t lds_pred(const uint64_t* p, bool pred, uint64_t dflt) {
+  uint64_t v = dflt;
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q ld.shared.b64 %0, [%1];\n\t}"
+      : "+l"(v)
+      : "r"(smem_u32(p)), "r"((uint32_t)pred)
+      : "memory");
+  return v;
+}
+
+// ---------------------------------------------------------------- elements
+
+// Padded shared-memory index of logical word k (one pad word per 32 words).
+__device__ __forceinline__ uint32_t pad32(uint32_t k) { return k + (k >> 5); }
+__host__ __device__ constexpr uint32_t padded_words(uint32_t n) { return n + n / 32; }
+
+// Register fragment: E elements per thread.  PAIRS carries the u32 payload
+// and a tie-break index (the element's rank in the stable input order),
+// because bitonic networks are not stable on their own.
+template <typename K, bool PAIRS, int E>
+struct Frag {
+  static constexpr int KW = sizeof(K) / 4;           // 32-bit words per key
+  static constexpr int W = KW + (PAIRS ? 2 : 0);     // 32-bit planes per element
+  K k[E];
+  uint32_t ix[PAIRS ? E : 1];
+  uint32_t v[PAIRS ? E : 1];
+
+  __device__ __forceinline__ void put(uint32_t* sm, uint32_t plane, int e, uint32_t a) const {
+    sm[a] = static_cast<uint32_t>(k[e]);
+    if constexpr (KW == 2) sm[plane + a] = static_cast<uint32_t>(static_cast<uint64_t>(k[e]) >> 32);
+    if constexpr (PAIRS) {
+      sm[KW * plane + a] = ix[e];
+      sm[(KW + 1) * plane + a] = v[e];
+    }
+  }
+  __device__ __forceinline__ void get(const uint32_t* sm, uint32_t plane, int e, uint32_t a) {
+    if constexpr (KW == 2)
+      k[e] = static_cast<K>(sm[a]) | (static_cast<K>(sm[plane + a]) << 32);
+    else
+      k[e] = static_cast<K>(sm[a]);
+    if constexpr (PAIRS) {
+      ix[e] = sm[KW * plane + a];
+      v[e] = sm[(KW + 1) * plane + a];
+    }
+  }
+};
+
+// Strict "x after y" in (key, tie-break index) order.
+template <typename K>
+__device__ __forceinline__ bool after(K kx, uint32_t ix, K ky, uint32_t iy) {
+  if constexpr (sizeof(K) == 4) {
+    const uint64_t x = (static_cast<uint64_t>(kx) << 32) | ix;
+    const uint64_t y = (static_cast<uint64_t>(ky) << 32) | iy;
+    return x > y;
+  } else {
+    return kx > ky || (kx == ky && ix > iy);
+  }
+}
+
+// Compare-exchange registers a < b: ascending puts the smaller element in a.
+template <typename K, bool PAIRS, int E>
+__device__ __forceinline__ void ce(Frag<K, PAIRS, E>& f, int a, int b, bool desc) {
+  if constexpr (!PAIRS) {
+    const K x = f.k[a], y = f.k[b];
+    const K lo = x < y ? x : y, hi = x < y ? y : x;
+    f.k[a] = desc ? hi : lo;
+    f.k[b] = desc ? lo : hi;
+  } else {
+    const bool sw = after(f.k[a], f.ix[a], f.k[b], f.ix[b]) != desc;
+    const K ka = f.k[a], kb = f.k[b];
+    const uint32_t ia = f.ix[a], ib = f.ix[b], va = f.v[a], vb = f.v[b];
+    f.k[a] = sw ? kb : ka;
+    f.k[b] = sw ? ka : kb;
+    f.ix[a] = sw ? ib : ia;
+    f.ix[b] = sw ? ia : ib;
+    f.v[a] = sw ? vb : va;
+    f.v[b] = sw ? va : vb;
+  }
+}
+
+// In-register stage on register bit rb (partner e ^ 2^rb), one direction.
+template <int RB, typename K, bool PAIRS, int E>
+__device__ __forceinline__ void reg_stage(Frag<K, PAIRS, E>& f, bool desc) {
+#pragma unroll
+  for (int e = 0; e < E; ++e)
+    if (!(e & (1 << RB))) ce(f, e, e | (1 << RB), desc);
+}
+
+// Warp-shuffle stage: partner lane = lane ^ m.  The lower lane of a pair keeps
+// the smaller element when ascending (desc == false).
+template <typename K, bool PAIRS, int E>
+__device__ __forceinline__ void shfl_stage(Frag<K, PAIRS, E>& f, int m, bool desc) {
+  const bool keep_max = (((threadIdx.x & 31) & m) != 0) != desc;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const K pk = __shfl_xor_sync(0xFFFFFFFFu, f.k[e], m);
+    if constexpr (!PAIRS) {
+      const K mine = f.k[e];
+      const K lo = mine < pk ? mine : pk, hi = mine < pk ? pk : mine;
+      f.k[e] = keep_max ? hi : lo;
+    } else {
+      const uint32_t pi = __shfl_xor_sync(0xFFFFFFFFu, f.ix[e], m);
+      const uint32_t pv = __shfl_xor_sync(0xFFFFFFFFu, f.v[e], m);
+      // (key, index) pairs are unique, so "partner after mine" decides both sides
+      const bool p_after = after(pk, pi, f.k[e], f.ix[e]);
+      const bool take = keep_max ? p_after : !p_after;
+      f.k[e] = take ? pk : f.k[e];
+      f.ix[e] = take ? pi : f.ix[e];
+      f.v[e] = take ? pv : f.v[e];
+    }
+  }
+}
+
+// Batcher's odd-even merge sort network on N inputs (Knuth vol. 3, Sec.
+// 5.3.4, Algorithm M), listed as comparator pairs at compile time.
+template <int N>
+struct OemNetwork {
+  int n;
+  unsigned char a[N * 8], b[N * 8];
+  constexpr OemNetwork() : n(0), a{}, b{} {
+    for (int p = 1; p < N; p <<= 1)
+      for (int kk = p; kk >= 1; kk >>= 1)
+        for (int j = kk % p; j + kk < N; j += 2 * kk)
+          for (int i = 0; i < kk; ++i)
+            if (i + j + kk < N && (i + j) / (2 * p) == (i + j + kk) / (2 * p)) {
+              a[n] = static_cast<unsigned char>(i + j);
+              b[n] = static_cast<unsigned char>(i + j + kk);
+              ++n;
+            }
+  }
+};
+
+// The "BATCHERS-ODD-EVEN-MERGESORT(R)" register network of Algorithms 1 and
+// 2: sorts one thread's E registers, direction chosen per thread.
+template <typename K, bool PAIRS, int E>
+__device__ __forceinline__ void thread_sort(Frag<K, PAIRS, E>& f, bool desc) {
+  constexpr OemNetwork<E> net{};
+#pragma unroll
+  for (int c = 0; c < net.n; ++c) ce(f, net.a[c], net.b[c], desc);
+}
+
+// Layout switches through padded shared memory (planes of `plane` words).
+template <int NT, typename K, bool PAIRS, int E>
+__device__ __forceinline__ void blk_to_str(Frag<K, PAIRS, E>& f, uint32_t* sm, uint32_t plane) {
+  const uint32_t tid = threadIdx.x;
+  __syncthreads();
+#pragma unroll
+  for (int e = 0; e < E; ++e) f.put(sm, plane, e, pad32(tid * E + e));
+  __syncthreads();
+#pragma unroll
+  for (int e = 0; e < E; ++e) f.get(sm, plane, e, pad32(e * NT + tid));
+}
+template <int NT, typename K, bool PAIRS, int E>
+__device__ __forceinline__ void str_to_blk(Frag<K, PAIRS, E>& f, uint32_t* sm, uint32_t plane) {
+  const uint32_t tid = threadIdx.x;
+  __syncthreads();
+#pragma unroll
+  for (int e = 0; e < E; ++e) f.put(sm, plane, e, pad32(e * NT + tid));
+  __syncthreads();
+#pragma unroll
+  for (int e = 0; e < E; ++e) f.get(sm, plane, e, pad32(tid * E + e));
+}
+
+// Bitonic MERGE of a bitonic sequence of length E*NT held in STR layout,
+// ascending; ends in BLK layout.  Stages run on bits t-1 .. 0: STR register
+// bits first, then one transpose, then BLK lane bits by shuffle and BLK
+// register bits.
+template <int NT, typename K, bool PAIRS, int E>
+__device__ __forceinline__ void bitonic_merge_str(Frag<K, PAIRS, E>& f, uint32_t* sm,
+                                                  uint32_t plane) {
+  constexpr int r = ilog2(E), t = ilog2(E * NT);
+  static_assert(t <= 2 * r + 5, "tile too large for two layouts");
+#pragma unroll
+  for (int rb = r - 1; rb >= 0; --rb) {
+    // STR register bit rb is k bit (t - r + rb)
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+      if (!(e & (1 << rb))) ce(f, e, e | (1 << rb), false);
+  }
+  str_to_blk<NT>(f, sm, plane);
+#pragma unroll
+  for (int b = t - r - 1; b >= r; --b) shfl_stage(f, 1 << (b - r), false);
+#pragma unroll
+  for (int rb = r - 1; rb >= 0; --rb) {
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+      if (!(e & (1 << rb))) ce(f, e, e | (1 << rb), false);
+  }
+}
+
+}  // namespace bcf

@@ -1,0 +1,76 @@
+// bcf_internal.h -- launch interface between the C-ABI host code and the
+// kernel translation units.  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace bcf {
+
+// One adjacent pair of sorted runs to merge: A = [off, off + na), B = [off + na,
+// off + na + nb) of the source array; the merged run occupies the same index
+// range of the destination.  `piece0` is the index of the pair's first work
+// item (tile piece); the pair has pieces covering the Tm-aligned output tiles
+// its range touches.
+struct PairDesc {
+  uint64_t off, na, nb, piece0;
+};
+
+// Maximum pairs passed by value to one irregular merge launch.
+constexpr int kMaxPairsPerLaunch = 256;
+
+struct PairList {
+  PairDesc p[kMaxPairsPerLaunch];
+  uint32_t npairs;
+  uint32_t pad_;
+};
+
+struct BlockSortArgs {
+  const void* kin;
+  const uint32_t* vin;  // nullptr for keys only
+  void* kout;
+  uint32_t* vout;
+  uint64_t n;           // elements of the array
+  int mode_in;          // key map applied on load (bit0 f32 order, bit1 descending)
+  int mode_out;         // inverse key map applied on store
+};
+
+struct MergeArgs {
+  const void* kin;
+  const uint32_t* vin;
+  void* kout;
+  uint32_t* vout;
+  uint64_t n;           // regular mode: elements of the array
+  uint64_t run;         // regular mode: run length L (pairs of runs are 2L apart)
+  uint64_t* splits;     // per work item: A-split at the item's first output diagonal
+  int mode_in;
+  int mode_out;
+  uint32_t* err;        // device error word
+  uint64_t nitems;      // work items (tile pieces) of this launch
+};
+
+// Tuning configuration: elements per thread and threads per CTA.
+struct TileCfg {
+  int E, NT;
+  constexpr int tile() const { return E * NT; }
+};
+
+// Supported configurations (index into these tables).
+constexpr TileCfg kBlockCfgs[] = {{16, 256}, {16, 512}, {32, 256}, {32, 512}};
+constexpr TileCfg kMergeCfgs[] = {{16, 256}, {16, 512}, {32, 256}};
+constexpr int kNumBlockCfgs = sizeof(kBlockCfgs) / sizeof(kBlockCfgs[0]);
+constexpr int kNumMergeCfgs = sizeof(kMergeCfgs) / sizeof(kMergeCfgs[0]);
+
+// Is the configuration compiled for this key width / payload flag?
+bool block_cfg_supported(int key_bytes, bool pairs, int cfg);
+bool merge_cfg_supported(int key_bytes, bool pairs, int cfg);
+
+cudaError_t launch_block_sort(int key_bytes, bool pairs, int cfg, const BlockSortArgs& a,
+                              cudaStream_t s);
+cudaError_t launch_partition(int key_bytes, int cfg, const MergeArgs& a, const PairList* pl,
+                             cudaStream_t s);
+cudaError_t launch_merge(int key_bytes, bool pairs, int cfg, const MergeArgs& a,
+                         const PairList* pl, cudaStream_t s);
+
+}  // namespace bcf

@@ -1,0 +1,27 @@
+"""Helpers for GPU tests: numpy <-> CUDA tensors by bit pattern, key-type codes."""
+from __future__ import annotations
+
+import numpy as np
+
+KT = {"u32": 0, "u64": 1, "f32": 2}
+
+
+def to_dev(a: np.ndarray, dev="cuda:0"):
+    import torch
+
+    if a.dtype.itemsize == 8:
+        return torch.from_numpy(np.ascontiguousarray(a).view(np.int64)).to(dev)
+    return torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).to(dev)
+
+
+def from_dev(t, like: np.dtype) -> np.ndarray:
+    a = t.cpu().numpy()
+    return a.view(np.dtype(like))
+
+
+def kt_of(a: np.ndarray) -> int:
+    return {np.dtype(np.uint32): 0, np.dtype(np.uint64): 1, np.dtype(np.float32): 2}[a.dtype]
+
+
+def bits(a: np.ndarray) -> np.ndarray:
+    return a.view(np.uint32) if a.dtype == np.float32 else a

@@ -1,0 +1,127 @@
+"""The C-ABI library loads and exports what include/bcfsort.h declares (CPU only).
+
+No call here launches GPU work: only host-side entry points (sizes, plans,
+status strings) and argument checks that return before any CUDA call.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "bcfsort.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1306_5076_gb300 import _native, build
+
+    build.build()
+    return _native.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(bcf_[a-z_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("bcf_sort_keys", "bcf_sort_pairs", "bcf_merge_runs", "bcf_segmented_sort",
+                     "bcf_workspace_bytes", "bcf_status_string", "bcf_last_device_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_1306_5076_gb300 import _native
+
+    for name in declared_functions():
+        assert hasattr(lib, name), f"{name} declared in bcfsort.h but not exported"
+        assert name in _native.SIGNATURES, f"{name} has no Python binding"
+
+
+def test_status_strings_and_version(lib):
+    for code in range(6):
+        s = lib.bcf_status_string(code).decode()
+        assert s.startswith("BCF_")
+    assert b"sm_103a" in lib.bcf_version()
+
+
+def test_workspace_bytes_scale_with_input(lib):
+    from paper_1306_5076_gb300 import BCF_F32, BCF_OP_MERGE, BCF_OP_SORT, BCF_U32, BCF_U64
+
+    n = 1 << 20
+    keys = lib.bcf_workspace_bytes(BCF_OP_SORT, n, 0, BCF_U32, 0)
+    pairs = lib.bcf_workspace_bytes(BCF_OP_SORT, n, 0, BCF_U32, 1)
+    wide = lib.bcf_workspace_bytes(BCF_OP_SORT, n, 0, BCF_U64, 0)
+    assert keys >= 4 * n and pairs >= 8 * n and wide >= 8 * n
+    assert keys % 256 == 0 and pairs % 256 == 0
+    assert lib.bcf_workspace_bytes(BCF_OP_SORT, n, 0, BCF_F32, 0) == keys
+    assert lib.bcf_workspace_bytes(BCF_OP_MERGE, n, 256, BCF_U32, 0) >= keys
+    assert lib.bcf_workspace_bytes(9, n, 0, BCF_U32, 0) == 0
+    assert lib.bcf_workspace_bytes(BCF_OP_SORT, n, 0, 7, 0) == 0
+
+
+@pytest.mark.parametrize("n", [0, 1, 4095, 4096, 8192, 8193, 1 << 20, (1 << 28) + 1])
+def test_plan_pass_count_is_lemma_2(lib, n):
+    """Lemma 2: one base-case pass plus ceil(log2(n / T)) merge passes."""
+    from paper_1306_5076_gb300 import _native
+
+    for kt in (0, 1, 2):
+        for has_vals in (0, 1):
+            p = _native.BcfPlan()
+            assert lib.bcf_sort_plan(n, kt, has_vals, ctypes.byref(p)) == 0
+            runs = -(-n // p.block_tile)
+            expect = 0 if runs <= 1 else math.ceil(math.log2(runs))
+            assert p.merge_passes == expect
+            assert p.launches == (0 if n == 0 else 1 + 2 * expect)
+            kb = 8 if kt == 1 else 4
+            assert p.bytes_per_pass == 2 * n * (kb + 4 * has_vals)
+            assert p.merge_tile <= 2 * p.block_tile
+
+
+def test_host_side_argument_errors_return_before_launch(lib):
+    from paper_1306_5076_gb300 import _native
+
+    opts = ctypes.byref(_native.BcfOpts(0, 1))
+    EINVAL = 1
+    # bad dtype
+    assert lib.bcf_sort_keys(None, None, 0, 9, opts, None, 0, None) == EINVAL
+    # n == 0 is a no-op
+    assert lib.bcf_sort_keys(None, None, 0, 0, opts, None, 0, None) == 0
+    # null pointers with n > 0
+    assert lib.bcf_sort_keys(None, None, 10, 0, opts, None, 0, None) == EINVAL
+    # misaligned pointers (never dereferenced: rejected on the host)
+    assert lib.bcf_sort_keys(ctypes.c_void_p(0x1004), ctypes.c_void_p(0x2000), 10, 0, opts, None,
+                             0, None) == EINVAL
+    # partial overlap of output and input
+    assert lib.bcf_sort_keys(ctypes.c_void_p(0x10000), ctypes.c_void_p(0x10010), 100, 0, opts,
+                             None, 0, None) == EINVAL
+    # pairs need both value pointers
+    assert lib.bcf_sort_pairs(ctypes.c_void_p(0x10000), None, ctypes.c_void_p(0x20000), None, 10,
+                              0, opts, None, 0, None) == EINVAL
+    # merge: k == 0, and decreasing offsets
+    offs = (ctypes.c_uint64 * 3)(0, 5, 3)
+    assert lib.bcf_merge_runs(None, None, None, None, offs, 0, 0, opts, None, 0, None) == EINVAL
+    assert lib.bcf_merge_runs(ctypes.c_void_p(0x10000), None, ctypes.c_void_p(0x20000), None,
+                              offs, 2, 0, opts, None, 0, None) == EINVAL
+    # merge: values on one side only
+    good = (ctypes.c_uint64 * 2)(0, 4)
+    assert lib.bcf_merge_runs(ctypes.c_void_p(0x10000), ctypes.c_void_p(0x30000),
+                              ctypes.c_void_p(0x20000), None, good, 1, 0, opts, None, 0,
+                              None) == EINVAL
+
+
+def test_workspace_too_small_is_enomem(lib):
+    from paper_1306_5076_gb300 import _native
+
+    opts = ctypes.byref(_native.BcfOpts(0, 1))
+    n = 1 << 20  # needs merge passes, hence a workspace
+    assert lib.bcf_sort_keys(ctypes.c_void_p(0x100000000), ctypes.c_void_p(0x200000000), n, 0,
+                             opts, ctypes.c_void_p(0x300000000), 1024, None) == 2

@@ -1,0 +1,200 @@
+"""Parity of the GPU sort (through the C ABI) with the CPU oracle -- bit-exact.
+
+Sizes span several block tiles and merge passes with ragged tails; every key
+type, both directions, keys-only and stable pairs, every workload
+distribution and the paper's data sets; edge cases (empty, single, all-equal,
+extreme key values that coincide with the network's pads, NaN / signed-zero
+floats, aliasing, misalignment, short workspace).
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from tests.gpu_util import bits, from_dev, kt_of, to_dev
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def bcf():
+    import paper_1306_5076_gb300 as m
+    from paper_1306_5076_gb300 import build
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    m._native.load()
+    return m
+
+
+def gpu_sort(bcf, keys, vals=None, descending=False, inplace=False):
+    kd = to_dev(keys)
+    kt = kt_of(keys)
+    if vals is None:
+        ko = kd if inplace else torch.empty_like(kd)
+        bcf.bcf_sort_keys(ko, kd, descending=descending, kt=kt)
+        torch.cuda.synchronize()
+        return from_dev(ko, keys.dtype), None
+    vd = to_dev(vals)
+    ko = kd if inplace else torch.empty_like(kd)
+    vo = vd if inplace else torch.empty_like(vd)
+    bcf.bcf_sort_pairs(ko, vo, kd, vd, descending=descending, kt=kt)
+    torch.cuda.synchronize()
+    return from_dev(ko, keys.dtype), from_dev(vo, np.uint32)
+
+
+def assert_same(got_k, got_v, exp_k, exp_v):
+    gk, ek = bits(got_k), bits(exp_k)
+    if not np.array_equal(gk, ek):
+        bad = np.flatnonzero(gk != ek)
+        raise AssertionError(f"keys differ at {bad.size} positions, first {bad[:8]}: "
+                             f"got {gk[bad[:4]]} expected {ek[bad[:4]]}")
+    if exp_v is not None:
+        if not np.array_equal(got_v, exp_v):
+            bad = np.flatnonzero(got_v != exp_v)
+            raise AssertionError(f"values differ at {bad.size} positions, first {bad[:8]}")
+
+
+SIZES = [0, 1, 2, 31, 1000, 4095, 4096, 4097, 8191, 8192, 8193, 3 * 8192 + 17, 65536,
+         (1 << 17) + 123, (1 << 20) + 5]
+
+
+@pytest.mark.parametrize("dtype", ["u32", "u64", "f32"])
+@pytest.mark.parametrize("n", SIZES)
+def test_uniform_keys_and_pairs_all_sizes(bcf, dtype, n):
+    keys = workloads.keys("uniform", dtype, n, seed=100 + n)
+    vals = workloads.row_index(n)
+    for desc in (False, True):
+        ek, _ = oracle.sort(keys, descending=desc)
+        gk, _ = gpu_sort(bcf, keys, descending=desc)
+        assert_same(gk, None, ek, None)
+        ek, ev = oracle.sort(keys, vals, descending=desc)
+        gk, gv = gpu_sort(bcf, keys, vals, descending=desc)
+        assert_same(gk, gv, ek, ev)
+
+
+@pytest.mark.parametrize("dtype", ["u32", "u64", "f32"])
+@pytest.mark.parametrize("dist", workloads.DISTRIBUTIONS)
+def test_workload_distributions(bcf, dtype, dist):
+    n = (1 << 18) + 4321
+    keys = workloads.keys(dist, dtype, n)
+    vals = workloads.row_index(n)
+    for desc in (False, True):
+        ek, ev = oracle.sort(keys, vals, descending=desc, nthreads=8)
+        gk, gv = gpu_sort(bcf, keys, vals, descending=desc)
+        assert_same(gk, gv, ek, ev)
+        gk, _ = gpu_sort(bcf, keys, descending=desc)
+        assert_same(gk, None, ek, None)
+
+
+@pytest.mark.parametrize("name", workloads.PAPER_SETS)
+def test_paper_data_sets(bcf, name):
+    n = (1 << 19) + 99
+    keys = workloads.paper_keys(name, n)
+    vals = workloads.row_index(n)
+    ek, ev = oracle.sort(keys, vals, nthreads=8)
+    gk, gv = gpu_sort(bcf, keys, vals)
+    assert_same(gk, gv, ek, ev)
+
+
+def test_extreme_keys_tie_with_pads(bcf):
+    """Real keys equal to the network's +inf/-inf pads must sort by position."""
+    n = 3 * 8192 + 77
+    r = workloads.rng(5)
+    for dtype, lo, hi in (("u32", 0, 0xFFFFFFFF), ("u64", 0, 2**64 - 1)):
+        keys = np.where(r.random(n) < 0.5, lo, hi).astype(workloads.DTYPES[dtype])
+        vals = workloads.row_index(n)
+        for desc in (False, True):
+            ek, ev = oracle.sort(keys, vals, descending=desc)
+            gk, gv = gpu_sort(bcf, keys, vals, descending=desc)
+            assert_same(gk, gv, ek, ev)
+    # f32 patterns that map to the extremes of the order: -NaN max and +NaN max
+    keys = np.where(r.random(n) < 0.5, 0xFFFFFFFF, 0x7FFFFFFF).astype(np.uint32).view(np.float32)
+    vals = workloads.row_index(n)
+    for desc in (False, True):
+        ek, ev = oracle.sort(keys, vals, descending=desc)
+        gk, gv = gpu_sort(bcf, keys, vals, descending=desc)
+        assert_same(gk, gv, ek, ev)
+
+
+def test_f32_golden_total_order(bcf):
+    from tests.test_oracle_pins import read_golden
+
+    g = read_golden()
+    r = workloads.rng(9)
+    keys = g[r.integers(0, g.size, size=50_000)].view(np.float32)
+    vals = workloads.row_index(keys.size)
+    ek, ev = oracle.sort(keys, vals)
+    gk, gv = gpu_sort(bcf, keys, vals)
+    assert_same(gk, gv, ek, ev)
+    # every golden pattern appears in golden order
+    seen = np.unique(gk.view(np.uint32), return_index=True)
+    order = np.argsort(seen[1])
+    assert np.array_equal(seen[0][order], g)
+
+
+def test_all_equal_and_sorted_inputs(bcf):
+    n = 100_003
+    for keys in (np.full(n, 7, np.uint32), np.arange(n, dtype=np.uint32),
+                 np.arange(n, 0, -1, dtype=np.uint32)):
+        vals = workloads.row_index(n)
+        ek, ev = oracle.sort(keys, vals)
+        gk, gv = gpu_sort(bcf, keys, vals)
+        assert_same(gk, gv, ek, ev)
+
+
+@pytest.mark.parametrize("n", [5000, 8192 * 5 + 3])
+def test_in_place(bcf, n):
+    keys = workloads.keys("gaussian", "u32", n, seed=3)
+    vals = workloads.row_index(n)
+    ek, ev = oracle.sort(keys, vals)
+    gk, gv = gpu_sort(bcf, keys, vals, inplace=True)
+    assert_same(gk, gv, ek, ev)
+    ek, _ = oracle.sort(keys, descending=True)
+    gk, _ = gpu_sort(bcf, keys, descending=True, inplace=True)
+    assert_same(gk, None, ek, None)
+
+
+def test_deterministic_repeat(bcf):
+    keys = workloads.keys("distinct16", "u32", 300_001, seed=4)
+    vals = workloads.row_index(keys.size)
+    first = gpu_sort(bcf, keys, vals)
+    for _ in range(5):
+        again = gpu_sort(bcf, keys, vals)
+        assert np.array_equal(first[0], again[0]) and np.array_equal(first[1], again[1])
+
+
+def test_errors_on_device_buffers(bcf):
+    n = 1 << 16
+    kd = torch.zeros(n + 4, dtype=torch.int32, device="cuda")
+    ko = torch.zeros(n + 4, dtype=torch.int32, device="cuda")
+    with pytest.raises(bcf.BcfError) as ei:  # misaligned input
+        bcf.bcf_sort_keys(ko[:n], kd[1:n + 1], kt=0)
+    assert ei.value.status == 1
+    small = torch.zeros(64, dtype=torch.uint8, device="cuda")
+    with pytest.raises(bcf.BcfError) as ei:
+        bcf.bcf_sort_keys(ko[:n], kd[:n], kt=0, ws=small)
+    assert ei.value.status == 2
+    assert bcf.bcf_last_device_error() == 0
+
+
+def test_full_size_bench_config_against_oracle(bcf):
+    """The benchmark's workload (2^28 uniform u32 keys) in its launch
+    configuration, compared with the oracle on every element."""
+    n = 1 << 28
+    keys = workloads.keys("uniform", "u32", n)
+    kd = to_dev(keys)
+    ko = torch.empty_like(kd)
+    bcf.bcf_sort_keys(ko, kd, kt=0)
+    torch.cuda.synchronize()
+    got = from_dev(ko, np.uint32)
+    del kd, ko
+    import os
+
+    exp, _ = oracle.sort(keys, nthreads=os.cpu_count() or 8)
+    assert np.array_equal(got, exp)
