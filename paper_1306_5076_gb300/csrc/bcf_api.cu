@@ -48,10 +48,8 @@ struct Tuning {
 // sweeps.
 Tuning default_tuning(int kb, bool pairs) {
   Tuning t;
-  if (kb == 4 && !pairs) t = {1, 0};       // T = 8192 (16 x 512), Tm = 4096 (16 x 256)
-  else if (kb == 4) t = {0, 0};            // T = 4096, Tm = 4096
-  else if (!pairs) t = {0, 0};             // u64 keys
-  else t = {0, 0};                         // u64 pairs
+  if (kb == 4 && !pairs) t = {1, 0};  // T = 8192 (32 x 256), Tm = 4096 (16 x 256)
+  else t = {0, 0};                    // pairs, 64-bit keys: T = Tm = 4096 (16 x 256)
   static const char* eb = std::getenv("BCF_BLOCK_CFG");
   static const char* em = std::getenv("BCF_MERGE_CFG");
   if (eb) {
@@ -87,7 +85,7 @@ Plan make_plan(uint64_t n, int kb, bool pairs) {
 }
 
 // smallest merge tile over all configurations: bounds the split arrays
-constexpr uint64_t kMinMergeTile = 4096;
+constexpr uint64_t kMinMergeTile = 2048;
 
 struct WsLayout {
   size_t splits, keys, vals, total;

@@ -7,16 +7,18 @@
 // diagonals so no transpose conflicts.  On sm_103a the same principles are
 // kept -- data-oblivious register networks, one thread per row/column of a
 // skewed shared-memory matrix -- but ShearSort's O(log w) row/column rounds
-// are replaced by a bitonic sort whose cross-thread stages are warp shuffles
-// (no shared memory at all) or a single padded transpose, which needs far
-// fewer compare-exchanges per key for tiles of 4K-16K keys.
+// are replaced by a bitonic sort whose cross-thread stages all go through
+// conflict-free padded transposes, which needs far fewer compare-exchanges
+// per key for tiles of 4K-16K keys.
 //
 //   1. coalesced 128-bit loads straight into registers (each thread takes V
 //      consecutive keys from every NT*V-key stripe); keys are mapped to
 //      unsigned order (f32 totalOrder, descending);
 //   2. Batcher odd-even merge sort of the thread's E registers;
-//   3. bitonic merge levels j = r+1 .. t in BLK layout, using the STR layout
-//      (one padded transpose each way) for the levels' top bits;
+//   3. bitonic merge levels j = r+1 .. t: every stage is an ascending
+//      register compare-exchange in one of three layouts (BLK / MID / STR),
+//      joined by conflict-free padded transposes; the bitonic "flip" of each
+//      level is folded into the transpose's read addresses;
 //   4. 128-bit stores of the thread's E consecutive outputs.
 // Pairs carry a tie-break index (input position in the tile) so that the
 // result is the stable order.
@@ -27,62 +29,6 @@
 
 namespace bcf {
 
-// Full bitonic sort of the CTA's E*NT elements.  On entry each thread's E
-// registers hold arbitrary elements; on exit the tile is ascending in BLK
-// layout (thread tid holds sorted positions tid*E .. tid*E + E - 1).
-template <int NT, typename K, bool PAIRS, int E>
-__device__ __forceinline__ void block_bitonic_sort(Frag<K, PAIRS, E>& f, uint32_t* sm,
-                                                   uint32_t plane) {
-  constexpr int r = ilog2(E), t = ilog2(E * NT);
-  static_assert(t <= 2 * r + 5, "tile too large for two layouts");
-  static_assert(E <= 32, "direction masks hold 32 registers");
-  const uint32_t tid = threadIdx.x;
-  // level r: each thread's run of E; run direction = bit r of k = bit 0 of tid
-  thread_sort(f, (tid & 1u) != 0);
-  // The level loop stays rolled (code size); register indices inside it are
-  // compile-time constants, guarded by uniform runtime conditions.
-#pragma unroll 1
-  for (int j = r + 1; j <= t; ++j) {
-    // merge sorted blocks of 2^(j-1) into blocks of 2^j; a block is ascending
-    // iff bit j of its index k is 0 (always ascending at the last level)
-    const bool desc_blk = (j < t) && (((tid >> (j - r)) & 1u) != 0);
-    int top_lane_bit = j - 1;
-    if (j - 1 >= r + 5) {
-      // bits j-1 .. t-r are warp bits in BLK but register bits in STR
-      blk_to_str<NT>(f, sm, plane);
-      // direction of register e in STR: bit j of k = e*NT + tid
-      uint32_t dmask = 0;
-      if (j < t) {
-        if (j >= t - r) {
-          constexpr uint32_t kBitPattern[5] = {0xAAAAAAAAu, 0xCCCCCCCCu, 0xF0F0F0F0u,
-                                               0xFF00FF00u, 0xFFFF0000u};
-          dmask = kBitPattern[j - (t - r)];
-        } else {
-          dmask = ((tid >> j) & 1u) ? 0xFFFFFFFFu : 0u;
-        }
-      }
-      const int rb_top = j - 1 - (t - r);
-#pragma unroll
-      for (int rb = r - 1; rb >= 0; --rb) {
-        if (rb > rb_top) continue;
-#pragma unroll
-        for (int e = 0; e < E; ++e)
-          if (!(e & (1 << rb))) ce(f, e, e | (1 << rb), ((dmask >> e) & 1u) != 0);
-      }
-      str_to_blk<NT>(f, sm, plane);
-      top_lane_bit = t - r - 1;
-    }
-#pragma unroll 1
-    for (int b = top_lane_bit; b >= r; --b) shfl_stage(f, 1 << (b - r), desc_blk);
-#pragma unroll
-    for (int rb = r - 1; rb >= 0; --rb) {
-#pragma unroll
-      for (int e = 0; e < E; ++e)
-        if (!(e & (1 << rb))) ce(f, e, e | (1 << rb), desc_blk);
-    }
-  }
-}
-
 template <typename K, int V> struct VecOf;
 template <> struct VecOf<uint32_t, 4> { using T = uint4; };
 template <> struct VecOf<uint64_t, 2> { using T = ulonglong2; };
@@ -90,14 +36,15 @@ template <int V> struct ValVec;
 template <> struct ValVec<4> { using T = uint4; };
 template <> struct ValVec<2> { using T = uint2; };
 
-template <typename K, bool PAIRS, int E, int NT>
+// MAP: the key map is applied on load / undone on store (runtime mode); when
+// false the kernel carries no map code at all (intermediate passes).
+template <typename K, bool PAIRS, int E, int NT, bool MAP>
 __global__ void __launch_bounds__(NT) block_sort_kernel(const BlockSortArgs a) {
   constexpr int T = E * NT;
   constexpr int V = 16 / sizeof(K);  // keys per 16-byte vector
   using KV = typename VecOf<K, V>::T;
   using VV = typename ValVec<V>::T;
   extern __shared__ __align__(16) uint32_t sm[];
-  constexpr uint32_t plane = padded_words(T);
 
   Frag<K, PAIRS, E> f;
   const uint32_t tid = threadIdx.x;
@@ -106,6 +53,8 @@ __global__ void __launch_bounds__(NT) block_sort_kernel(const BlockSortArgs a) {
   const uint32_t cnt = rem < static_cast<uint64_t>(T) ? static_cast<uint32_t>(rem) : T;
   const K* kin = static_cast<const K*>(a.kin) + base;
   const uint32_t* vin = PAIRS ? a.vin + base : nullptr;
+  const int mode_in = MAP ? a.mode_in : 0;
+  const int mode_out = MAP ? a.mode_out : 0;
 
   if (cnt == T) {
 #pragma unroll
@@ -114,7 +63,7 @@ __global__ void __launch_bounds__(NT) block_sort_kernel(const BlockSortArgs a) {
       const KV kv = *reinterpret_cast<const KV*>(kin + pos);
       const K* kp = reinterpret_cast<const K*>(&kv);
 #pragma unroll
-      for (int c = 0; c < V; ++c) f.k[q * V + c] = map_key(kp[c], a.mode_in);
+      for (int c = 0; c < V; ++c) f.k[q * V + c] = MAP ? map_key(kp[c], mode_in) : kp[c];
       if constexpr (PAIRS) {
         const VV vv = *reinterpret_cast<const VV*>(vin + pos);
         const uint32_t* vp = reinterpret_cast<const uint32_t*>(&vv);
@@ -132,7 +81,9 @@ __global__ void __launch_bounds__(NT) block_sort_kernel(const BlockSortArgs a) {
     for (int e = 0; e < E; ++e) {
       const uint32_t pos = (e / V) * V * NT + V * tid + (e % V);
       const bool real = pos < cnt;
-      f.k[e] = real ? map_key(kin[pos], a.mode_in) : KeyLimits<K>::kMax;
+      K x = KeyLimits<K>::kMax;
+      if (real) x = MAP ? map_key(kin[pos], mode_in) : kin[pos];
+      f.k[e] = x;
       if constexpr (PAIRS) {
         f.v[e] = real ? vin[pos] : 0u;
         f.ix[e] = pos;
@@ -140,7 +91,7 @@ __global__ void __launch_bounds__(NT) block_sort_kernel(const BlockSortArgs a) {
     }
   }
 
-  block_bitonic_sort<NT>(f, sm, plane);
+  block_sort_tile<NT>(f, sm);
 
   K* kout = static_cast<K*>(a.kout) + base;
   uint32_t* vout = PAIRS ? a.vout + base : nullptr;
@@ -151,7 +102,8 @@ __global__ void __launch_bounds__(NT) block_sort_kernel(const BlockSortArgs a) {
       KV kv;
       K* kp = reinterpret_cast<K*>(&kv);
 #pragma unroll
-      for (int c = 0; c < V; ++c) kp[c] = unmap_key(f.k[q * V + c], a.mode_out);
+      for (int c = 0; c < V; ++c)
+        kp[c] = MAP ? unmap_key(f.k[q * V + c], mode_out) : f.k[q * V + c];
       *reinterpret_cast<KV*>(kout + p0 + q * V) = kv;
     }
     if constexpr (PAIRS) {
@@ -164,7 +116,7 @@ __global__ void __launch_bounds__(NT) block_sort_kernel(const BlockSortArgs a) {
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       if (p0 + e < cnt) {
-        kout[p0 + e] = unmap_key(f.k[e], a.mode_out);
+        kout[p0 + e] = MAP ? unmap_key(f.k[e], mode_out) : f.k[e];
         if constexpr (PAIRS) vout[p0 + e] = f.v[e];
       }
     }
@@ -178,34 +130,39 @@ static cudaError_t launch_bs(const BlockSortArgs& a, cudaStream_t s) {
   constexpr int T = E * NT;
   constexpr int W = Frag<K, PAIRS, E>::W;
   const size_t smem = static_cast<size_t>(W) * padded_words(T) * sizeof(uint32_t);
-  auto kern = block_sort_kernel<K, PAIRS, E, NT>;
+  const uint64_t tiles = (a.n + T - 1) / T;
+  if (tiles == 0) return cudaSuccess;
+  const bool map = (a.mode_in | a.mode_out) != 0;
+  auto kern = map ? block_sort_kernel<K, PAIRS, E, NT, true>
+                  : block_sort_kernel<K, PAIRS, E, NT, false>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
   if (err != cudaSuccess) return err;
-  const uint64_t tiles = (a.n + T - 1) / T;
-  if (tiles == 0) return cudaSuccess;
   kern<<<static_cast<unsigned>(tiles), NT, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-// Register budget: pairs with E = 32 would need ~100 data registers per
-// thread, so only E = 16 is built for pairs.
+// Register budget: pairs carry three words per element, so only E = 16 is
+// built for them; 64-bit keys-only also use E = 16.
 bool block_cfg_supported(int key_bytes, bool pairs, int cfg) {
   if (cfg < 0 || cfg >= kNumBlockCfgs) return false;
   if (key_bytes != 4 && key_bytes != 8) return false;
-  return !(pairs && kBlockCfgs[cfg].E > 16);
+  if (pairs || key_bytes == 8) return kBlockCfgs[cfg].E == 16;
+  return true;
 }
 
 template <typename K, bool PAIRS>
 static cudaError_t dispatch_bs(int cfg, const BlockSortArgs& a, cudaStream_t s) {
   switch (cfg) {
     case 0: return launch_bs<K, PAIRS, 16, 256>(a, s);
-    case 1: return launch_bs<K, PAIRS, 16, 512>(a, s);
+    case 1:
+      if constexpr (!PAIRS && sizeof(K) == 4) return launch_bs<K, PAIRS, 32, 256>(a, s);
+      break;
     case 2:
-      if constexpr (!PAIRS) return launch_bs<K, PAIRS, 32, 256>(a, s);
+      if constexpr (!PAIRS && sizeof(K) == 4) return launch_bs<K, PAIRS, 32, 512>(a, s);
       break;
     case 3:
-      if constexpr (!PAIRS) return launch_bs<K, PAIRS, 32, 512>(a, s);
+      if constexpr (!PAIRS && sizeof(K) == 4) return launch_bs<K, PAIRS, 32, 128>(a, s);
       break;
     default: break;
   }

@@ -216,39 +216,6 @@ __device__ __forceinline__ void ce(Frag<K, PAIRS, E>& f, int a, int b, bool desc
   }
 }
 
-// In-register stage on register bit rb (partner e ^ 2^rb), one direction.
-template <int RB, typename K, bool PAIRS, int E>
-__device__ __forceinline__ void reg_stage(Frag<K, PAIRS, E>& f, bool desc) {
-#pragma unroll
-  for (int e = 0; e < E; ++e)
-    if (!(e & (1 << RB))) ce(f, e, e | (1 << RB), desc);
-}
-
-// Warp-shuffle stage: partner lane = lane ^ m.  The lower lane of a pair keeps
-// the smaller element when ascending (desc == false).
-template <typename K, bool PAIRS, int E>
-__device__ __forceinline__ void shfl_stage(Frag<K, PAIRS, E>& f, int m, bool desc) {
-  const bool keep_max = (((threadIdx.x & 31) & m) != 0) != desc;
-#pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const K pk = __shfl_xor_sync(0xFFFFFFFFu, f.k[e], m);
-    if constexpr (!PAIRS) {
-      const K mine = f.k[e];
-      const K lo = mine < pk ? mine : pk, hi = mine < pk ? pk : mine;
-      f.k[e] = keep_max ? hi : lo;
-    } else {
-      const uint32_t pi = __shfl_xor_sync(0xFFFFFFFFu, f.ix[e], m);
-      const uint32_t pv = __shfl_xor_sync(0xFFFFFFFFu, f.v[e], m);
-      // (key, index) pairs are unique, so "partner after mine" decides both sides
-      const bool p_after = after(pk, pi, f.k[e], f.ix[e]);
-      const bool take = keep_max ? p_after : !p_after;
-      f.k[e] = take ? pk : f.k[e];
-      f.ix[e] = take ? pi : f.ix[e];
-      f.v[e] = take ? pv : f.v[e];
-    }
-  }
-}
-
 // Batcher's odd-even merge sort network on N inputs (Knuth vol. 3, Sec.
 // 5.3.4, Algorithm M), listed as comparator pairs at compile time.
 template <int N>
@@ -277,53 +244,176 @@ __device__ __forceinline__ void thread_sort(Frag<K, PAIRS, E>& f, bool desc) {
   for (int c = 0; c < net.n; ++c) ce(f, net.a[c], net.b[c], desc);
 }
 
-// Layout switches through padded shared memory (planes of `plane` words).
-template <int NT, typename K, bool PAIRS, int E>
-__device__ __forceinline__ void blk_to_str(Frag<K, PAIRS, E>& f, uint32_t* sm, uint32_t plane) {
+// ---------------------------------------------------------------- layouts
+// Three register layouts of a CTA tile X[0, 2^t) with E = 2^r registers per
+// thread, NT = 2^(t-r) threads, lane = tid & 31, warp = tid >> 5:
+//   BLK  register window k bits [0, r)     k = tid*E + e
+//   MID  register window k bits [r, 2r)    r = 5: k = warp<<10 | e<<5 | lane
+//                                          r = 4: k = lane[0:4] | e<<4 |
+//                                                 warp[0]<<8 | lane[4]<<9 |
+//                                                 warp[1:]<<10
+//   STR  register window k bits [t-r, t)   k = e*NT + tid
+// For t <= 3r the windows cover every bit, so every stage of a bitonic
+// network is an in-register compare-exchange in one of them.  Layouts change
+// through shared memory padded with one word per 32 (word k lives at
+// k + (k >> 5)).  A warp's 32 accesses then always hit 32 distinct banks:
+//   STR, MID(r=5): lanes are k bits [0,5)        -> consecutive words
+//   MID(r=4)     : lanes are k bits {0..3, 9}    -> banks l[0:4] + 16*l[4]
+//   BLK          : lanes are k bits [r, r+5)     -> banks (l*E + l*E/32) mod 32
+// which is the paper's row-per-thread / skewed-matrix principle (Sec. 2.1,
+// Sec. 3.3 "implicit matrix transposition").  Every address is a per-thread
+// base plus a compile-time offset, so layout changes cost no arithmetic.
+enum { kBLK = 0, kMID = 1, kSTR = 2 };
+
+template <int E, int NT>
+struct Geo {
+  static constexpr int r = ilog2(E);
+  static constexpr int t = ilog2(E * NT);
+  static constexpr uint32_t T = E * NT;
+  static constexpr uint32_t kPlane = padded_words(T);
+  static_assert(r == 4 || r == 5, "E must be 16 or 32");
+  static_assert(t >= 10 && t <= 3 * r, "tile size outside what three layouts cover");
+
+  template <int L>
+  static constexpr int win() { return L == kBLK ? 0 : (L == kMID ? r : t - r); }
+
+  // per-thread base of layout L; MIRROR: the base of the element whose index
+  // has every bit below the register window flipped (lanes / threads mirrored)
+  template <int L, bool MIRROR>
+  __device__ static __forceinline__ uint32_t base(uint32_t tid) {
+    if constexpr (L == kBLK) {
+      static_assert(!MIRROR, "BLK is never read mirrored");
+      const uint32_t k0 = tid * E;
+      return k0 + (k0 >> 5);
+    } else if constexpr (L == kSTR) {
+      const uint32_t tt = MIRROR ? (tid ^ (NT - 1)) : tid;
+      return tt + (tt >> 5);
+    } else {
+      const uint32_t w = tid >> 5, l = tid & 31;
+      if constexpr (r == 5) {
+        return w * 1056u + (MIRROR ? (l ^ 31u) : l);
+      } else {
+        const uint32_t lo = MIRROR ? ((l & 15u) ^ 15u) : (l & 15u);
+        return lo + 264u * (w & 1u) + 528u * (l >> 4) + 1056u * (w >> 1);
+      }
+    }
+  }
+  template <int L>
+  __host__ __device__ static constexpr uint32_t off(int e) {
+    return L == kBLK ? static_cast<uint32_t>(e)
+         : L == kSTR ? static_cast<uint32_t>(e) * (NT + NT / 32)
+         : (r == 5 ? 33u * e : 16u * e + (e >> 1));
+  }
+};
+
+// Layout change FROM -> TO through shared memory.  FLIPJ > 0 reverses the
+// upper half of every 2^FLIPJ block while reading (element k of an upper half
+// is fetched from k ^ (2^(FLIPJ-1) - 1)), turning two ascending halves into
+// one bitonic sequence -- so every compare-exchange of the sort is ascending.
+// Requires bit FLIPJ-1 to lie in TO's register window.
+template <int FROM, int TO, int FLIPJ, int NT, typename K, bool PAIRS, int E>
+__device__ __forceinline__ void relayout(Frag<K, PAIRS, E>& f, uint32_t* sm) {
+  using G = Geo<E, NT>;
   const uint32_t tid = threadIdx.x;
   __syncthreads();
+  {
+    const uint32_t b = G::template base<FROM, false>(tid);
 #pragma unroll
-  for (int e = 0; e < E; ++e) f.put(sm, plane, e, pad32(tid * E + e));
+    for (int e = 0; e < E; ++e) f.put(sm, G::kPlane, e, b + G::template off<FROM>(e));
+  }
   __syncthreads();
+  const uint32_t b = G::template base<TO, false>(tid);
+  if constexpr (FLIPJ == 0) {
 #pragma unroll
-  for (int e = 0; e < E; ++e) f.get(sm, plane, e, pad32(e * NT + tid));
-}
-template <int NT, typename K, bool PAIRS, int E>
-__device__ __forceinline__ void str_to_blk(Frag<K, PAIRS, E>& f, uint32_t* sm, uint32_t plane) {
-  const uint32_t tid = threadIdx.x;
-  __syncthreads();
+    for (int e = 0; e < E; ++e) f.get(sm, G::kPlane, e, b + G::template off<TO>(e));
+  } else {
+    constexpr int q = FLIPJ - 1 - G::template win<TO>();  // register bit of k bit FLIPJ-1
+    static_assert(q >= 0 && q < G::r, "flip bit outside the target window");
+    const uint32_t bm = G::template base<TO, true>(tid);
 #pragma unroll
-  for (int e = 0; e < E; ++e) f.put(sm, plane, e, pad32(e * NT + tid));
-  __syncthreads();
-#pragma unroll
-  for (int e = 0; e < E; ++e) f.get(sm, plane, e, pad32(tid * E + e));
+    for (int e = 0; e < E; ++e) {
+      if (e & (1 << q))
+        f.get(sm, G::kPlane, e, bm + G::template off<TO>(e ^ ((1 << q) - 1)));
+      else
+        f.get(sm, G::kPlane, e, b + G::template off<TO>(e));
+    }
+  }
 }
 
-// Bitonic MERGE of a bitonic sequence of length E*NT held in STR layout,
-// ascending; ends in BLK layout.  Stages run on bits t-1 .. 0: STR register
-// bits first, then one transpose, then BLK lane bits by shuffle and BLK
-// register bits.
+// Ascending half-cleaner stages on k bits HI down to LO, all inside layout
+// L's register window.
+template <int L, int HI, int LO, int NT, typename K, bool PAIRS, int E>
+__device__ __forceinline__ void stages(Frag<K, PAIRS, E>& f) {
+  using G = Geo<E, NT>;
+#pragma unroll
+  for (int b = HI; b >= LO; --b) {
+    const int q = b - G::template win<L>();
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+      if (!(e & (1 << q))) ce(f, e, e | (1 << q), false);
+  }
+}
+
+// Bitonic merge of the bitonic sequence of length E*NT held in STR layout;
+// ascending result in BLK layout.  Stages on bits t-1 .. 0 in STR, MID, BLK.
 template <int NT, typename K, bool PAIRS, int E>
-__device__ __forceinline__ void bitonic_merge_str(Frag<K, PAIRS, E>& f, uint32_t* sm,
-                                                  uint32_t plane) {
-  constexpr int r = ilog2(E), t = ilog2(E * NT);
-  static_assert(t <= 2 * r + 5, "tile too large for two layouts");
-#pragma unroll
-  for (int rb = r - 1; rb >= 0; --rb) {
-    // STR register bit rb is k bit (t - r + rb)
-#pragma unroll
-    for (int e = 0; e < E; ++e)
-      if (!(e & (1 << rb))) ce(f, e, e | (1 << rb), false);
+__device__ __forceinline__ void bitonic_merge_str(Frag<K, PAIRS, E>& f, uint32_t* sm) {
+  using G = Geo<E, NT>;
+  constexpr int r = G::r, t = G::t;
+  stages<kSTR, t - 1, t - r, NT>(f);
+  if constexpr (t - r - 1 >= r) {
+    relayout<kSTR, kMID, 0, NT>(f, sm);
+    stages<kMID, t - r - 1, r, NT>(f);
+    relayout<kMID, kBLK, 0, NT>(f, sm);
+  } else {
+    relayout<kSTR, kBLK, 0, NT>(f, sm);
   }
-  str_to_blk<NT>(f, sm, plane);
-#pragma unroll
-  for (int b = t - r - 1; b >= r; --b) shfl_stage(f, 1 << (b - r), false);
-#pragma unroll
-  for (int rb = r - 1; rb >= 0; --rb) {
-#pragma unroll
-    for (int e = 0; e < E; ++e)
-      if (!(e & (1 << rb))) ce(f, e, e | (1 << rb), false);
+  stages<kBLK, r - 1, 0, NT>(f);
+}
+
+// One level J of the bitonic sort (r < J <= t): the tile's blocks of 2^(J-1)
+// are ascending; merge pairs of them into ascending blocks of 2^J.  Enters and
+// leaves in BLK layout.
+template <int J, int NT, typename K, bool PAIRS, int E>
+__device__ __forceinline__ void sort_level(Frag<K, PAIRS, E>& f, uint32_t* sm) {
+  using G = Geo<E, NT>;
+  constexpr int r = G::r, t = G::t, top = J - 1;
+  if constexpr (top >= t - r) {
+    relayout<kBLK, kSTR, J, NT>(f, sm);
+    stages<kSTR, top, t - r, NT>(f);
+    if constexpr (t - r - 1 >= r) {
+      relayout<kSTR, kMID, 0, NT>(f, sm);
+      stages<kMID, t - r - 1, r, NT>(f);
+      relayout<kMID, kBLK, 0, NT>(f, sm);
+    } else {
+      relayout<kSTR, kBLK, 0, NT>(f, sm);
+    }
+  } else {
+    relayout<kBLK, kMID, J, NT>(f, sm);
+    stages<kMID, top, r, NT>(f);
+    relayout<kMID, kBLK, 0, NT>(f, sm);
   }
+  stages<kBLK, r - 1, 0, NT>(f);
+}
+
+template <int J, int NT, typename K, bool PAIRS, int E, bool DONE = (J > ilog2(E * NT))>
+struct SortLevels {
+  __device__ static __forceinline__ void run(Frag<K, PAIRS, E>& f, uint32_t* sm) {
+    sort_level<J, NT>(f, sm);
+    SortLevels<J + 1, NT, K, PAIRS, E>::run(f, sm);
+  }
+};
+template <int J, int NT, typename K, bool PAIRS, int E>
+struct SortLevels<J, NT, K, PAIRS, E, true> {
+  __device__ static __forceinline__ void run(Frag<K, PAIRS, E>&, uint32_t*) {}
+};
+
+// Sort of the whole CTA tile: each thread's registers with Batcher's network
+// (levels 1..r), then levels r+1..t; ascending result in BLK layout.
+template <int NT, typename K, bool PAIRS, int E>
+__device__ __forceinline__ void block_sort_tile(Frag<K, PAIRS, E>& f, uint32_t* sm) {
+  thread_sort(f, false);
+  SortLevels<ilog2(E) + 1, NT, K, PAIRS, E>::run(f, sm);
 }
 
 }  // namespace bcf

@@ -57,8 +57,11 @@ struct TileCfg {
 };
 
 // Supported configurations (index into these tables).
-constexpr TileCfg kBlockCfgs[] = {{16, 256}, {16, 512}, {32, 256}, {32, 512}};
-constexpr TileCfg kMergeCfgs[] = {{16, 256}, {16, 512}, {32, 256}};
+// E is 16 or 32 and the tile E*NT lies in [2^10, E^3], the range the three
+// register layouts of bcf_device.cuh cover.  Block tiles {4096, 8192, 16384,
+// 4096}; merge tiles {4096, 4096, 8192, 2048}.
+constexpr TileCfg kBlockCfgs[] = {{16, 256}, {32, 256}, {32, 512}, {32, 128}};
+constexpr TileCfg kMergeCfgs[] = {{16, 256}, {32, 128}, {32, 256}, {16, 128}};
 constexpr int kNumBlockCfgs = sizeof(kBlockCfgs) / sizeof(kBlockCfgs[0]);
 constexpr int kNumMergeCfgs = sizeof(kMergeCfgs) / sizeof(kMergeCfgs[0]);
 

@@ -16,9 +16,9 @@
 //      registers in STR layout (a warp reads 32 consecutive shared words;
 //      rows that contain both A- and B-lanes issue two predicated loads so
 //      the two arrays never share a request -- no bank conflicts);
-//   3. runs the bitonic merge (log2 Tm stages: register stages, one padded
-//      transpose, shuffle stages) -- data-oblivious, so its shared-memory
-//      accesses are conflict-free like the paper's ShearSort merge;
+//   3. runs the bitonic merge: log2 Tm ascending register stages in the STR,
+//      MID and BLK layouts joined by two padded, conflict-free transposes --
+//      data-oblivious like the paper's ShearSort merge;
 //   4. writes its Tm outputs with 128-bit stores.
 // Stability: each element carries its rank in the stable merged order (A
 // before B on equal keys); the network compares (key, rank).
@@ -85,23 +85,6 @@ __device__ __forceinline__ Piece piece_irregular(const PairList& pl, uint64_t it
   return p;
 }
 
-// Merge path: number of A-keys among the first d outputs of the stable merge
-// (A first on equal keys), i.e. the smallest i with A[i] > B[d-1-i].
-template <typename K>
-__device__ __forceinline__ uint64_t merge_path(const K* A, uint64_t na, const K* B, uint64_t nb,
-                                               uint64_t d, int mode) {
-  uint64_t lo = d > nb ? d - nb : 0;
-  uint64_t hi = d < na ? d : na;
-  while (lo < hi) {
-    const uint64_t mid = (lo + hi) >> 1;
-    if (map_key(A[mid], mode) > map_key(B[d - 1 - mid], mode))
-      hi = mid;
-    else
-      lo = mid + 1;
-  }
-  return lo;
-}
-
 // Regular launches (one sort pass) carry no pair list.
 struct NoPairs {
   uint32_t unused;
@@ -125,31 +108,63 @@ __device__ __forceinline__ uint64_t first_item(const PairParam<IRREG>& pl) {
     return 0;
 }
 
-template <typename K, bool IRREG>
+// Merge path (exact splitter): the number of A-keys among the first d outputs
+// of the stable merge (A first on equal keys), i.e. the smallest i with
+// A[i] > B[d-1-i], or min(d, |A|) if there is none.  One warp per search:
+// each round the 32 lanes probe 32 evenly spaced candidates of the current
+// range and keep the sub-range between the last "false" and the first "true"
+// probe, shrinking it ~32x per round (about 6 dependent rounds of global
+// loads for runs of 2^27 keys instead of 27 for a binary search).
+template <typename K, bool IRREG, bool MAP>
 __global__ void __launch_bounds__(256) partition_kernel(const MergeArgs a, int Tm,
                                                         const __grid_constant__ PairParam<IRREG> pl) {
-  const uint64_t local = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (local >= a.nitems) return;
+  const uint64_t local = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t lane = threadIdx.x & 31u;
+  if (local >= a.nitems) return;  // whole warps exit together
   const uint64_t item = first_item<IRREG>(pl) + local;
   const Piece p = piece_of<IRREG>(a, pl, item, Tm);
   const K* A = static_cast<const K*>(a.kin) + p.src;
-  a.splits[item] = merge_path(A, p.na_tot, A + p.na_tot, p.nb_tot, p.d0, a.mode_in);
+  const K* B = A + p.na_tot;
+  const uint64_t d = p.d0;
+  uint64_t lo = d > p.nb_tot ? d - p.nb_tot : 0;
+  uint64_t hi = d < p.na_tot ? d : p.na_tot;
+  while (lo < hi) {
+    const uint64_t span = hi - lo;
+    const uint64_t pos = lo + (span * lane) / 32;  // lo <= pos < hi, so A[pos], B[d-1-pos] exist
+    K x = __ldg(A + pos), y = __ldg(B + (d - 1 - pos));
+    if constexpr (MAP) {
+      x = map_key(x, a.mode_in);
+      y = map_key(y, a.mode_in);
+    }
+    const uint32_t m = __ballot_sync(0xFFFFFFFFu, x > y);
+    if (m == 0) {
+      lo = lo + (span * 31) / 32 + 1;  // every probe "false": beyond the last one
+    } else {
+      const int fl = __ffs(m) - 1;     // first "true" probe
+      const uint64_t pf = lo + (span * fl) / 32;
+      if (fl > 0) lo = lo + (span * (fl - 1)) / 32 + 1;
+      hi = pf;
+    }
+  }
+  if (lane == 0) a.splits[item] = lo;
 }
 
 // Stage elements [g0, g1) of `src` (absolute indices; src 16-byte aligned)
 // into shared memory at `dst` (16-byte aligned) so that element x lands at
-// dst[x - align_down(g0)].  The 16-byte-aligned body goes by bulk copy issued
-// by the calling thread; returns its byte count (0 if none).  The ragged tail
-// is left to stage_tail().
+// dst[x - align_down(g0)].  The 16-byte-aligned body goes by one bulk copy
+// issued by the calling thread; the ragged tail is left to stage_tail().
 template <typename T>
-__device__ __forceinline__ uint32_t stage_bulk(T* dst, const T* src, uint64_t g0, uint64_t g1,
-                                               uint64_t* bar) {
+__device__ __forceinline__ uint32_t body_bytes(uint64_t g0, uint64_t g1) {
   constexpr uint64_t V = 16 / sizeof(T);
   const uint64_t a0 = g0 & ~(V - 1), a1 = g1 & ~(V - 1);
-  if (g1 <= g0 || a1 <= a0) return 0;
-  const uint32_t bytes = static_cast<uint32_t>((a1 - a0) * sizeof(T));
-  bulk_g2s(dst, src + a0, bytes, bar);
-  return bytes;
+  return (g1 > g0 && a1 > a0) ? static_cast<uint32_t>((a1 - a0) * sizeof(T)) : 0u;
+}
+template <typename T>
+__device__ __forceinline__ void stage_bulk(T* dst, const T* src, uint64_t g0, uint64_t g1,
+                                           uint64_t* bar) {
+  constexpr uint64_t V = 16 / sizeof(T);
+  const uint32_t bytes = body_bytes<T>(g0, g1);
+  if (bytes) bulk_g2s(dst, src + (g0 & ~(V - 1)), bytes, bar);
 }
 template <typename T>
 __device__ __forceinline__ void stage_tail(T* dst, const T* src, uint64_t g0, uint64_t g1,
@@ -170,19 +185,40 @@ struct MergeSmem {
   static constexpr uint32_t kKeyBytes = ((Tm + 3 * VK) * sizeof(K) + 15) / 16 * 16;
   static constexpr uint32_t kValBytes = PAIRS ? ((Tm + 12) * 4 + 15) / 16 * 16 : 0;
   static constexpr uint32_t kStageBytes = kKeyBytes + kValBytes;
-  static constexpr uint32_t kPlane = padded_words(Tm);
-  static constexpr uint32_t kPlaneBytes = Frag<K, PAIRS, E>::W * kPlane * 4;
+  static constexpr uint32_t kPlaneBytes = Frag<K, PAIRS, E>::W * Geo<E, NT>::kPlane * 4;
   static constexpr uint32_t kBody = kStageBytes > kPlaneBytes ? kStageBytes : kPlaneBytes;
   static constexpr uint32_t kTotal = 16 + kBody;  // + mbarrier
 };
 
-template <typename K, bool PAIRS, int E, int NT, bool IRREG>
+// Element k of the bitonic sequence [-inf pads | A | +inf pads | reversed B]
+// read from the staged windows for a whole warp row (uniform fast paths) or
+// lane by lane at the boundaries.
+template <typename T>
+__device__ __forceinline__ T read_seq(const T* sa, const T* sb, uint32_t k, uint32_t row0,
+                                      uint32_t front, uint32_t endA, uint32_t begB,
+                                      uint32_t Tm1, T pad_lo, T pad_hi, bool& real) {
+  if (row0 >= front && row0 + 32 <= endA) {  // the warp's 32 lanes all read A
+    real = true;
+    return sa[k - front];
+  }
+  if (row0 >= begB) {  // all read B, reversed
+    real = true;
+    return sb[Tm1 - k];
+  }
+  const bool isA = k >= front && k < endA, isB = k >= begB;
+  real = isA || isB;
+  T v = lds_pred(sa + (k - front), isA, k < front ? pad_lo : pad_hi);
+  return lds_pred(sb + (Tm1 - k), isB, v);
+}
+
+template <typename K, bool PAIRS, int E, int NT, bool IRREG, bool MAP>
 __global__ void __launch_bounds__(NT) merge_kernel(const MergeArgs a,
                                                    const __grid_constant__ PairParam<IRREG> pl) {
   using S = MergeSmem<K, PAIRS, E, NT>;
   constexpr int Tm = S::Tm;
   constexpr uint64_t VK = S::VK;
   extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ int s_ok;
   uint64_t* bar = reinterpret_cast<uint64_t*>(smraw);
   unsigned char* body = smraw + 16;
   const uint32_t tid = threadIdx.x;
@@ -211,19 +247,9 @@ __global__ void __launch_bounds__(NT) merge_kernel(const MergeArgs a,
   if (tid == 0) {
     mbar_init(bar, 1);
     fence_mbar_init();
-  }
-  __syncthreads();
-  if (tid == 0) {
-    // the bulk copies' total byte count must be announced before any of them
-    // can complete, so sum first, then arm, then issue
-    constexpr uint64_t VV = 4;
-    auto body_bytes = [](uint64_t g0, uint64_t g1, uint64_t V, uint64_t sz) -> uint32_t {
-      const uint64_t a0 = g0 & ~(V - 1), a1 = g1 & ~(V - 1);
-      return (g1 > g0 && a1 > a0) ? static_cast<uint32_t>((a1 - a0) * sz) : 0u;
-    };
-    uint32_t total = body_bytes(ga0, ga1, VK, sizeof(K)) + body_bytes(gb0, gb1, VK, sizeof(K));
-    if constexpr (PAIRS)
-      total += body_bytes(ga0, ga1, VV, 4) + body_bytes(gb0, gb1, VV, 4);
+    // the total byte count is announced before any copy can complete
+    uint32_t total = body_bytes<K>(ga0, ga1) + body_bytes<K>(gb0, gb1);
+    if constexpr (PAIRS) total += body_bytes<uint32_t>(ga0, ga1) + body_bytes<uint32_t>(gb0, gb1);
     mbar_arrive_expect_tx(bar, total);
     stage_bulk(smA, kin, ga0, ga1, bar);
     stage_bulk(smB, kin, gb0, gb1, bar);
@@ -231,6 +257,10 @@ __global__ void __launch_bounds__(NT) merge_kernel(const MergeArgs a,
       stage_bulk(svA, a.vin, ga0, ga1, bar);
       stage_bulk(svB, a.vin, gb0, gb1, bar);
     }
+    // one thread waits (bounded); the barrier below releases the others
+    bool ok = mbar_wait_bounded(bar, 0, a.err, kErrTmaTimeout);
+    if (!ok) mbar_wait_bounded(bar, 0, nullptr, 0);  // let copies in flight land
+    s_ok = ok ? 1 : 0;
   } else if (tid >= 32 && tid < 64) {
     const uint32_t lane = tid - 32;
     // lanes 0-7: A keys, 8-15: B keys, 16-23: A values, 24-31: B values
@@ -239,12 +269,8 @@ __global__ void __launch_bounds__(NT) merge_kernel(const MergeArgs a,
     else if (PAIRS && lane < 24) stage_tail(svA, a.vin, ga0, ga1, lane - 16);
     else if (PAIRS) stage_tail(svB, a.vin, gb0, gb1, lane - 24);
   }
-  if (!mbar_wait_bounded(bar, 0, a.err, kErrTmaTimeout)) {
-    // give the copies one more bounded chance to land before the CTA exits
-    mbar_wait_bounded(bar, 0, nullptr, 0);
-    return;
-  }
-  __syncthreads();  // tails written with plain stores
+  __syncthreads();
+  if (!s_ok) return;
 
   // Read the bitonic sequence into STR registers: k = e*NT + tid.
   //   [0, front)            -inf pads          (rank k)
@@ -254,46 +280,35 @@ __global__ void __launch_bounds__(NT) merge_kernel(const MergeArgs a,
   Frag<K, PAIRS, E> f;
   const uint32_t endA = front + na, begB = Tm - nb;
   const uint32_t warp0 = tid & ~31u;
+  const K* sa = smA + offA;
+  const K* sb = smB + offB;
+  const int mode_in = MAP ? a.mode_in : 0;
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const uint32_t k = e * NT + tid;
     const uint32_t row0 = e * NT + warp0;
-    const bool isA = k >= front && k < endA;
-    const bool isB = k >= begB;
-    const K pad = k < front ? KeyLimits<K>::kMin : KeyLimits<K>::kMax;
-    const K* pa = smA + offA + (k - front);
-    const K* pb = smB + offB + (Tm - 1 - k);
-    K key;
-    if (row0 < endA && row0 + 31 >= begB) {
-      key = lds_pred(pa, isA, pad);
-      key = lds_pred(pb, isB, key);
-    } else {
-      key = isA ? *pa : (isB ? *pb : pad);
-    }
-    f.k[e] = (isA || isB) ? map_key(key, a.mode_in) : key;
+    bool real;
+    K key = read_seq<K>(sa, sb, k, row0, front, endA, begB, Tm - 1, KeyLimits<K>::kMin,
+                        KeyLimits<K>::kMax, real);
+    if constexpr (MAP) key = real ? map_key(key, mode_in) : key;
+    f.k[e] = key;
     if constexpr (PAIRS) {
-      const uint32_t* qa = svA + offvA + (k - front);
-      const uint32_t* qb = svB + offvB + (Tm - 1 - k);
-      uint32_t val;
-      if (row0 < endA && row0 + 31 >= begB) {
-        val = lds_pred(qa, isA, 0u);
-        val = lds_pred(qb, isB, val);
-      } else {
-        val = isA ? *qa : (isB ? *qb : 0u);
-      }
-      f.v[e] = val;
-      f.ix[e] = isB ? endA + (Tm - 1 - k) : (k < endA ? k : Tm + k);
+      bool rv;
+      f.v[e] = read_seq<uint32_t>(svA + offvA, svB + offvB, k, row0, front, endA, begB, Tm - 1,
+                                  0u, 0u, rv);
+      f.ix[e] = k >= begB ? endA + (Tm - 1 - k) : (k < endA ? k : Tm + k);
     }
   }
 
   uint32_t* planes = reinterpret_cast<uint32_t*>(body);
-  bitonic_merge_str<NT>(f, planes, S::kPlane);
+  bitonic_merge_str<NT>(f, planes);
 
   // outputs: BLK layout, thread holds tile slots tid*E .. tid*E+E-1
   K* kout = static_cast<K*>(a.kout) + p.out0;
   uint32_t* vout = PAIRS ? a.vout + p.out0 : nullptr;
   const uint32_t s0 = tid * E;
   const uint32_t cnt = static_cast<uint32_t>(p.d1 - p.d0);
+  const int mode_out = MAP ? a.mode_out : 0;
   if (s0 >= front && s0 + E <= front + cnt) {
     using KV = typename std::conditional<sizeof(K) == 4, uint4, ulonglong2>::type;
 #pragma unroll
@@ -302,7 +317,7 @@ __global__ void __launch_bounds__(NT) merge_kernel(const MergeArgs a,
       K* kp = reinterpret_cast<K*>(&kv);
 #pragma unroll
       for (int c = 0; c < static_cast<int>(VK); ++c)
-        kp[c] = unmap_key(f.k[q * VK + c], a.mode_out);
+        kp[c] = MAP ? unmap_key(f.k[q * VK + c], mode_out) : f.k[q * VK + c];
       *reinterpret_cast<KV*>(kout + s0 + q * VK) = kv;
     }
     if constexpr (PAIRS) {
@@ -316,7 +331,7 @@ __global__ void __launch_bounds__(NT) merge_kernel(const MergeArgs a,
     for (int e = 0; e < E; ++e) {
       const uint32_t s = s0 + e;
       if (s >= front && s < front + cnt) {
-        kout[s] = unmap_key(f.k[e], a.mode_out);
+        kout[s] = MAP ? unmap_key(f.k[e], mode_out) : f.k[e];
         if constexpr (PAIRS) vout[s] = f.v[e];
       }
     }
@@ -325,40 +340,47 @@ __global__ void __launch_bounds__(NT) merge_kernel(const MergeArgs a,
 
 // ---------------------------------------------------------------- dispatch
 
+// Pairs and 64-bit keys are built with E = 16 only (register budget).
 bool merge_cfg_supported(int key_bytes, bool pairs, int cfg) {
   if (cfg < 0 || cfg >= kNumMergeCfgs) return false;
   if (key_bytes != 4 && key_bytes != 8) return false;
-  return !(pairs && kMergeCfgs[cfg].E > 16);
+  if (pairs || key_bytes == 8) return kMergeCfgs[cfg].E == 16;
+  return true;
+}
+
+template <typename K, bool PAIRS, int E, int NT, bool IRREG, bool MAP>
+static cudaError_t launch_m2(const MergeArgs& a, const PairParam<IRREG>& pl, cudaStream_t s) {
+  using S = MergeSmem<K, PAIRS, E, NT>;
+  auto kern = merge_kernel<K, PAIRS, E, NT, IRREG, MAP>;
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         S::kTotal);
+  if (err != cudaSuccess) return err;
+  kern<<<static_cast<unsigned>(a.nitems), NT, S::kTotal, s>>>(a, pl);
+  return cudaGetLastError();
 }
 
 template <typename K, bool PAIRS, int E, int NT>
 static cudaError_t launch_m(const MergeArgs& a, const PairList* pl, cudaStream_t s) {
-  using S = MergeSmem<K, PAIRS, E, NT>;
   if (a.nitems == 0) return cudaSuccess;
-  const unsigned grid = static_cast<unsigned>(a.nitems);
-  cudaError_t err;
-  if (pl) {
-    auto kern = merge_kernel<K, PAIRS, E, NT, true>;
-    err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kTotal);
-    if (err != cudaSuccess) return err;
-    kern<<<grid, NT, S::kTotal, s>>>(a, *pl);
-  } else {
-    auto kern = merge_kernel<K, PAIRS, E, NT, false>;
-    err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kTotal);
-    if (err != cudaSuccess) return err;
-    kern<<<grid, NT, S::kTotal, s>>>(a, NoPairs{0});
-  }
-  return cudaGetLastError();
+  const bool map = (a.mode_in | a.mode_out) != 0;
+  if (pl)
+    return map ? launch_m2<K, PAIRS, E, NT, true, true>(a, *pl, s)
+               : launch_m2<K, PAIRS, E, NT, true, false>(a, *pl, s);
+  return map ? launch_m2<K, PAIRS, E, NT, false, true>(a, NoPairs{0}, s)
+             : launch_m2<K, PAIRS, E, NT, false, false>(a, NoPairs{0}, s);
 }
 
 template <typename K, bool PAIRS>
 static cudaError_t dispatch_m(int cfg, const MergeArgs& a, const PairList* pl, cudaStream_t s) {
   switch (cfg) {
     case 0: return launch_m<K, PAIRS, 16, 256>(a, pl, s);
-    case 1: return launch_m<K, PAIRS, 16, 512>(a, pl, s);
-    case 2:
-      if constexpr (!PAIRS) return launch_m<K, PAIRS, 32, 256>(a, pl, s);
+    case 1:
+      if constexpr (!PAIRS && sizeof(K) == 4) return launch_m<K, PAIRS, 32, 128>(a, pl, s);
       break;
+    case 2:
+      if constexpr (!PAIRS && sizeof(K) == 4) return launch_m<K, PAIRS, 32, 256>(a, pl, s);
+      break;
+    case 3: return launch_m<K, PAIRS, 16, 128>(a, pl, s);
     default: break;
   }
   return cudaErrorInvalidValue;
@@ -374,18 +396,29 @@ cudaError_t launch_merge(int key_bytes, bool pairs, int cfg, const MergeArgs& a,
                : dispatch_m<uint64_t, false>(cfg, a, pl, s);
 }
 
+template <typename K, bool IRREG, bool MAP>
+static void launch_p(const MergeArgs& a, int Tm, const PairParam<IRREG>& pl, cudaStream_t s) {
+  const uint64_t threads = a.nitems * 32;
+  const unsigned grid = static_cast<unsigned>((threads + 255) / 256);
+  partition_kernel<K, IRREG, MAP><<<grid, 256, 0, s>>>(a, Tm, pl);
+}
+
 cudaError_t launch_partition(int key_bytes, int cfg, const MergeArgs& a, const PairList* pl,
                              cudaStream_t s) {
   if (cfg < 0 || cfg >= kNumMergeCfgs) return cudaErrorInvalidValue;
   if (a.nitems == 0) return cudaSuccess;
   const int Tm = kMergeCfgs[cfg].tile();
-  const unsigned grid = static_cast<unsigned>((a.nitems + 255) / 256);
+  const bool map = a.mode_in != 0;
   if (key_bytes == 4) {
-    if (pl) partition_kernel<uint32_t, true><<<grid, 256, 0, s>>>(a, Tm, *pl);
-    else partition_kernel<uint32_t, false><<<grid, 256, 0, s>>>(a, Tm, NoPairs{0});
+    if (pl) map ? launch_p<uint32_t, true, true>(a, Tm, *pl, s)
+                : launch_p<uint32_t, true, false>(a, Tm, *pl, s);
+    else map ? launch_p<uint32_t, false, true>(a, Tm, NoPairs{0}, s)
+             : launch_p<uint32_t, false, false>(a, Tm, NoPairs{0}, s);
   } else {
-    if (pl) partition_kernel<uint64_t, true><<<grid, 256, 0, s>>>(a, Tm, *pl);
-    else partition_kernel<uint64_t, false><<<grid, 256, 0, s>>>(a, Tm, NoPairs{0});
+    if (pl) map ? launch_p<uint64_t, true, true>(a, Tm, *pl, s)
+                : launch_p<uint64_t, true, false>(a, Tm, *pl, s);
+    else map ? launch_p<uint64_t, false, true>(a, Tm, NoPairs{0}, s)
+             : launch_p<uint64_t, false, false>(a, Tm, NoPairs{0}, s);
   }
   return cudaGetLastError();
 }

@@ -107,7 +107,8 @@ def test_extreme_keys_tie_with_pads(bcf):
     n = 3 * 8192 + 77
     r = workloads.rng(5)
     for dtype, lo, hi in (("u32", 0, 0xFFFFFFFF), ("u64", 0, 2**64 - 1)):
-        keys = np.where(r.random(n) < 0.5, lo, hi).astype(workloads.DTYPES[dtype])
+        dt = workloads.DTYPES[dtype]
+        keys = np.where(r.random(n) < 0.5, dt(lo), dt(hi)).astype(dt)
         vals = workloads.row_index(n)
         for desc in (False, True):
             ek, ev = oracle.sort(keys, vals, descending=desc)
