@@ -48,8 +48,8 @@ struct Tuning {
 // sweeps.
 Tuning default_tuning(int kb, bool pairs) {
   Tuning t;
-  if (kb == 4 && !pairs) t = {1, 0};  // T = 8192 (32 x 256), Tm = 4096 (16 x 256)
-  else t = {0, 0};                    // pairs, 64-bit keys: T = Tm = 4096 (16 x 256)
+  if (kb == 4 && !pairs) t = {1, 3};  // T = 8192 (32 x 256), Tm = 2048 (16 x 128)
+  else t = {0, 3};                    // pairs, 64-bit keys: T = 4096 (16 x 256), Tm = 2048
   static const char* eb = std::getenv("BCF_BLOCK_CFG");
   static const char* em = std::getenv("BCF_MERGE_CFG");
   if (eb) {

@@ -356,6 +356,8 @@ __device__ __forceinline__ void stages(Frag<K, PAIRS, E>& f) {
 
 // Bitonic merge of the bitonic sequence of length E*NT held in STR layout;
 // ascending result in BLK layout.  Stages on bits t-1 .. 0 in STR, MID, BLK.
+// Both layout changes reuse one buffer (a second buffer would save two
+// barriers but halves the CTAs per SM, which was measured slower).
 template <int NT, typename K, bool PAIRS, int E>
 __device__ __forceinline__ void bitonic_merge_str(Frag<K, PAIRS, E>& f, uint32_t* sm) {
   using G = Geo<E, NT>;

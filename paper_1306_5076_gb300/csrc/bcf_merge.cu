@@ -110,17 +110,15 @@ __device__ __forceinline__ uint64_t first_item(const PairParam<IRREG>& pl) {
 
 // Merge path (exact splitter): the number of A-keys among the first d outputs
 // of the stable merge (A first on equal keys), i.e. the smallest i with
-// A[i] > B[d-1-i], or min(d, |A|) if there is none.  One warp per search:
-// each round the 32 lanes probe 32 evenly spaced candidates of the current
-// range and keep the sub-range between the last "false" and the first "true"
-// probe, shrinking it ~32x per round (about 6 dependent rounds of global
-// loads for runs of 2^27 keys instead of 27 for a binary search).
+// A[i] > B[d-1-i], or min(d, |A|) if there is none.  One thread per work item,
+// binary search in global memory.  (A warp-cooperative 32-ary search needs
+// ~6 instead of ~27 dependent rounds but reads ~7x more sectors, and was
+// measured slower at every run length.)
 template <typename K, bool IRREG, bool MAP>
 __global__ void __launch_bounds__(256) partition_kernel(const MergeArgs a, int Tm,
                                                         const __grid_constant__ PairParam<IRREG> pl) {
-  const uint64_t local = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  const uint32_t lane = threadIdx.x & 31u;
-  if (local >= a.nitems) return;  // whole warps exit together
+  const uint64_t local = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (local >= a.nitems) return;
   const uint64_t item = first_item<IRREG>(pl) + local;
   const Piece p = piece_of<IRREG>(a, pl, item, Tm);
   const K* A = static_cast<const K*>(a.kin) + p.src;
@@ -129,24 +127,18 @@ __global__ void __launch_bounds__(256) partition_kernel(const MergeArgs a, int T
   uint64_t lo = d > p.nb_tot ? d - p.nb_tot : 0;
   uint64_t hi = d < p.na_tot ? d : p.na_tot;
   while (lo < hi) {
-    const uint64_t span = hi - lo;
-    const uint64_t pos = lo + (span * lane) / 32;  // lo <= pos < hi, so A[pos], B[d-1-pos] exist
-    K x = __ldg(A + pos), y = __ldg(B + (d - 1 - pos));
+    const uint64_t mid = (lo + hi) >> 1;  // lo <= mid < hi: A[mid] and B[d-1-mid] exist
+    K x = __ldg(A + mid), y = __ldg(B + (d - 1 - mid));
     if constexpr (MAP) {
       x = map_key(x, a.mode_in);
       y = map_key(y, a.mode_in);
     }
-    const uint32_t m = __ballot_sync(0xFFFFFFFFu, x > y);
-    if (m == 0) {
-      lo = lo + (span * 31) / 32 + 1;  // every probe "false": beyond the last one
-    } else {
-      const int fl = __ffs(m) - 1;     // first "true" probe
-      const uint64_t pf = lo + (span * fl) / 32;
-      if (fl > 0) lo = lo + (span * (fl - 1)) / 32 + 1;
-      hi = pf;
-    }
+    if (x > y)
+      hi = mid;
+    else
+      lo = mid + 1;
   }
-  if (lane == 0) a.splits[item] = lo;
+  a.splits[item] = lo;
 }
 
 // Stage elements [g0, g1) of `src` (absolute indices; src 16-byte aligned)
@@ -186,6 +178,7 @@ struct MergeSmem {
   static constexpr uint32_t kValBytes = PAIRS ? ((Tm + 12) * 4 + 15) / 16 * 16 : 0;
   static constexpr uint32_t kStageBytes = kKeyBytes + kValBytes;
   static constexpr uint32_t kPlaneBytes = Frag<K, PAIRS, E>::W * Geo<E, NT>::kPlane * 4;
+  // the transposes reuse the staging area once it has been read
   static constexpr uint32_t kBody = kStageBytes > kPlaneBytes ? kStageBytes : kPlaneBytes;
   static constexpr uint32_t kTotal = 16 + kBody;  // + mbarrier
 };
@@ -300,8 +293,7 @@ __global__ void __launch_bounds__(NT) merge_kernel(const MergeArgs a,
     }
   }
 
-  uint32_t* planes = reinterpret_cast<uint32_t*>(body);
-  bitonic_merge_str<NT>(f, planes);
+  bitonic_merge_str<NT>(f, reinterpret_cast<uint32_t*>(body));
 
   // outputs: BLK layout, thread holds tile slots tid*E .. tid*E+E-1
   K* kout = static_cast<K*>(a.kout) + p.out0;
@@ -398,8 +390,7 @@ cudaError_t launch_merge(int key_bytes, bool pairs, int cfg, const MergeArgs& a,
 
 template <typename K, bool IRREG, bool MAP>
 static void launch_p(const MergeArgs& a, int Tm, const PairParam<IRREG>& pl, cudaStream_t s) {
-  const uint64_t threads = a.nitems * 32;
-  const unsigned grid = static_cast<unsigned>((threads + 255) / 256);
+  const unsigned grid = static_cast<unsigned>((a.nitems + 255) / 256);
   partition_kernel<K, IRREG, MAP><<<grid, 256, 0, s>>>(a, Tm, pl);
 }
 
