@@ -175,6 +175,34 @@ bcf_status bcf_profile_collect(bcf_profile* out);
 /* Version string of the library. */
 const char* bcf_version(void);
 
+/* ---- sort without a caller workspace ------------------------------------ */
+
+/*
+ * bcf_sort_keys_static: bcf_sort_keys for callers that cannot allocate device
+ * memory.  The paper has no counterpart; this is a deployment convenience.
+ *
+ * Some callers cannot call cudaMalloc: a framework or plugin host that owns
+ * every device allocation and hands a plugin only its input and output
+ * buffers, code running while another thread captures a CUDA graph in global
+ * capture mode (cudaMalloc is an error there), or a latency-critical loop that
+ * must not take cudaMalloc's implicit device synchronisation.  They pass only
+ * keys_in / keys_out; the merge passes' scratch (ping-pong copy and split
+ * array) lives in a device array inside the library.
+ *
+ *   - n <= BCF_STATIC_MAX_KEYS, else BCF_EUNSUPPORTED before any launch; keys
+ *     only; otherwise the arguments, results and errors of bcf_sort_keys.
+ *   - The array (about 8 MiB) is held by every GPU that loads the library until
+ *     the process exits.  The call allocates nothing.
+ *   - All calls share the array: calls whose GPU work overlaps in time (other
+ *     streams, other host threads) race and give wrong results.  Serialise them.
+ *     Nothing in it needs to start at zero; it keeps the last call's contents.
+ *   - The first call on a device looks up the array's device address with that
+ *     device current; make that first call before any stream capture.
+ */
+#define BCF_STATIC_MAX_KEYS (1u << 20)
+bcf_status bcf_sort_keys_static(void* keys_out, const void* keys_in, uint64_t n, bcf_dtype kt,
+                                const bcf_opts* opts, cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

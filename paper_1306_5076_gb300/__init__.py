@@ -20,7 +20,8 @@ from ._native import BCF_F32, BCF_OP_MERGE, BCF_OP_SEGMENTED, BCF_OP_SORT, BCF_U
 __all__ = [
     "BcfError", "bcf_workspace_bytes", "bcf_sort_keys", "bcf_sort_pairs", "bcf_merge_runs",
     "bcf_segmented_sort", "bcf_last_device_error", "bcf_sort_plan", "bcf_profile_enable",
-    "bcf_profile_collect", "bcf_version", "key_dtype_of", "BCF_U32", "BCF_U64", "BCF_F32",
+    "bcf_profile_collect", "bcf_version", "bcf_sort_keys_static", "key_dtype_of", "BCF_U32",
+    "BCF_U64", "BCF_F32",
     "BCF_OP_SORT", "BCF_OP_MERGE", "BCF_OP_SEGMENTED",
 ]
 
@@ -158,6 +159,17 @@ def bcf_profile_collect() -> dict:
     kinds = ("block_sort", "partition", "merge", "segmented")
     return {k: {"launches": int(p.launches[i]), "total_ms": float(p.total_ms[i])}
             for i, k in enumerate(kinds)}
+
+
+def bcf_sort_keys_static(keys_out, keys_in, *, descending=False, stream=None, kt=None):
+    """Sort without a caller workspace: the library's own device array serves as
+    scratch, so neither this call nor the library allocates (at most
+    ``_native.BCF_STATIC_MAX_KEYS`` keys; calls must not overlap on the GPU)."""
+    kt = key_dtype_of(keys_in) if kt is None else kt
+    _check(_native.load().bcf_sort_keys_static(_ptr(keys_out), _ptr(keys_in), keys_in.numel(),
+                                               kt, _opts(descending), _stream(stream)),
+           "bcf_sort_keys_static")
+    return keys_out
 
 
 def bcf_version() -> str:

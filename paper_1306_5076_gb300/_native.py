@@ -50,7 +50,11 @@ SIGNATURES = {
     "bcf_profile_enable": (_i32, [_i32]),
     "bcf_profile_collect": (_i32, [ctypes.POINTER(BcfProfile)]),
     "bcf_version": (ctypes.c_char_p, []),
+    "bcf_sort_keys_static": (_i32, [_vp, _vp, _u64, _i32, ctypes.POINTER(BcfOpts), _vp]),
 }
+
+# keys per call accepted by bcf_sort_keys_static (BCF_STATIC_MAX_KEYS)
+BCF_STATIC_MAX_KEYS = 1 << 20
 
 _lock = threading.Lock()
 _lib = None

@@ -1,0 +1,67 @@
+// bcf_static.cu -- bcf_sort_keys_static: the key sort with its scratch memory
+// in a file-scope device array instead of a caller-provided workspace.
+//
+// Who needs it: callers that cannot call cudaMalloc at all -- for example a
+// plugin or kernel-hosting framework that owns every device allocation and
+// hands out only input and output buffers, code that runs while another
+// thread captures a CUDA graph in global capture mode (where cudaMalloc is an
+// error), or a latency-critical loop that must never hit cudaMalloc's
+// implicit device-wide synchronisation.  Such callers pass inputs and outputs
+// only; the ping-pong buffer and split array of the merge passes live in
+// g_static_workspace below, reserved when the library is loaded on a GPU.
+//
+// Costs and rules:
+//  - every GPU that loads this library holds kStaticBytes (about 8 MiB) of
+//    device memory until the process exits;
+//  - at most BCF_STATIC_MAX_KEYS keys per call;
+//  - every call shares the one array: calls whose GPU work overlaps (two
+//    streams, or two host threads) race and corrupt each other's results;
+//  - nothing in the array has to start at zero (every word is written before
+//    it is read), so calls need not clear it; it keeps the last call's data;
+//  - the first call on a device looks up the array's device address
+//    (cudaGetSymbolAddress) with that device current; make that first call
+//    before any stream capture.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "bcfsort.h"
+
+namespace {
+
+// The sort's workspace for BCF_STATIC_MAX_KEYS keys of the widest type (u64),
+// keys only: a 256-byte header, one u64 split per 2048-key merge tile (+2),
+// rounded to 256 bytes, then one copy of the keys.  A spare page on top.
+constexpr size_t kMaxKeys = BCF_STATIC_MAX_KEYS;
+constexpr size_t kSplitBytes = ((256 + (kMaxKeys / 2048 + 2) * 8) + 255) / 256 * 256;
+constexpr size_t kStaticBytes = kSplitBytes + kMaxKeys * 8 + 4096;
+
+static __device__ __align__(256) unsigned char g_static_workspace[kStaticBytes];
+
+// Device address of g_static_workspace on the current device (its host-side
+// name is only a stand-in; kernels must be given this address).
+void* static_workspace() {
+  static std::mutex mu;
+  static void* addr[64] = {};
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_static_workspace) != cudaSuccess) return nullptr;
+    addr[dev] = p;
+  }
+  return addr[dev];
+}
+
+}  // namespace
+
+extern "C" bcf_status bcf_sort_keys_static(void* keys_out, const void* keys_in, uint64_t n,
+                                           bcf_dtype kt, const bcf_opts* opts,
+                                           cudaStream_t stream) {
+  if (n > kMaxKeys) return BCF_EUNSUPPORTED;
+  if (n == 0) return bcf_sort_keys(keys_out, keys_in, 0, kt, opts, nullptr, 0, stream);
+  void* ws = static_workspace();
+  if (!ws) return BCF_ECUDA;
+  return bcf_sort_keys(keys_out, keys_in, n, kt, opts, ws, kStaticBytes, stream);
+}
