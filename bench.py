@@ -38,7 +38,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "keys/s & % HBM roofline per pass (bit-exact); served vs plain p99 latency on one GB300"
 LOG2N = 28
-N = 1 << LOG2N
+N = 1 << LOG2N  # the benchmark workload; --log2n shrinks it for profiling captures only
 SAMPLE_LOG2N = 24  # oracle sample (CPU legs)
 KEY_BYTES = 4
 
@@ -333,7 +333,7 @@ def run_gpu(args, world, rank, local, pg):
         "vs_baseline": None,
         "dtype": "u32",
         "data": "synthetic",
-        "config": {"workload": "sort of 2^28 uniform u32 keys, keys only, ascending",
+        "config": {"workload": f"sort of 2^{args.log2n} uniform u32 keys, keys only, ascending",
                    "n": N, "key": "u32", "payload": None, "seed": seed,
                    "block_tile": plan["block_tile"], "merge_tile": plan["merge_tile"],
                    "merge_passes": plan["merge_passes"],
@@ -367,7 +367,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--log2n", type=int, default=LOG2N,
+                    help="keys = 2^log2n (default 28, the benchmark workload; smaller values "
+                         "are for ncu captures)")
     args = ap.parse_args()
+    global N
+    N = 1 << args.log2n
     if args.warmup < 3:
         args.warmup = 3
     world, rank, local, pg = dist_setup(args)

@@ -101,6 +101,43 @@ WsLayout ws_layout(uint64_t n, uint64_t runs_or_segs, int kb, bool pairs) {
   return w;
 }
 
+// Segmented sort workspace: counters, per-segment state, the work queue and
+// one copy of the keys (+ values).  The queue bound holds for any segment
+// sizes: a segment touches at most size/T + 2 tiles, and each of its passes
+// has one item per tile.
+struct SegLayout {
+  size_t ctl, items, tiny, queue, keys, vals, total;
+  uint64_t capacity;
+};
+
+SegLayout seg_layout(uint64_t n, uint64_t nseg, int kb, bool pairs) {
+  SegLayout w;
+  const uint64_t tiles = n / kMinSegTile + 2 * nseg + 2;
+  uint64_t passes = 1;
+  while ((1ull << passes) < tiles) ++passes;
+  w.capacity = tiles * (1 + passes) + nseg / 8 + 2;
+  w.ctl = kAlign;
+  w.items = align_up(w.ctl + seg_ctl_bytes(), kAlign);
+  w.tiny = align_up(w.items + nseg * 4, kAlign);
+  w.queue = align_up(w.tiny + nseg * 4, kAlign);
+  w.keys = align_up(w.queue + w.capacity * seg_work_bytes(), kAlign);
+  w.vals = align_up(w.keys + n * kb, kAlign);
+  w.total = align_up(w.vals + (pairs ? n * 4 : 0), kAlign);
+  return w;
+}
+
+int default_seg_cfg(int kb, bool pairs) {
+  (void)kb;
+  (void)pairs;
+  int c = 0;  // 16 x 256: 4096-key tiles
+  static const char* es = std::getenv("BCF_SEG_CFG");
+  if (es) {
+    const int v = std::atoi(es);
+    if (seg_cfg_supported(kb, pairs, v)) c = v;
+  }
+  return c;
+}
+
 // ---------------------------------------------------------------- device error word
 
 uint32_t* error_word_ptr() {
@@ -387,6 +424,50 @@ bcf_status run_merge(void* ko, uint32_t* vo, const void* ki, const uint32_t* vi,
   return BCF_OK;
 }
 
+// ---------------------------------------------------------------- segmented
+
+bcf_status run_segmented(void* ko, uint32_t* vo, const void* ki, const uint32_t* vi,
+                         const uint64_t* off, uint64_t nseg, uint64_t n, bcf_dtype kt,
+                         const bcf_opts* o, void* ws, size_t ws_bytes, cudaStream_t s) {
+  const bool pairs = vo != nullptr || vi != nullptr;
+  if (pairs && (!vo || !vi)) return BCF_EINVAL;
+  bcf_status st = check_common(ko, vo, ki, vi, n, kt, pairs);
+  if (st != BCF_OK) return st;
+  if (n == 0 || nseg == 0) return BCF_OK;
+  if (!off || (reinterpret_cast<uintptr_t>(off) & 7u)) return BCF_EINVAL;
+  if (nseg > 0xFFFFFFFFull) return BCF_EUNSUPPORTED;
+  const int kb = key_bytes_of(kt);
+  const SegLayout wl = seg_layout(n, nseg, kb, pairs);
+  st = check_ws(ws, ws_bytes, wl.total, ko, vo, ki, vi, n, kb);
+  if (st != BCF_OK) return st;
+  uint32_t* err = error_word_ptr();
+  if (!err) return BCF_ECUDA;
+  char* wsb = static_cast<char*>(ws);
+  SegLaunch L{};
+  L.kin = ki;
+  L.vin = vi;
+  L.kout = ko;
+  L.vout = vo;
+  L.kbuf = wsb + wl.keys;
+  L.vbuf = pairs ? reinterpret_cast<uint32_t*>(wsb + wl.vals) : nullptr;
+  L.off = off;
+  L.nseg = nseg;
+  L.n = n;
+  L.mode = mode_of(kt, o);
+  L.queue = wsb + wl.queue;
+  L.capacity = wl.capacity;
+  L.items_left = reinterpret_cast<uint32_t*>(wsb + wl.items);
+  L.tiny_list = reinterpret_cast<uint32_t*>(wsb + wl.tiny);
+  L.ctl = wsb + wl.ctl;
+  L.err = err;
+  // unpublished queue slots must read "not ready"
+  if (cudaMemsetAsync(L.queue, 0, wl.capacity * seg_work_bytes(), s) != cudaSuccess)
+    return BCF_ECUDA;
+  const int cfg = default_seg_cfg(kb, pairs);
+  const cudaError_t e = timed(3, s, [&] { return launch_segmented(kb, pairs, cfg, L, s); });
+  return from_cuda(e);
+}
+
 }  // namespace
 }  // namespace bcf
 
@@ -402,7 +483,7 @@ size_t bcf_workspace_bytes(int op, uint64_t n, uint64_t nseg_or_k, bcf_dtype kt,
   switch (op) {
     case BCF_OP_SORT: return ws_layout(n, 0, kb, has_vals != 0).total;
     case BCF_OP_MERGE: return ws_layout(n, nseg_or_k, kb, has_vals != 0).total;
-    case BCF_OP_SEGMENTED: return ws_layout(n, nseg_or_k, kb, has_vals != 0).total;
+    case BCF_OP_SEGMENTED: return seg_layout(n, nseg_or_k, kb, has_vals != 0).total;
     default: return 0;
   }
 }
@@ -432,9 +513,9 @@ bcf_status bcf_segmented_sort(void* keys_out, uint32_t* vals_out, const void* ke
                               uint64_t nseg, uint64_t n_total, bcf_dtype kt,
                               const bcf_opts* opts, void* ws, size_t ws_bytes,
                               cudaStream_t stream) {
-  (void)keys_out; (void)vals_out; (void)keys_in; (void)vals_in; (void)seg_offsets_dev;
-  (void)nseg; (void)n_total; (void)kt; (void)opts; (void)ws; (void)ws_bytes; (void)stream;
-  return BCF_EUNSUPPORTED;
+  if ((vals_out == nullptr) != (vals_in == nullptr)) return BCF_EINVAL;
+  return run_segmented(keys_out, vals_out, keys_in, vals_in, seg_offsets_dev, nseg, n_total, kt,
+                       opts, ws, ws_bytes, stream);
 }
 
 const char* bcf_status_string(bcf_status s) {

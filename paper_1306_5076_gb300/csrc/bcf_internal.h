@@ -69,6 +69,34 @@ constexpr int kNumMergeCfgs = sizeof(kMergeCfgs) / sizeof(kMergeCfgs[0]);
 bool block_cfg_supported(int key_bytes, bool pairs, int cfg);
 bool merge_cfg_supported(int key_bytes, bool pairs, int cfg);
 
+// Segmented sort (persistent kernel); tile = merge tile = E * NT.
+constexpr TileCfg kSegCfgs[] = {{16, 256}, {16, 128}, {32, 128}};
+constexpr int kNumSegCfgs = sizeof(kSegCfgs) / sizeof(kSegCfgs[0]);
+constexpr uint64_t kMinSegTile = 2048;
+
+struct SegLaunch {
+  const void* kin;
+  const uint32_t* vin;
+  void* kout;
+  uint32_t* vout;
+  void* kbuf;            // workspace copy of the keys (ping-pong)
+  uint32_t* vbuf;
+  const uint64_t* off;   // device, nseg + 1
+  uint64_t nseg, n;
+  int mode;
+  void* queue;           // work descriptors, `capacity` of them, cleared to 0
+  uint64_t capacity;
+  uint32_t* items_left;  // nseg
+  uint32_t* tiny_list;   // nseg
+  void* ctl;             // queue counters
+  uint32_t* err;
+};
+bool seg_cfg_supported(int key_bytes, bool pairs, int cfg);
+cudaError_t launch_segmented(int key_bytes, bool pairs, int cfg, const SegLaunch& L,
+                             cudaStream_t s);
+size_t seg_work_bytes();
+size_t seg_ctl_bytes();
+
 cudaError_t launch_block_sort(int key_bytes, bool pairs, int cfg, const BlockSortArgs& a,
                               cudaStream_t s);
 cudaError_t launch_partition(int key_bytes, int cfg, const MergeArgs& a, const PairList* pl,

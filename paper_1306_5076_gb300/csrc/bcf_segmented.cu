@@ -1,0 +1,160 @@
+// bcf_segmented.cu -- sorting many independent segments in one persistent
+// launch (the batching extension of the paper's method; the paper's own
+// "segmented ShearSort" sorts segments inside one tile, Sec. 3.1 and
+// Algorithm 5).
+//
+// Plan (plan_kernel, one CTA): every segment is classified --
+//   tiny   : 1..512 keys, sorted by one warp entirely in registers (Batcher's
+//            network per lane, then bitonic merges across lanes by shuffle);
+//   others : block-sorted in T-key tiles (T-aligned in the array, clipped to
+//            the segment, ragged ends padded), then merged pairwise with
+//            ceil(log2 tiles) segment-local merge passes (Sec. 3.2; Lemma 2).
+// The plan publishes the first-phase work items in a device queue: all tile
+// sorts, then tiny groups of 8 segments (one warp each).
+//
+// Execution (seg_worker, persistent: one wave of co-resident CTAs): each CTA
+// repeatedly takes the next queue slot.  When the last item of a segment's
+// pass completes, the CTA that completed it enqueues the segment's next pass
+// (one item per T-aligned output tile of the segment), so every segment
+// advances as soon as its own data is ready and no grid-wide barrier exists.
+// Waiting for a slot to be published is bounded (global timer); on expiry the
+// device error word is set and the CTA exits.
+//
+// Merge pieces compute their own exact splitters (merge path, two warps in
+// parallel, 32-ary search) and read their windows straight from global memory
+// (.cg loads: data written by other SMs earlier in the same launch must not be
+// served from a stale L1 line), then run the same conflict-free bitonic merge
+// as the merge pass kernel.
+#include <cuda_runtime.h>
+
+#include "bcf_segmented.cuh"
+
+namespace bcf {
+
+// ---------------------------------------------------------------- plan
+
+// Inclusive block scan of one value per thread (blockDim.x == 1024).
+template <typename T>
+__device__ __forceinline__ T block_scan_incl(T v, T* warp_sums, T& total) {
+  const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const T u = __shfl_up_sync(0xFFFFFFFFu, v, d);
+    if (lane >= static_cast<uint32_t>(d)) v += u;
+  }
+  if (lane == 31) warp_sums[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    T x = warp_sums[lane];
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const T u = __shfl_up_sync(0xFFFFFFFFu, x, d);
+      if (lane >= static_cast<uint32_t>(d)) x += u;
+    }
+    warp_sums[lane] = x;
+  }
+  __syncthreads();
+  if (w > 0) v += warp_sums[w - 1];
+  total = warp_sums[31];
+  __syncthreads();
+  return v;
+}
+
+__global__ void __launch_bounds__(1024) plan_kernel(const SegArgs a, uint32_t T) {
+  __shared__ unsigned long long ws[32];
+  unsigned long long carry_tiles = 0, carry_tiny = 0, carry_total = 0;
+  for (uint64_t c = 0; c < a.nseg; c += 1024) {
+    const uint64_t s = c + threadIdx.x;
+    SegGeo g{};
+    if (s < a.nseg) g = seg_geo(a.off, s, a.n, T);
+    const unsigned long long tiles = g.tiles;
+    const unsigned long long tiny = g.tiny ? 1 : 0;
+    const unsigned long long tot = tiles + static_cast<unsigned long long>(g.passes) * g.pieces;
+    unsigned long long sum;
+    const unsigned long long t_incl = block_scan_incl(tiles, ws, sum);
+    const unsigned long long t_excl = t_incl - tiles;
+    const unsigned long long sum_tiles = sum;
+    const unsigned long long y_incl = block_scan_incl(tiny, ws, sum);
+    const unsigned long long sum_tiny = sum;
+    const unsigned long long tot_incl = block_scan_incl(tot, ws, sum);
+    (void)tot_incl;
+    const unsigned long long sum_tot = sum;
+    if (s < a.nseg) {
+      a.items_left[s] = g.tiles;
+      if (g.tiny) a.tiny_list[carry_tiny + y_incl - 1] = static_cast<uint32_t>(s);
+      const unsigned long long base = carry_tiles + t_excl;
+      for (uint32_t q = 0; q < g.tiles; ++q) {
+        if (base + q < a.capacity) {
+          SegWork w;
+          w.meta = kReady | kWTile;
+          w.seg = static_cast<uint32_t>(s);
+          w.arg = q;
+          a.queue[base + q] = w;
+        }
+      }
+    }
+    carry_tiles += sum_tiles;
+    carry_tiny += sum_tiny;
+    carry_total += sum_tot;
+  }
+  const unsigned long long groups = (carry_tiny + kTinyPerGroup - 1) / kTinyPerGroup;
+  for (unsigned long long q = threadIdx.x; q < groups; q += blockDim.x) {
+    if (carry_tiles + q < a.capacity) {
+      SegWork w;
+      w.meta = kReady | kWTiny;
+      w.seg = 0;
+      w.arg = q;
+      a.queue[carry_tiles + q] = w;
+    }
+  }
+  if (threadIdx.x == 0) {
+    const unsigned long long total = carry_total + groups;
+    a.ctl->head = 0;
+    a.ctl->reserve = carry_tiles + groups;
+    a.ctl->total = total <= a.capacity ? total : 0;  // overflow: nothing runs
+    a.ctl->n_tiny = carry_tiny;
+    if (total > a.capacity) atomicOr(a.err, kErrQueueOverflow);
+  }
+}
+
+cudaError_t launch_plan(const SegArgs& a, uint32_t T, cudaStream_t s) {
+  plan_kernel<<<1, 1024, 0, s>>>(a, T);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- host side
+
+bool seg_cfg_supported(int key_bytes, bool pairs, int cfg) {
+  if (cfg < 0 || cfg >= kNumSegCfgs) return false;
+  if (key_bytes != 4 && key_bytes != 8) return false;
+  return kSegCfgs[cfg].E == 16 || (!pairs && key_bytes == 4);
+}
+
+cudaError_t launch_segmented(int key_bytes, bool pairs, int cfg, const SegLaunch& L,
+                             cudaStream_t s) {
+  if (!seg_cfg_supported(key_bytes, pairs, cfg)) return cudaErrorInvalidValue;
+  SegArgs a;
+  a.kin = L.kin;
+  a.vin = L.vin;
+  a.kout = L.kout;
+  a.vout = L.vout;
+  a.kbuf = L.kbuf;
+  a.vbuf = L.vbuf;
+  a.off = L.off;
+  a.nseg = L.nseg;
+  a.n = L.n;
+  a.mode = L.mode;
+  a.queue = static_cast<SegWork*>(L.queue);
+  a.capacity = L.capacity;
+  a.items_left = L.items_left;
+  a.tiny_list = L.tiny_list;
+  a.ctl = static_cast<SegCtl*>(L.ctl);
+  a.err = L.err;
+  return key_bytes == 4 ? launch_segmented_typed<uint32_t>(pairs, cfg, a, s)
+                         : launch_segmented_typed<uint64_t>(pairs, cfg, a, s);
+}
+
+size_t seg_work_bytes() { return sizeof(SegWork); }
+size_t seg_ctl_bytes() { return sizeof(SegCtl); }
+
+}  // namespace bcf

@@ -1,0 +1,449 @@
+// bcf_segmented.cuh -- device code of the segmented sort (see bcf_segmented.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <type_traits>
+
+#include "bcf_device.cuh"
+#include "bcf_internal.h"
+
+namespace bcf {
+
+constexpr uint32_t kTinyMax = 512;      // keys per tiny segment (32 lanes x 16)
+constexpr uint32_t kTinyPerGroup = 8;   // tiny segments per work item (one per warp)
+constexpr uint32_t kErrQueueTimeout = 2u;
+constexpr uint32_t kErrQueueOverflow = 4u;
+
+enum : uint32_t { kWTiny = 1, kWTile = 2, kWPiece = 3, kReady = 0x80000000u };
+
+struct SegWork {
+  uint32_t meta;  // kReady | pass << 8 | type
+  uint32_t seg;
+  uint64_t arg;   // tile / output-tile index relative to the segment, or tiny group
+};
+
+struct SegCtl {
+  unsigned long long head;     // next slot to take
+  unsigned long long reserve;  // slots published or being published
+  unsigned long long total;    // work items that will ever exist
+  unsigned long long n_tiny;
+};
+
+__host__ __device__ constexpr uint32_t ceil_log2(uint64_t x) {
+  uint32_t p = 0;
+  while ((1ull << p) < x) ++p;
+  return p;
+}
+
+struct SegGeo {
+  uint64_t lo, hi;
+  uint32_t tiles, passes, pieces;
+  bool tiny;
+};
+
+__device__ __forceinline__ SegGeo seg_geo(const uint64_t* off, uint64_t s, uint64_t n, uint32_t T) {
+  SegGeo g;
+  uint64_t lo = __ldcg(off + s), hi = __ldcg(off + s + 1);
+  // memory safety for malformed offsets: clamp into [0, n] and make hi >= lo
+  lo = lo < n ? lo : n;
+  hi = hi < n ? hi : n;
+  hi = hi > lo ? hi : lo;
+  g.lo = lo;
+  g.hi = hi;
+  const uint64_t size = hi - lo;
+  g.tiny = size > 0 && size <= kTinyMax;
+  g.tiles = (size == 0 || g.tiny) ? 0 : static_cast<uint32_t>((hi - 1) / T - lo / T + 1);
+  g.passes = g.tiles > 1 ? ceil_log2(g.tiles) : 0;
+  g.pieces = g.tiles;  // merge output tiles: the same T-aligned tiles as the sort
+  return g;
+}
+
+struct SegArgs {
+  const void* kin;
+  const uint32_t* vin;
+  void* kout;
+  uint32_t* vout;
+  void* kbuf;      // ping-pong copy (workspace)
+  uint32_t* vbuf;
+  const uint64_t* off;
+  uint64_t nseg, n;
+  int mode;
+  SegWork* queue;
+  uint64_t capacity;
+  uint32_t* items_left;
+  uint32_t* tiny_list;
+  SegCtl* ctl;
+  uint32_t* err;
+};
+
+// The plan kernel lives in bcf_segmented.cu.
+cudaError_t launch_plan(const SegArgs& a, uint32_t T, cudaStream_t s);
+
+// ---------------------------------------------------------------- tiny segments
+
+// Sort of one tiny segment (<= 512 keys) by one warp: 16 registers per lane,
+// Batcher's network per lane, then bitonic merges across lanes with the
+// level's flip as a mirrored shuffle, so every compare-exchange ascends.
+template <typename K, bool PAIRS, bool MAP>
+__device__ __forceinline__ void warp_sort_segment(const SegArgs& a, uint64_t lo, uint64_t hi) {
+  constexpr int E = 16;
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t size = static_cast<uint32_t>(hi - lo);
+  const K* kin = static_cast<const K*>(a.kin) + lo;
+  Frag<K, PAIRS, E> f;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const uint32_t k = e * 32 + lane;
+    const bool real = k < size;
+    K x = KeyLimits<K>::kMax;
+    if (real) x = MAP ? map_key(__ldcg(kin + k), a.mode) : __ldcg(kin + k);
+    f.k[e] = x;
+    if constexpr (PAIRS) {
+      f.v[e] = real ? __ldcg(a.vin + lo + k) : 0u;
+      f.ix[e] = k;
+    }
+  }
+  thread_sort(f, false);
+#pragma unroll 1
+  for (int j = 5; j <= 9; ++j) {
+    // flip: my register e meets the mirrored lane's register 15 - e
+    {
+      const uint32_t m = (1u << (j - 4)) - 1u;
+      const bool upper = (lane & (1u << (j - 5))) != 0;
+      K pk[E];
+      uint32_t pi[PAIRS ? E : 1], pv[PAIRS ? E : 1];
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        pk[e] = __shfl_xor_sync(0xFFFFFFFFu, f.k[E - 1 - e], m);
+        if constexpr (PAIRS) {
+          pi[e] = __shfl_xor_sync(0xFFFFFFFFu, f.ix[E - 1 - e], m);
+          pv[e] = __shfl_xor_sync(0xFFFFFFFFu, f.v[E - 1 - e], m);
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        if constexpr (!PAIRS) {
+          const K x = f.k[e], y = pk[e];
+          f.k[e] = upper ? (x > y ? x : y) : (x < y ? x : y);
+        } else {
+          const bool p_after = after(pk[e], pi[e], f.k[e], f.ix[e]);
+          const bool take = upper ? p_after : !p_after;
+          f.k[e] = take ? pk[e] : f.k[e];
+          f.ix[e] = take ? pi[e] : f.ix[e];
+          f.v[e] = take ? pv[e] : f.v[e];
+        }
+      }
+    }
+    // half-cleaners on lane bits j-2 .. 4
+#pragma unroll 1
+    for (int b = j - 2; b >= 4; --b) {
+      const uint32_t m = 1u << (b - 4);
+      const bool upper = (lane & m) != 0;
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const K y = __shfl_xor_sync(0xFFFFFFFFu, f.k[e], m);
+        if constexpr (!PAIRS) {
+          const K x = f.k[e];
+          f.k[e] = upper ? (x > y ? x : y) : (x < y ? x : y);
+        } else {
+          const uint32_t yi = __shfl_xor_sync(0xFFFFFFFFu, f.ix[e], m);
+          const uint32_t yv = __shfl_xor_sync(0xFFFFFFFFu, f.v[e], m);
+          const bool p_after = after(y, yi, f.k[e], f.ix[e]);
+          const bool take = upper ? p_after : !p_after;
+          f.k[e] = take ? y : f.k[e];
+          f.ix[e] = take ? yi : f.ix[e];
+          f.v[e] = take ? yv : f.v[e];
+        }
+      }
+    }
+    // register bits 3 .. 0
+#pragma unroll
+    for (int q = 3; q >= 0; --q) {
+#pragma unroll
+      for (int e = 0; e < E; ++e)
+        if (!(e & (1 << q))) ce(f, e, e | (1 << q), false);
+    }
+  }
+  K* kout = static_cast<K*>(a.kout) + lo;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const uint32_t k = lane * E + e;
+    if (k < size) {
+      kout[k] = MAP ? unmap_key(f.k[e], a.mode) : f.k[e];
+      if constexpr (PAIRS) a.vout[lo + k] = f.v[e];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- tile sort
+
+template <typename K, bool PAIRS, int E, int NT, bool MAP>
+__device__ __forceinline__ void sort_tile_item(const SegArgs& a, const SegGeo& g, uint64_t q,
+                                               uint32_t* sm) {
+  constexpr uint32_t T = E * NT;
+  const uint32_t tid = threadIdx.x;
+  const uint64_t base = (g.lo / T + q) * T;
+  const uint64_t s0 = g.lo > base ? g.lo : base;
+  const uint64_t s1 = g.hi < base + T ? g.hi : base + T;
+  const uint32_t front = static_cast<uint32_t>(s0 - base), cnt = static_cast<uint32_t>(s1 - s0);
+  const K* kin = static_cast<const K*>(a.kin) + base;
+  Frag<K, PAIRS, E> f;
+  // striped loads (coalesced); slot k is the element's tile position, which is
+  // also its rank in the stable input order; -inf pads before, +inf after
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const uint32_t k = e * NT + tid;
+    const bool real = k >= front && k < front + cnt;
+    K x = k < front ? KeyLimits<K>::kMin : KeyLimits<K>::kMax;
+    if (real) x = MAP ? map_key(__ldcg(kin + k), a.mode) : __ldcg(kin + k);
+    f.k[e] = x;
+    if constexpr (PAIRS) {
+      f.v[e] = real ? __ldcg(a.vin + base + k) : 0u;
+      f.ix[e] = k;
+    }
+  }
+  block_sort_tile<NT>(f, sm);
+  // the segment's passes alternate buffers so that its last one writes the output
+  const bool to_out = (g.passes % 2) == 0;
+  K* kout = static_cast<K*>(to_out ? a.kout : a.kbuf) + base;
+  uint32_t* vout = PAIRS ? (to_out ? a.vout : a.vbuf) + base : nullptr;
+  const bool last = g.passes == 0;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const uint32_t k = tid * E + e;
+    if (k >= front && k < front + cnt) {
+      kout[k] = (MAP && last) ? unmap_key(f.k[e], a.mode) : f.k[e];
+      if constexpr (PAIRS) vout[k] = f.v[e];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- merge piece
+
+// Merge path by one warp, 32-ary (see partition_kernel in bcf_merge.cu for
+// the predicate); A and B are read with .cg loads.
+template <typename K>
+__device__ __forceinline__ uint64_t warp_merge_path(const K* A, uint64_t na, const K* B,
+                                                    uint64_t nb, uint64_t d) {
+  const uint32_t lane = threadIdx.x & 31u;
+  uint64_t lo = d > nb ? d - nb : 0;
+  uint64_t hi = d < na ? d : na;
+  while (lo < hi) {
+    const uint64_t span = hi - lo;
+    const uint64_t pos = lo + (span * lane) / 32;
+    const bool p = __ldcg(A + pos) > __ldcg(B + (d - 1 - pos));
+    const uint32_t m = __ballot_sync(0xFFFFFFFFu, p);
+    if (m == 0) {
+      lo = lo + (span * 31) / 32 + 1;
+    } else {
+      const int fl = __ffs(m) - 1;
+      const uint64_t pf = lo + (span * fl) / 32;
+      if (fl > 0) lo = lo + (span * (fl - 1)) / 32 + 1;
+      hi = pf;
+    }
+  }
+  return lo;
+}
+
+template <typename K, bool PAIRS, int E, int NT, bool MAP>
+__device__ __forceinline__ void merge_piece_item(const SegArgs& a, const SegGeo& g,
+                                                 uint32_t pass, uint64_t rel, uint32_t* sm,
+                                                 uint64_t* s_split) {
+  constexpr uint64_t T = E * NT;  // merge tile == sort tile here
+  const uint32_t tid = threadIdx.x;
+  const uint64_t G0 = g.lo / T;
+  const uint64_t gt = G0 + rel;                 // absolute output tile
+  const uint64_t q = rel >> pass;               // pair index within the segment
+  const uint64_t half = 1ull << (pass - 1);     // tiles per input run
+  const uint64_t a0 = (G0 + (q << pass)) * T;
+  const uint64_t A0 = a0 > g.lo ? a0 : g.lo;
+  const uint64_t a1 = (G0 + (q << pass) + half) * T;
+  const uint64_t A1 = a1 < g.hi ? a1 : g.hi;
+  const uint64_t b1 = (G0 + ((q + 1) << pass)) * T;
+  const uint64_t B1 = b1 < g.hi ? b1 : g.hi;
+  const uint64_t na = A1 - A0, nb = B1 > A1 ? B1 - A1 : 0;
+  const uint64_t ps = gt * T > A0 ? gt * T : A0;
+  const uint64_t pe = (gt + 1) * T < A0 + na + nb ? (gt + 1) * T : A0 + na + nb;
+  const uint64_t d0 = ps - A0, d1 = pe - A0;
+  // pass p reads the buffer pass p-1 wrote
+  const bool src_out = ((g.passes - (pass - 1)) % 2) == 0;
+  const bool dst_out = ((g.passes - pass) % 2) == 0;
+  const K* src = static_cast<const K*>(src_out ? a.kout : a.kbuf);
+  const uint32_t* vsrc = PAIRS ? (src_out ? a.vout : a.vbuf) : nullptr;
+  const K* A = src + A0;
+  const K* B = src + A1;
+  const uint32_t w = tid >> 5;
+  if (w < 2) {
+    const uint64_t d = w == 0 ? d0 : d1;
+    const uint64_t i = (w == 1 && d1 == na + nb) ? na : warp_merge_path(A, na, B, nb, d);
+    if ((tid & 31u) == 0) s_split[w] = i;
+  }
+  __syncthreads();
+  const uint64_t i0 = s_split[0], i1 = s_split[1];
+  const uint32_t wa = static_cast<uint32_t>(i1 - i0);
+  const uint32_t wb = static_cast<uint32_t>((d1 - i1) - (d0 - i0));
+  const uint32_t front = static_cast<uint32_t>(ps - gt * T);
+  const uint32_t endA = front + wa, begB = static_cast<uint32_t>(T) - wb;
+  const uint64_t ja = A0 + i0, jb = A1 + (d0 - i0);  // first A / B window element
+  Frag<K, PAIRS, E> f;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const uint32_t k = e * NT + tid;
+    const bool isA = k >= front && k < endA, isB = k >= begB;
+    const uint64_t pos = isA ? ja + (k - front) : jb + (T - 1 - k);
+    K x = k < front ? KeyLimits<K>::kMin : KeyLimits<K>::kMax;
+    if (isA || isB) x = __ldcg(src + pos);
+    f.k[e] = x;
+    if constexpr (PAIRS) {
+      f.v[e] = (isA || isB) ? __ldcg(vsrc + pos) : 0u;
+      f.ix[e] = isB ? endA + (static_cast<uint32_t>(T) - 1 - k) : (k < endA ? k : T + k);
+    }
+  }
+  bitonic_merge_str<NT>(f, sm);
+  K* dst = static_cast<K*>(dst_out ? a.kout : a.kbuf) + gt * T;
+  uint32_t* vdst = PAIRS ? (dst_out ? a.vout : a.vbuf) + gt * T : nullptr;
+  const bool last = pass == g.passes;
+  const uint32_t cnt = static_cast<uint32_t>(pe - ps);
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const uint32_t k = tid * E + e;
+    if (k >= front && k < front + cnt) {
+      dst[k] = (MAP && last) ? unmap_key(f.k[e], a.mode) : f.k[e];
+      if constexpr (PAIRS) vdst[k] = f.v[e];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- worker
+
+__device__ __forceinline__ bool wait_ready(const SegWork* slot, uint32_t* err) {
+  const volatile uint32_t* meta = &slot->meta;
+  if (*meta & kReady) return true;
+  const uint64_t t0 = globaltimer_ns();
+  while (!(*meta & kReady)) {
+    if (globaltimer_ns() - t0 > kWaitLimitNs) {
+      atomicOr(err, kErrQueueTimeout);
+      return false;
+    }
+    __nanosleep(200);
+  }
+  return true;
+}
+
+template <typename K, bool PAIRS, int E, int NT, bool MAP>
+__global__ void __launch_bounds__(NT) seg_worker(const SegArgs a) {
+  constexpr uint32_t T = E * NT;
+  extern __shared__ __align__(16) uint32_t sm[];
+  __shared__ SegWork s_w;
+  __shared__ int s_go;
+  __shared__ uint64_t s_split[2];
+  const uint32_t tid = threadIdx.x;
+  for (;;) {
+    if (tid == 0) {
+      const unsigned long long idx = atomicAdd(&a.ctl->head, 1ull);
+      int go = 0;
+      if (idx < __ldcg(&a.ctl->total) && wait_ready(a.queue + idx, a.err)) {
+        __threadfence();
+        // the slot may have been written by another SM during this launch
+        SegWork w;
+        w.meta = *const_cast<const volatile uint32_t*>(&a.queue[idx].meta);
+        w.seg = __ldcg(&a.queue[idx].seg);
+        w.arg = __ldcg(&a.queue[idx].arg);
+        s_w = w;
+        go = 1;
+      }
+      s_go = go;
+    }
+    __syncthreads();
+    if (!s_go) return;
+    const SegWork w = s_w;
+    const uint32_t type = w.meta & 0xFFu, pass = (w.meta >> 8) & 0xFFu;
+    if (type == kWTiny) {
+      const uint64_t t = w.arg * kTinyPerGroup + (tid >> 5);
+      if ((tid >> 5) < kTinyPerGroup && t < __ldcg(&a.ctl->n_tiny)) {
+        const uint32_t s = __ldcg(a.tiny_list + t);
+        const SegGeo g = seg_geo(a.off, s, a.n, T);
+        warp_sort_segment<K, PAIRS, MAP>(a, g.lo, g.hi);
+      }
+      __syncthreads();
+      continue;
+    }
+    const SegGeo g = seg_geo(a.off, w.seg, a.n, T);
+    if (type == kWTile)
+      sort_tile_item<K, PAIRS, E, NT, MAP>(a, g, w.arg, sm);
+    else
+      merge_piece_item<K, PAIRS, E, NT, MAP>(a, g, pass, w.arg, sm, s_split);
+    __syncthreads();  // every store of this item is issued
+    if (tid == 0) {
+      __threadfence();  // ... and visible before the completion is counted
+      const uint32_t left = atomicSub(a.items_left + w.seg, 1u);
+      if (left == 1 && pass < g.passes) {
+        // last item of this pass: publish the segment's next pass
+        const uint32_t m = g.pieces;
+        a.items_left[w.seg] = m;
+        const unsigned long long base = atomicAdd(&a.ctl->reserve, static_cast<unsigned long long>(m));
+        if (base + m > a.capacity) {
+          atomicOr(a.err, kErrQueueOverflow);
+        } else {
+          for (uint32_t j = 0; j < m; ++j) {
+            a.queue[base + j].seg = w.seg;
+            a.queue[base + j].arg = j;
+          }
+          __threadfence();
+          for (uint32_t j = 0; j < m; ++j)
+            *const_cast<volatile uint32_t*>(&a.queue[base + j].meta) =
+                kReady | ((pass + 1) << 8) | kWPiece;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename K, bool PAIRS, int E, int NT, bool MAP>
+cudaError_t launch_seg(const SegArgs& a, cudaStream_t s) {
+  constexpr int W = Frag<K, PAIRS, E>::W;
+  const size_t smem = static_cast<size_t>(W) * Geo<E, NT>::kPlane * sizeof(uint32_t);
+  auto kern = seg_worker<K, PAIRS, E, NT, MAP>;
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+  if (err != cudaSuccess) return err;
+  int dev = 0, sms = 0, per_sm = 0;
+  if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
+  if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    return err;
+  if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem)) !=
+      cudaSuccess)
+    return err;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  if ((err = launch_plan(a, E * NT, s)) != cudaSuccess) return err;
+  kern<<<sms * per_sm, NT, smem, s>>>(a);  // one co-resident wave
+  return cudaGetLastError();
+}
+
+template <typename K, bool PAIRS, bool MAP>
+cudaError_t dispatch_seg(int cfg, const SegArgs& a, cudaStream_t s) {
+  switch (cfg) {
+    case 0: return launch_seg<K, PAIRS, 16, 256, MAP>(a, s);
+    case 1: return launch_seg<K, PAIRS, 16, 128, MAP>(a, s);
+    case 2:
+      if constexpr (!PAIRS && sizeof(K) == 4) return launch_seg<K, PAIRS, 32, 128, MAP>(a, s);
+      break;
+    default: break;
+  }
+  return cudaErrorInvalidValue;
+}
+
+// Launch of the persistent sort for key type K (instantiated per key type in
+// bcf_segmented_u32.cu / bcf_segmented_u64.cu so the two compile in parallel).
+template <typename K>
+cudaError_t launch_segmented_typed(bool pairs, int cfg, const SegArgs& a, cudaStream_t s) {
+  const bool map = a.mode != 0;
+  if (pairs) return map ? dispatch_seg<K, true, true>(cfg, a, s) : dispatch_seg<K, true, false>(cfg, a, s);
+  return map ? dispatch_seg<K, false, true>(cfg, a, s) : dispatch_seg<K, false, false>(cfg, a, s);
+}
+
+extern template cudaError_t launch_segmented_typed<uint32_t>(bool, int, const SegArgs&, cudaStream_t);
+extern template cudaError_t launch_segmented_typed<uint64_t>(bool, int, const SegArgs&, cudaStream_t);
+
+}  // namespace bcf

@@ -1,0 +1,142 @@
+"""Parity of bcf_segmented_sort (persistent launch, through the C ABI) with the
+oracle -- bit-exact.
+
+Segment sizes cover every class of the plan: empty, 1, tiny (<= 512 keys, one
+warp), one tile, a few tiles (one or two merge passes) and many tiles (several
+passes), at arbitrary (unaligned) offsets; keys and stable pairs, every key
+type, both directions, in place, repeated, and replayed from a CUDA graph.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from tests.gpu_util import bits, from_dev, kt_of, to_dev
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def bcf():
+    import paper_1306_5076_gb300 as m
+    from paper_1306_5076_gb300 import build
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    m._native.load()
+    return m
+
+
+def mixed_sizes(r, count):
+    """A mix of every size class, shuffled."""
+    parts = [np.zeros(count // 10, np.int64), np.ones(count // 10, np.int64),
+             r.integers(2, 513, size=count // 4), r.integers(513, 4097, size=count // 6),
+             r.integers(4097, 40000, size=count // 8), r.integers(40000, 140000, size=3)]
+    sizes = np.concatenate(parts)
+    return sizes[r.permutation(sizes.size)]
+
+
+def run(bcf, keys, offs, vals=None, descending=False, inplace=False):
+    kd = to_dev(keys)
+    vd = None if vals is None else to_dev(vals)
+    ko = kd if inplace else torch.empty_like(kd)
+    vo = None if vals is None else (vd if inplace else torch.empty_like(vd))
+    od = torch.from_numpy(offs.astype(np.int64)).to("cuda")
+    bcf.bcf_segmented_sort(ko, vo, kd, vd, od, descending=descending, kt=kt_of(keys))
+    torch.cuda.synchronize()
+    assert bcf.bcf_last_device_error() == 0
+    return from_dev(ko, keys.dtype), (None if vals is None else from_dev(vo, np.uint32))
+
+
+def check(bcf, keys, offs, vals, descending=False, inplace=False):
+    ek, ev = oracle.segmented_sort(keys, vals, offs, descending=descending)
+    gk, gv = run(bcf, keys, offs, vals, descending, inplace)
+    bad = np.flatnonzero(bits(gk) != bits(ek))
+    assert bad.size == 0, f"keys differ at {bad.size} positions, first {bad[:6]}"
+    if vals is not None:
+        assert np.array_equal(gv, ev)
+
+
+@pytest.mark.parametrize("dtype", ["u32", "u64", "f32"])
+@pytest.mark.parametrize("descending", [False, True])
+def test_mixed_size_classes(bcf, dtype, descending):
+    r = workloads.rng(31)
+    sizes = mixed_sizes(r, 400)
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
+    keys = workloads.keys("uniform" if dtype != "u32" else "gaussian", dtype, int(offs[-1]),
+                          seed=7)
+    vals = workloads.row_index(keys.size)
+    check(bcf, keys, offs, None, descending)
+    check(bcf, keys, offs, vals, descending)
+
+
+def test_ties_and_extreme_keys(bcf):
+    r = workloads.rng(32)
+    sizes = mixed_sizes(r, 300)
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
+    n = int(offs[-1])
+    keys = np.where(r.random(n) < 0.5, np.uint32(0), np.uint32(0xFFFFFFFF)).astype(np.uint32)
+    vals = workloads.row_index(n)
+    for desc in (False, True):
+        check(bcf, keys, offs, vals, desc)
+
+
+def test_one_big_segment_and_empty_edges(bcf):
+    n = (1 << 20) + 333
+    keys = workloads.keys("uniform", "u32", n, seed=8)
+    vals = workloads.row_index(n)
+    for offs in ([0, n], [0, 0, n, n], [0, 1, n - 1, n]):
+        check(bcf, keys, np.array(offs, np.uint64), vals)
+
+
+def test_log_uniform_family_scaled(bcf):
+    """The batched workload's size law (log-uniform in [1, 2^18]) on fewer segments."""
+    keys, offs = workloads.segments(1500, 1 << 18, "u32", seed=4000)
+    vals = workloads.row_index(keys.size)
+    check(bcf, keys, offs, vals)
+    check(bcf, keys, offs, None)
+
+
+def test_in_place_and_repeat(bcf):
+    r = workloads.rng(33)
+    sizes = mixed_sizes(r, 200)
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
+    keys = workloads.keys("distinct16", "u32", int(offs[-1]), seed=9)
+    vals = workloads.row_index(keys.size)
+    check(bcf, keys, offs, vals, inplace=True)
+    first = run(bcf, keys, offs, vals)
+    for _ in range(3):
+        again = run(bcf, keys, offs, vals)
+        assert np.array_equal(first[0], again[0]) and np.array_equal(first[1], again[1])
+
+
+def test_cuda_graph_replay(bcf):
+    """Captured once (after a warm-up call), replayed; every replay is exact."""
+    keys, offs = workloads.segments(800, 1 << 16, "u32", seed=4001)
+    vals = workloads.row_index(keys.size)
+    ek, ev = oracle.segmented_sort(keys, vals, offs)
+    kd, vd = to_dev(keys), to_dev(vals)
+    ko, vo = torch.empty_like(kd), torch.empty_like(vd)
+    od = torch.from_numpy(offs.astype(np.int64)).to("cuda")
+    ws = torch.empty(bcf.bcf_workspace_bytes(bcf.BCF_OP_SEGMENTED, keys.size, offs.size - 1,
+                                             bcf.BCF_U32, True), dtype=torch.uint8, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        bcf.bcf_segmented_sort(ko, vo, kd, vd, od, kt=0, ws=ws, stream=s)  # warm-up
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        bcf.bcf_segmented_sort(ko, vo, kd, vd, od, kt=0, ws=ws, stream=s)
+    for _ in range(3):
+        ko.zero_()
+        vo.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(from_dev(ko, np.uint32), ek)
+        assert np.array_equal(from_dev(vo, np.uint32), ev)
+    assert bcf.bcf_last_device_error() == 0
