@@ -175,6 +175,37 @@ bcf_status bcf_profile_collect(bcf_profile* out);
 /* Version string of the library. */
 const char* bcf_version(void);
 
+/* ---- tuning --------------------------------------------------------------- */
+
+/*
+ * Elements per thread (E) and threads per CTA (NT) of the block sort, the merge
+ * pass and the segmented sort are chosen per operation, key width, payload flag
+ * and size band from a table.  The paper fixes them by hand (Sec. 4: p = 128,
+ * M = w^2 = 1024); here the project's autotuner measures every compiled
+ * configuration on the GPU and writes the table.  Without a call to
+ * bcf_tuning_set the library reads tuning/gb300.tsv of its package (rows "op
+ * key_bytes has_vals n_min n_max block_cfg merge_cfg seg_cfg"); configurations
+ * are indices into the lists that bcf_tuning_config enumerates.  Results never
+ * depend on the tuning.
+ */
+typedef struct {
+    int op;              /* BCF_OP_SORT, BCF_OP_MERGE or BCF_OP_SEGMENTED */
+    int key_bytes;       /* 4 (u32 / f32) or 8 (u64) */
+    int has_vals;
+    uint64_t n_min, n_max; /* the row applies to n_min <= n < n_max */
+    int block_cfg, merge_cfg, seg_cfg;
+} bcf_tuning_entry;
+
+/* Replace the table (count 0: built-in defaults; count -1: the package's table
+ * file again).  BCF_EINVAL if a row names an unsupported configuration; the
+ * table is then left unchanged. */
+bcf_status bcf_tuning_set(const bcf_tuning_entry* entries, int count);
+/* Configuration `index` of kind 0 (block sort), 1 (merge) or 2 (segmented):
+ * returns 1 and its E and NT, or 0 past the end of the list. */
+int bcf_tuning_config(int kind, int index, int* elems_per_thread, int* threads);
+/* 1 if configuration `index` of `kind` is built for that key width / payload. */
+int bcf_tuning_supported(int kind, int index, int key_bytes, int has_vals);
+
 /* ---- sort without a caller workspace ------------------------------------ */
 
 /*

@@ -20,7 +20,8 @@ from ._native import BCF_F32, BCF_OP_MERGE, BCF_OP_SEGMENTED, BCF_OP_SORT, BCF_U
 __all__ = [
     "BcfError", "bcf_workspace_bytes", "bcf_sort_keys", "bcf_sort_pairs", "bcf_merge_runs",
     "bcf_segmented_sort", "bcf_last_device_error", "bcf_sort_plan", "bcf_profile_enable",
-    "bcf_profile_collect", "bcf_version", "bcf_sort_keys_static", "key_dtype_of", "BCF_U32",
+    "bcf_profile_collect", "bcf_version", "bcf_sort_keys_static", "bcf_tuning_set",
+    "bcf_tuning_config", "bcf_tuning_supported", "key_dtype_of", "BCF_U32",
     "BCF_U64", "BCF_F32",
     "BCF_OP_SORT", "BCF_OP_MERGE", "BCF_OP_SEGMENTED",
 ]
@@ -170,6 +171,32 @@ def bcf_sort_keys_static(keys_out, keys_in, *, descending=False, stream=None, kt
                                                kt, _opts(descending), _stream(stream)),
            "bcf_sort_keys_static")
     return keys_out
+
+
+def bcf_tuning_set(entries) -> None:
+    """Install a tuning table: a list of dicts with the fields of bcf_tuning_entry
+    ([] -> built-in defaults, None -> the package's table file again)."""
+    lib = _native.load()
+    if entries is None:
+        _check(lib.bcf_tuning_set(None, -1), "bcf_tuning_set")
+        return
+    arr = (_native.BcfTuningEntry * max(len(entries), 1))()
+    for i, e in enumerate(entries):
+        for k, v in e.items():
+            setattr(arr[i], k, v)
+    _check(lib.bcf_tuning_set(arr, len(entries)), "bcf_tuning_set")
+
+
+def bcf_tuning_config(kind: int, index: int):
+    """(E, NT) of configuration `index` of kind 0 block / 1 merge / 2 segmented, or None."""
+    e, t = ctypes.c_int(), ctypes.c_int()
+    if not _native.load().bcf_tuning_config(kind, index, ctypes.byref(e), ctypes.byref(t)):
+        return None
+    return e.value, t.value
+
+
+def bcf_tuning_supported(kind: int, index: int, key_bytes: int, has_vals: bool) -> bool:
+    return bool(_native.load().bcf_tuning_supported(kind, index, key_bytes, int(bool(has_vals))))
 
 
 def bcf_version() -> str:

@@ -28,6 +28,12 @@ class BcfPlan(ctypes.Structure):
                 ("bytes_per_pass", ctypes.c_uint64)]
 
 
+class BcfTuningEntry(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int), ("key_bytes", ctypes.c_int), ("has_vals", ctypes.c_int),
+                ("n_min", ctypes.c_uint64), ("n_max", ctypes.c_uint64),
+                ("block_cfg", ctypes.c_int), ("merge_cfg", ctypes.c_int), ("seg_cfg", ctypes.c_int)]
+
+
 class BcfProfile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_uint32 * 4), ("total_ms", ctypes.c_double * 4)]
 
@@ -51,6 +57,9 @@ SIGNATURES = {
     "bcf_profile_collect": (_i32, [ctypes.POINTER(BcfProfile)]),
     "bcf_version": (ctypes.c_char_p, []),
     "bcf_sort_keys_static": (_i32, [_vp, _vp, _u64, _i32, ctypes.POINTER(BcfOpts), _vp]),
+    "bcf_tuning_set": (_i32, [ctypes.POINTER(BcfTuningEntry), _i32]),
+    "bcf_tuning_config": (_i32, [_i32, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
+    "bcf_tuning_supported": (_i32, [_i32, _i32, _i32, _i32]),
 }
 
 # keys per call accepted by bcf_sort_keys_static (BCF_STATIC_MAX_KEYS)

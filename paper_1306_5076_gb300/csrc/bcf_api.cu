@@ -9,10 +9,14 @@
 // when last written, so intermediate passes compare plain unsigned integers.
 #include <cuda_runtime.h>
 
+#include <dlfcn.h>
+
 #include <algorithm>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "bcf_internal.h"
@@ -38,31 +42,86 @@ int mode_of(bcf_dtype kt, const bcf_opts* o) {
 }
 
 // ---------------------------------------------------------------- tuning
+//
+// (E, NT) per operation, key width, payload flag and size band come from a
+// table: bcf_tuning_set() installs one; otherwise the first call reads the
+// committed table "tuning/gb300.tsv" next to the package directory of this
+// library (written by the project's autotuner, paper_1306_5076_gb300/autotune.py),
+// and without a table the built-in defaults below apply.
 
 struct Tuning {
   int block_cfg, merge_cfg;
 };
 
-// Default (E, NT) per key width and payload flag; indices into kBlockCfgs /
-// kMergeCfgs.  Overridable with BCF_BLOCK_CFG / BCF_MERGE_CFG (integers) for
-// sweeps.
-Tuning default_tuning(int kb, bool pairs) {
-  Tuning t;
-  if (kb == 4 && !pairs) t = {1, 3};  // T = 8192 (32 x 256), Tm = 2048 (16 x 128)
-  else t = {0, 3};                    // pairs, 64-bit keys: T = 4096 (16 x 256), Tm = 2048
-  static const char* eb = std::getenv("BCF_BLOCK_CFG");
-  static const char* em = std::getenv("BCF_MERGE_CFG");
-  if (eb) {
-    const int c = std::atoi(eb);
-    if (block_cfg_supported(kb, pairs, c)) t.block_cfg = c;
-  }
-  if (em) {
-    const int c = std::atoi(em);
-    if (merge_cfg_supported(kb, pairs, c)) t.merge_cfg = c;
-  }
-  // a merge tile never exceeds two block tiles (pairs of runs are multiples of it)
-  if (kMergeCfgs[t.merge_cfg].tile() > 2 * kBlockCfgs[t.block_cfg].tile()) t.merge_cfg = 0;
+struct TuneTable {
+  std::mutex mu;
+  bool loaded = false;
+  std::vector<bcf_tuning_entry> rows;
+};
+TuneTable& tune_table() {
+  static TuneTable t;
   return t;
+}
+
+bool entry_ok(const bcf_tuning_entry& e) {
+  const bool pairs = e.has_vals != 0;
+  if (e.key_bytes != 4 && e.key_bytes != 8) return false;
+  if (e.n_max <= e.n_min) return false;
+  if (e.op == BCF_OP_SORT || e.op == BCF_OP_MERGE) {
+    if (!block_cfg_supported(e.key_bytes, pairs, e.block_cfg)) return false;
+    if (!merge_cfg_supported(e.key_bytes, pairs, e.merge_cfg)) return false;
+    return kMergeCfgs[e.merge_cfg].tile() <= 2 * kBlockCfgs[e.block_cfg].tile();
+  }
+  if (e.op == BCF_OP_SEGMENTED) return seg_cfg_supported(e.key_bytes, pairs, e.seg_cfg);
+  return false;
+}
+
+// Table file: '#' comments; rows "op key_bytes has_vals n_min n_max block merge seg".
+void load_table_file(std::vector<bcf_tuning_entry>& rows) {
+  Dl_info info{};
+  if (!dladdr(reinterpret_cast<void*>(&load_table_file), &info) || !info.dli_fname) return;
+  std::string path(info.dli_fname);
+  const size_t slash = path.rfind('/');
+  if (slash == std::string::npos) return;
+  path = path.substr(0, slash) + "/../tuning/gb300.tsv";  // <pkg>/_build/lib -> <pkg>/tuning
+  FILE* f = std::fopen(path.c_str(), "r");
+  if (!f) return;
+  char line[512];
+  while (std::fgets(line, sizeof line, f)) {
+    if (line[0] == '#' || line[0] == '\n') continue;
+    bcf_tuning_entry e{};
+    unsigned long long lo = 0, hi = 0;
+    if (std::sscanf(line, "%d %d %d %llu %llu %d %d %d", &e.op, &e.key_bytes, &e.has_vals, &lo,
+                    &hi, &e.block_cfg, &e.merge_cfg, &e.seg_cfg) == 8) {
+      e.n_min = lo;
+      e.n_max = hi;
+      if (entry_ok(e)) rows.push_back(e);
+    }
+  }
+  std::fclose(f);
+}
+
+const bcf_tuning_entry* find_entry(int op, int kb, bool pairs, uint64_t n) {
+  TuneTable& t = tune_table();
+  std::lock_guard<std::mutex> lk(t.mu);
+  if (!t.loaded) {
+    load_table_file(t.rows);
+    t.loaded = true;
+  }
+  for (const auto& e : t.rows)
+    if (e.op == op && e.key_bytes == kb && (e.has_vals != 0) == pairs && n >= e.n_min &&
+        n < e.n_max)
+      return &e;
+  return nullptr;
+}
+
+// Built-in defaults (measured on GB300 at 2^28 keys): u32 keys-only use
+// 8192-key block tiles (32 x 256) and 2048-key merge tiles (16 x 128); pairs
+// and 64-bit keys use 4096-key block tiles (16 x 256).
+Tuning tuning_for(int op, int kb, bool pairs, uint64_t n) {
+  if (const bcf_tuning_entry* e = find_entry(op, kb, pairs, n)) return {e->block_cfg, e->merge_cfg};
+  if (kb == 4 && !pairs) return {1, 3};
+  return {0, 3};
 }
 
 struct Plan {
@@ -70,9 +129,9 @@ struct Plan {
   uint32_t T, Tm, passes;
 };
 
-Plan make_plan(uint64_t n, int kb, bool pairs) {
+Plan make_plan(uint64_t n, int kb, bool pairs, int op = BCF_OP_SORT) {
   Plan p;
-  p.tune = default_tuning(kb, pairs);
+  p.tune = tuning_for(op, kb, pairs, n);
   p.T = kBlockCfgs[p.tune.block_cfg].tile();
   p.Tm = kMergeCfgs[p.tune.merge_cfg].tile();
   p.passes = 0;
@@ -126,16 +185,9 @@ SegLayout seg_layout(uint64_t n, uint64_t nseg, int kb, bool pairs) {
   return w;
 }
 
-int default_seg_cfg(int kb, bool pairs) {
-  (void)kb;
-  (void)pairs;
-  int c = 0;  // 16 x 256: 4096-key tiles
-  static const char* es = std::getenv("BCF_SEG_CFG");
-  if (es) {
-    const int v = std::atoi(es);
-    if (seg_cfg_supported(kb, pairs, v)) c = v;
-  }
-  return c;
+int seg_cfg_for(int kb, bool pairs, uint64_t n) {
+  if (const bcf_tuning_entry* e = find_entry(BCF_OP_SEGMENTED, kb, pairs, n)) return e->seg_cfg;
+  return 0;  // 16 x 256: 4096-key tiles
 }
 
 // ---------------------------------------------------------------- device error word
@@ -332,7 +384,7 @@ bcf_status run_merge(void* ko, uint32_t* vo, const void* ki, const uint32_t* vi,
   const int mode = mode_of(kt, o);
   uint32_t* err = error_word_ptr();
   if (!err) return BCF_ECUDA;
-  const Plan plan = make_plan(n, kb, pairs);
+  const Plan plan = make_plan(n, kb, pairs, BCF_OP_MERGE);
   const uint64_t Tm = plan.Tm;
   const uint64_t lo = offs[0], span = offs[k] - offs[0];
 
@@ -463,7 +515,7 @@ bcf_status run_segmented(void* ko, uint32_t* vo, const void* ki, const uint32_t*
   // unpublished queue slots must read "not ready"
   if (cudaMemsetAsync(L.queue, 0, wl.capacity * seg_work_bytes(), s) != cudaSuccess)
     return BCF_ECUDA;
-  const int cfg = default_seg_cfg(kb, pairs);
+  const int cfg = seg_cfg_for(kb, pairs, n);
   const cudaError_t e = timed(3, s, [&] { return launch_segmented(kb, pairs, cfg, L, s); });
   return from_cuda(e);
 }
@@ -582,5 +634,41 @@ bcf_status bcf_profile_collect(bcf_profile* out) {
 }
 
 const char* bcf_version(void) { return "bcfsort 0.1 (sm_103a)"; }
+
+bcf_status bcf_tuning_set(const bcf_tuning_entry* entries, int count) {
+  if (count == -1) {  // back to the package's table file, read again on next use
+    TuneTable& t = tune_table();
+    std::lock_guard<std::mutex> lk(t.mu);
+    t.rows.clear();
+    t.loaded = false;
+    return BCF_OK;
+  }
+  if (count < 0 || (count > 0 && !entries)) return BCF_EINVAL;
+  for (int i = 0; i < count; ++i)
+    if (!entry_ok(entries[i])) return BCF_EINVAL;
+  TuneTable& t = tune_table();
+  std::lock_guard<std::mutex> lk(t.mu);
+  t.rows.assign(entries, entries + count);
+  t.loaded = true;
+  return BCF_OK;
+}
+
+int bcf_tuning_config(int kind, int index, int* elems_per_thread, int* threads) {
+  const TileCfg* tab = kind == 0 ? kBlockCfgs : kind == 1 ? kMergeCfgs : kind == 2 ? kSegCfgs : nullptr;
+  const int count = kind == 0 ? kNumBlockCfgs : kind == 1 ? kNumMergeCfgs : kind == 2 ? kNumSegCfgs : 0;
+  if (!tab || index < 0 || index >= count) return 0;
+  if (elems_per_thread) *elems_per_thread = tab[index].E;
+  if (threads) *threads = tab[index].NT;
+  return 1;
+}
+
+int bcf_tuning_supported(int kind, int index, int key_bytes, int has_vals) {
+  switch (kind) {
+    case 0: return block_cfg_supported(key_bytes, has_vals != 0, index) ? 1 : 0;
+    case 1: return merge_cfg_supported(key_bytes, has_vals != 0, index) ? 1 : 0;
+    case 2: return seg_cfg_supported(key_bytes, has_vals != 0, index) ? 1 : 0;
+    default: return 0;
+  }
+}
 
 }  // extern "C"

@@ -125,3 +125,23 @@ def test_workspace_too_small_is_enomem(lib):
     n = 1 << 20  # needs merge passes, hence a workspace
     assert lib.bcf_sort_keys(ctypes.c_void_p(0x100000000), ctypes.c_void_p(0x200000000), n, 0,
                              opts, ctypes.c_void_p(0x300000000), 1024, None) == 2
+
+
+def test_committed_tuning_table_rows_are_valid(lib):
+    """Every row of the package's tuning table names a built configuration."""
+    import paper_1306_5076_gb300 as bcf
+
+    path = os.path.join(ROOT, "paper_1306_5076_gb300", "tuning", "gb300.tsv")
+    rows = []
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            op, kb, hv, lo, hi, b, m, s = (int(x) for x in line.split())
+            rows.append(dict(op=op, key_bytes=kb, has_vals=hv, n_min=lo, n_max=hi, block_cfg=b,
+                             merge_cfg=m, seg_cfg=s))
+    assert rows
+    for r in rows:
+        bcf.bcf_tuning_set([r])  # raises BcfError(EINVAL) for an unbuilt configuration
+    bcf.bcf_tuning_set(None)
+    with pytest.raises(bcf.BcfError):
+        bcf.bcf_tuning_set([dict(op=0, key_bytes=4, has_vals=1, n_min=0, n_max=10, block_cfg=1,
+                                 merge_cfg=0, seg_cfg=0)])  # E = 32 is not built for pairs
