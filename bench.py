@@ -214,6 +214,67 @@ def run_reference(args, world, rank):
     return 0
 
 
+def serving_bench(torch, dev, seconds, rate=2000.0, seed=5000):
+    """Served (continuous batching) vs plain (one launch chain per request,
+    FIFO) on the same open-loop Poisson trace: sizes log-uniform in
+    [2^8, 2^24] u32 keys, 30 % with u32 payloads, arena 40 GB.  Inputs are
+    slices of a pool resident in HBM outside the arena; outputs go to a pool
+    managed with the library's allocator.  Latency = completion observed by
+    the server - scheduled arrival."""
+    import numpy as np
+
+    import workloads
+    from paper_1306_5076_gb300 import serve
+
+    tr = workloads.request_trace(rate_hz=rate, duration_s=seconds, seed=seed)
+    t, sizes, pairs = tr["t"], tr["n"], tr["pairs"]
+    pool = 1 << 27
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    kin = torch.randint(-2**31, 2**31 - 1, (pool,), dtype=torch.int32, device=dev, generator=g)
+    vin = torch.arange(pool, dtype=torch.int32, device=dev)
+    out_keys = 1 << 28
+    kout = torch.empty(out_keys, dtype=torch.int32, device=dev)
+    vout = torch.empty(out_keys, dtype=torch.int32, device=dev)
+    arena = torch.empty(40 << 30, dtype=torch.uint8, device=dev)
+    res = {}
+    for name, mode in (("served", serve.BCF_SERVE_BATCHED), ("plain", serve.BCF_SERVE_PLAIN)):
+        torch.cuda.synchronize()
+        srv = serve.Server(arena, mode=mode, streams=4, small_max=1 << 16)
+        outs = serve.Arena(out_keys * 4)
+        held = {}
+
+        def make(i):
+            n = int(sizes[i])
+            off = outs.alloc(n * 4)
+            if off is None:
+                return None  # output pool full: the request waits (its latency counts)
+            held[i] = off
+            src = ((i * 2654435761) % (pool - n)) & ~3
+            kw = dict(kt=0, n=n, keys_in=kin[src:].data_ptr(), keys_out=kout.data_ptr() + off)
+            if pairs[i]:
+                kw.update(vals_in=vin[src:].data_ptr(), vals_out=vout.data_ptr() + off)
+            return kw
+
+        def release(i):
+            outs.free(held.pop(i), int(sizes[i]) * 4)
+
+        r = serve.replay(srv, list(t), make, release)
+        srv.close()
+        outs.close()
+        keys = float(sizes.sum())
+        res[name] = {"p50_ms": r["p50_s"] * 1e3, "p99_ms": r["p99_s"] * 1e3,
+                     "mean_ms": r["mean_s"] * 1e3, "keys_per_s": keys / r["span_s"],
+                     "span_s": r["span_s"], "launch_units": r["stats"]["launched_units"],
+                     "coalesced_batches": r["stats"]["launched_batches"],
+                     "arena_peak_gb": r["stats"]["arena_peak"] / 1e9,
+                     "errors": int(sum(1 for x in r["status"] if x != 0))}
+    del arena, kin, vin, kout, vout
+    return {"trace": f"Poisson {rate:g} req/s for {seconds:g} s, {len(t)} requests, "
+                     "sizes log-uniform [2^8, 2^24] u32, 30 % pairs, seed 5000",
+            "offered_keys_per_s": float(sizes.sum()) / seconds, **res}
+
+
 def run_gpu(args, world, rank, local, pg):
     import numpy as np
     import torch
@@ -304,6 +365,11 @@ def run_gpu(args, world, rank, local, pg):
         e2e_ms = float(t.item())
     ok_e2e = bool(torch.equal(host_out, ko.cpu()))
 
+    serving = None
+    if args.serve_seconds > 0:
+        del ws
+        serving = serving_bench(torch, dev, args.serve_seconds)
+
     if rank != 0:
         return 0
     peak, peak_kind = measured_peaks()
@@ -356,6 +422,8 @@ def run_gpu(args, world, rank, local, pg):
     }
     if cpu is not None:
         line["cpu_baseline"] = cpu
+    if serving is not None:
+        line["serving"] = serving
     print(json.dumps(line))
     return 0
 
@@ -367,6 +435,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
+                    help="length of the served-vs-plain request trace (0: skip)")
     ap.add_argument("--log2n", type=int, default=LOG2N,
                     help="keys = 2^log2n (default 28, the benchmark workload; smaller values "
                          "are for ncu captures)")

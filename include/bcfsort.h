@@ -206,6 +206,93 @@ int bcf_tuning_config(int kind, int index, int* elems_per_thread, int* threads);
 /* 1 if configuration `index` of `kind` is built for that key width / payload. */
 int bcf_tuning_supported(int kind, int index, int key_bytes, int has_vals);
 
+/* ---- continuous-batching request server ---------------------------------- */
+
+/*
+ * A request server for sort and merge requests (the paper measures one sort at
+ * a time, Sec. 4; serving many requests is this library's extension).  The
+ * caller provides a device arena and drives the server from ONE host thread:
+ * bcf_server_submit() queues requests, bcf_server_step() reaps finished work
+ * (event polling, no blocking), frees its arena space and admits queued
+ * requests by memory, bcf_server_poll() returns completion records.
+ *
+ * BCF_SERVE_BATCHED (continuous batching): requests of at most small_max keys
+ * are coalesced -- per key type, order and payload flag -- into one segmented
+ * sort over a packed batch in the arena (a merge of sorted runs equals the
+ * stable sort of their concatenation, so small merges batch too); larger
+ * requests run as their own sort / merge with the workspace in the arena,
+ * round-robin over `streams` streams.  Requests that arrive while others are
+ * on the GPU are admitted on the next step as memory frees up; small requests
+ * may overtake a large one that does not fit yet.
+ * BCF_SERVE_PLAIN (baseline): each request is its own launch chain, in arrival
+ * order, on one stream.
+ * Results are the same in both modes and the same as a call on its own.
+ */
+typedef struct bcf_server bcf_server;
+enum { BCF_SERVE_BATCHED = 0, BCF_SERVE_PLAIN = 1 };
+
+typedef struct {
+    void* arena;             /* device memory owned by the caller, 256-byte aligned */
+    uint64_t arena_bytes;
+    int streams;             /* parallel streams in batched mode (1..64) */
+    int mode;                /* BCF_SERVE_BATCHED or BCF_SERVE_PLAIN */
+    uint64_t small_max;      /* requests up to this many keys are coalesced */
+    uint64_t batch_max_keys; /* keys per coalesced launch (0: 2^22) */
+} bcf_server_config;
+
+typedef struct {
+    int op;                  /* BCF_OP_SORT or BCF_OP_MERGE */
+    bcf_dtype kt;
+    int descending;
+    uint64_t n;
+    const void* keys_in;     /* device, caller-owned; must stay valid until completion */
+    const uint32_t* vals_in; /* NULL for keys only (then vals_out NULL too) */
+    void* keys_out;          /* device, caller-owned, n keys */
+    uint32_t* vals_out;
+    const uint64_t* run_offsets; /* merge: host, k+1 offsets from 0 to n (copied on submit) */
+    uint32_t k;
+    uint64_t tag;            /* returned in the completion record */
+} bcf_request;
+
+typedef struct {
+    uint64_t tag;
+    bcf_status status;
+    double submit_s, admit_s, done_s; /* server clock (bcf_server_now) */
+} bcf_completion;
+
+typedef struct {
+    uint64_t pending, inflight, arena_used, arena_peak, launched_units, launched_batches;
+} bcf_server_stats_t;
+
+/* Create: streams and a pinned staging ring are created here (set-up, not the
+ * request path).  BCF_EINVAL for a bad config. */
+bcf_status bcf_server_create(const bcf_server_config* cfg, bcf_server** out);
+/* Seconds since the server was created (steady clock). */
+double bcf_server_now(const bcf_server* s);
+/* Queue a request (host bookkeeping only).  BCF_EINVAL for a malformed request,
+ * BCF_ENOMEM if it can never fit in the arena. */
+bcf_status bcf_server_submit(bcf_server* s, const bcf_request* r);
+/* Reap finished work, admit and launch queued requests; *inflight (may be
+ * NULL) gets the number of launch units still on the GPU.  Never blocks. */
+bcf_status bcf_server_step(bcf_server* s, int* inflight);
+/* Move up to max completion records into out; returns how many. */
+int bcf_server_poll(bcf_server* s, bcf_completion* out, int max);
+bcf_status bcf_server_stats(const bcf_server* s, bcf_server_stats_t* out);
+/* Block until every submitted request completed. */
+bcf_status bcf_server_drain(bcf_server* s);
+bcf_status bcf_server_destroy(bcf_server* s);
+
+/* The server's arena allocator on its own: first fit over [0, bytes) with a
+ * coalescing free list, 256-byte granules.  Host bookkeeping only (no device
+ * memory), exported for testing; bcf_arena_free takes back exactly a range
+ * that bcf_arena_alloc returned. */
+typedef struct bcf_arena bcf_arena;
+bcf_status bcf_arena_create(uint64_t bytes, bcf_arena** out);
+bcf_status bcf_arena_alloc(bcf_arena* a, uint64_t bytes, uint64_t* offset);
+bcf_status bcf_arena_free(bcf_arena* a, uint64_t offset, uint64_t bytes);
+bcf_status bcf_arena_usage(const bcf_arena* a, uint64_t* used, uint64_t* largest_free);
+bcf_status bcf_arena_destroy(bcf_arena* a);
+
 /* ---- sort without a caller workspace ------------------------------------ */
 
 /*

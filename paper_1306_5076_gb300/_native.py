@@ -38,6 +38,33 @@ class BcfProfile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_uint32 * 4), ("total_ms", ctypes.c_double * 4)]
 
 
+BCF_SERVE_BATCHED, BCF_SERVE_PLAIN = 0, 1
+
+
+class BcfServerConfig(ctypes.Structure):
+    _fields_ = [("arena", ctypes.c_void_p), ("arena_bytes", ctypes.c_uint64),
+                ("streams", ctypes.c_int), ("mode", ctypes.c_int),
+                ("small_max", ctypes.c_uint64), ("batch_max_keys", ctypes.c_uint64)]
+
+
+class BcfRequest(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int), ("kt", ctypes.c_int), ("descending", ctypes.c_int),
+                ("n", ctypes.c_uint64), ("keys_in", ctypes.c_void_p), ("vals_in", ctypes.c_void_p),
+                ("keys_out", ctypes.c_void_p), ("vals_out", ctypes.c_void_p),
+                ("run_offsets", ctypes.c_void_p), ("k", ctypes.c_uint32), ("tag", ctypes.c_uint64)]
+
+
+class BcfCompletion(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_uint64), ("status", ctypes.c_int), ("submit_s", ctypes.c_double),
+                ("admit_s", ctypes.c_double), ("done_s", ctypes.c_double)]
+
+
+class BcfServerStats(ctypes.Structure):
+    _fields_ = [("pending", ctypes.c_uint64), ("inflight", ctypes.c_uint64),
+                ("arena_used", ctypes.c_uint64), ("arena_peak", ctypes.c_uint64),
+                ("launched_units", ctypes.c_uint64), ("launched_batches", ctypes.c_uint64)]
+
+
 # name -> (restype, argtypes); the exported symbol set of include/bcfsort.h
 _vp, _u64, _u32, _i32, _sz = (ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int,
                                ctypes.c_size_t)
@@ -60,6 +87,19 @@ SIGNATURES = {
     "bcf_tuning_set": (_i32, [ctypes.POINTER(BcfTuningEntry), _i32]),
     "bcf_tuning_config": (_i32, [_i32, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "bcf_tuning_supported": (_i32, [_i32, _i32, _i32, _i32]),
+    "bcf_server_create": (_i32, [ctypes.POINTER(BcfServerConfig), ctypes.POINTER(_vp)]),
+    "bcf_server_now": (ctypes.c_double, [_vp]),
+    "bcf_server_submit": (_i32, [_vp, ctypes.POINTER(BcfRequest)]),
+    "bcf_server_step": (_i32, [_vp, ctypes.POINTER(_i32)]),
+    "bcf_server_poll": (_i32, [_vp, ctypes.POINTER(BcfCompletion), _i32]),
+    "bcf_server_stats": (_i32, [_vp, ctypes.POINTER(BcfServerStats)]),
+    "bcf_server_drain": (_i32, [_vp]),
+    "bcf_server_destroy": (_i32, [_vp]),
+    "bcf_arena_create": (_i32, [_u64, ctypes.POINTER(_vp)]),
+    "bcf_arena_alloc": (_i32, [_vp, _u64, ctypes.POINTER(_u64)]),
+    "bcf_arena_free": (_i32, [_vp, _u64, _u64]),
+    "bcf_arena_usage": (_i32, [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64)]),
+    "bcf_arena_destroy": (_i32, [_vp]),
 }
 
 # keys per call accepted by bcf_sort_keys_static (BCF_STATIC_MAX_KEYS)

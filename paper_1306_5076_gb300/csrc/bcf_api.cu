@@ -174,7 +174,7 @@ SegLayout seg_layout(uint64_t n, uint64_t nseg, int kb, bool pairs) {
   const uint64_t tiles = n / kMinSegTile + 2 * nseg + 2;
   uint64_t passes = 1;
   while ((1ull << passes) < tiles) ++passes;
-  w.capacity = tiles * (1 + passes) + nseg / 8 + 2;
+  w.capacity = tiles * (1 + passes) + nseg / 4 + 2;  // tiny groups: >= 4 per item
   w.ctl = kAlign;
   w.items = align_up(w.ctl + seg_ctl_bytes(), kAlign);
   w.tiny = align_up(w.items + nseg * 4, kAlign);

@@ -10,7 +10,7 @@
 //            the segment, ragged ends padded), then merged pairwise with
 //            ceil(log2 tiles) segment-local merge passes (Sec. 3.2; Lemma 2).
 // The plan publishes the first-phase work items in a device queue: all tile
-// sorts, then tiny groups of 8 segments (one warp each).
+// sorts, then groups of tiny segments (one per warp of the worker CTA).
 //
 // Execution (seg_worker, persistent: one wave of co-resident CTAs): each CTA
 // repeatedly takes the next queue slot.  When the last item of a segment's
@@ -60,7 +60,8 @@ __device__ __forceinline__ T block_scan_incl(T v, T* warp_sums, T& total) {
   return v;
 }
 
-__global__ void __launch_bounds__(1024) plan_kernel(const SegArgs a, uint32_t T) {
+__global__ void __launch_bounds__(1024) plan_kernel(const SegArgs a, uint32_t T,
+                                                    uint32_t per_group) {
   __shared__ unsigned long long ws[32];
   unsigned long long carry_tiles = 0, carry_tiny = 0, carry_total = 0;
   for (uint64_t c = 0; c < a.nseg; c += 1024) {
@@ -97,7 +98,7 @@ __global__ void __launch_bounds__(1024) plan_kernel(const SegArgs a, uint32_t T)
     carry_tiny += sum_tiny;
     carry_total += sum_tot;
   }
-  const unsigned long long groups = (carry_tiny + kTinyPerGroup - 1) / kTinyPerGroup;
+  const unsigned long long groups = (carry_tiny + per_group - 1) / per_group;
   for (unsigned long long q = threadIdx.x; q < groups; q += blockDim.x) {
     if (carry_tiles + q < a.capacity) {
       SegWork w;
@@ -117,8 +118,8 @@ __global__ void __launch_bounds__(1024) plan_kernel(const SegArgs a, uint32_t T)
   }
 }
 
-cudaError_t launch_plan(const SegArgs& a, uint32_t T, cudaStream_t s) {
-  plan_kernel<<<1, 1024, 0, s>>>(a, T);
+cudaError_t launch_plan(const SegArgs& a, uint32_t T, uint32_t tiny_per_group, cudaStream_t s) {
+  plan_kernel<<<1, 1024, 0, s>>>(a, T, tiny_per_group);
   return cudaGetLastError();
 }
 

@@ -10,7 +10,7 @@
 namespace bcf {
 
 constexpr uint32_t kTinyMax = 512;      // keys per tiny segment (32 lanes x 16)
-constexpr uint32_t kTinyPerGroup = 8;   // tiny segments per work item (one per warp)
+// tiny segments per work item: one per warp of the worker CTA (NT / 32)
 constexpr uint32_t kErrQueueTimeout = 2u;
 constexpr uint32_t kErrQueueOverflow = 4u;
 
@@ -77,7 +77,7 @@ struct SegArgs {
 };
 
 // The plan kernel lives in bcf_segmented.cu.
-cudaError_t launch_plan(const SegArgs& a, uint32_t T, cudaStream_t s);
+cudaError_t launch_plan(const SegArgs& a, uint32_t T, uint32_t tiny_per_group, cudaStream_t s);
 
 // ---------------------------------------------------------------- tiny segments
 
@@ -359,8 +359,9 @@ __global__ void __launch_bounds__(NT) seg_worker(const SegArgs a) {
     const SegWork w = s_w;
     const uint32_t type = w.meta & 0xFFu, pass = (w.meta >> 8) & 0xFFu;
     if (type == kWTiny) {
-      const uint64_t t = w.arg * kTinyPerGroup + (tid >> 5);
-      if ((tid >> 5) < kTinyPerGroup && t < __ldcg(&a.ctl->n_tiny)) {
+      constexpr uint32_t kPerGroup = NT / 32;
+      const uint64_t t = w.arg * kPerGroup + (tid >> 5);
+      if (t < __ldcg(&a.ctl->n_tiny)) {
         const uint32_t s = __ldcg(a.tiny_list + t);
         const SegGeo g = seg_geo(a.off, s, a.n, T);
         warp_sort_segment<K, PAIRS, MAP>(a, g.lo, g.hi);
@@ -416,7 +417,7 @@ cudaError_t launch_seg(const SegArgs& a, cudaStream_t s) {
       cudaSuccess)
     return err;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  if ((err = launch_plan(a, E * NT, s)) != cudaSuccess) return err;
+  if ((err = launch_plan(a, E * NT, NT / 32, s)) != cudaSuccess) return err;
   kern<<<sms * per_sm, NT, smem, s>>>(a);  // one co-resident wave
   return cudaGetLastError();
 }

@@ -55,7 +55,7 @@ def piece_item(lo, hi, T, p, rel):
     return A0, A1, na, nb, ps, pe, ps - A0, pe - A0, gt
 
 
-def simulate(offs, keys, T):
+def simulate(offs, keys, T, per_group=8):
     out = keys.copy()
     buf = np.zeros_like(keys)
     total_items = 0
@@ -94,12 +94,12 @@ def simulate(offs, keys, T):
                 executed += 1
             assert np.all(covered == 1), "pieces do not tile the segment exactly once"
         assert np.array_equal(out[lo:hi], np.sort(keys[lo:hi]))
-    groups = -(-ntiny // 8)
+    groups = -(-ntiny // per_group)  # one tiny segment per warp of the worker CTA
     return out, total_items + groups, executed + groups
 
 
-@pytest.mark.parametrize("T", [2048, 4096])
-def test_schedule_sorts_every_segment(T):
+@pytest.mark.parametrize("T,per_group", [(2048, 4), (4096, 8), (4096, 4)])
+def test_schedule_sorts_every_segment(T, per_group):
     r = np.random.default_rng(T)
     for trial in range(4):
         sizes = np.concatenate([np.zeros(5, np.int64), np.ones(5, np.int64),
@@ -108,18 +108,20 @@ def test_schedule_sorts_every_segment(T):
         sizes = sizes[r.permutation(sizes.size)]
         offs = np.concatenate([[0], np.cumsum(sizes)])
         keys = r.integers(0, 1000, size=int(offs[-1]))
-        out, planned, executed = simulate(offs, keys, T)
+        out, planned, executed = simulate(offs, keys, T, per_group)
         assert planned == executed
 
 
 def test_queue_capacity_bound_holds():
-    """The host's queue bound (tiles <= n/2048 + 2*nseg + 2, times 1 + passes)
-    covers the plan's item count for adversarial size mixes."""
+    """The host's queue bound (tiles <= n/2048 + 2*nseg + 2, times 1 + passes,
+    plus tiny groups of at least 4) covers the plan's item count, including a
+    batch of nothing but tiny segments."""
     r = np.random.default_rng(5)
     for T in (2048, 4096):
         for _ in range(20):
             nseg = int(r.integers(1, 300))
-            sizes = r.integers(0, 200000, size=nseg)
+            hi = 600 if _ % 4 == 0 else 200000  # every fourth mix: (almost) all tiny
+            sizes = r.integers(0, hi, size=nseg)
             offs = np.concatenate([[0], np.cumsum(sizes)])
             n = int(offs[-1])
             items = 0
@@ -128,8 +130,8 @@ def test_queue_capacity_bound_holds():
                 tiny, tiles, passes, pieces = seg_geo(int(offs[s]), int(offs[s + 1]), T)
                 ntiny += tiny
                 items += tiles + passes * pieces
-            items += -(-ntiny // 8)
+            items += -(-ntiny // 4)
             tiles_bound = n // 2048 + 2 * nseg + 2
             passes_bound = max(1, ceil_log2(tiles_bound))
-            capacity = tiles_bound * (1 + passes_bound) + nseg // 8 + 2
+            capacity = tiles_bound * (1 + passes_bound) + nseg // 4 + 2
             assert items <= capacity
