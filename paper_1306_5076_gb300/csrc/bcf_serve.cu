@@ -7,9 +7,10 @@
 //   step()    reaps finished work (event polling), frees its arena space,
 //             then admits queued requests by memory and launches them;
 //   poll()    hands back completion records (submit / admit / done times).
-// Served mode (continuous batching): requests up to `small_max` keys are
-// coalesced -- per (key type, order, payload) -- into one segmented-sort
-// launch over a packed batch in the arena (a merge of sorted runs is the
+// Served mode (continuous batching): requests up to `small_max` keys that are
+// waiting together are coalesced -- per (key type, order, payload) -- into one
+// segmented-sort launch over a packed batch in the arena (a lone one runs on
+// its own) (a merge of sorted runs is the
 // stable sort of their concatenation, so small merges batch the same way);
 // larger requests run as their own sort / merge chain with the workspace in
 // the arena, round-robin over parallel streams.  Small requests may overtake
@@ -376,6 +377,12 @@ void admit_served(bcf_server* s) {
     keep.push_back(std::move(q));
   }
   for (auto& g : groups) {
+    if (g.reqs.size() == 1) {
+      // nothing to coalesce with: a lone small request runs on its own, which
+      // skips the batch's staging copies
+      if (launch_solo(s, g.reqs[0], pick_stream(s)) != BCF_OK) keep.push_back(std::move(g.reqs[0]));
+      continue;
+    }
     if (launch_batch(s, g.reqs, pick_stream(s)) != BCF_OK) {
       for (auto& q : g.reqs) keep.push_back(std::move(q));  // retry on a later step
     }
