@@ -368,7 +368,11 @@ def run_gpu(args, world, rank, local, pg):
     serving = None
     if args.serve_seconds > 0:
         del ws
-        serving = serving_bench(torch, dev, args.serve_seconds)
+        # the workload's trace (2000 req/s), then the same request mix at 8x the
+        # rate, past what one launch chain per request can sustain
+        serving = {"nominal": serving_bench(torch, dev, args.serve_seconds),
+                   "stress_8x": serving_bench(torch, dev, min(2.0, args.serve_seconds),
+                                              rate=16000.0)}
 
     if rank != 0:
         return 0
