@@ -147,14 +147,19 @@ Plan make_plan(uint64_t n, int kb, bool pairs, int op = BCF_OP_SORT) {
 constexpr uint64_t kMinMergeTile = 2048;
 
 struct WsLayout {
-  size_t splits, keys, vals, total;
+  size_t splits, samples0, samples1, keys, vals, total;
 };
 
+// [header | splits | samples of the output buffer | samples of the workspace
+// copy | keys copy | values copy]
 WsLayout ws_layout(uint64_t n, uint64_t runs_or_segs, int kb, bool pairs) {
   WsLayout w;
   const uint64_t items = (n + kMinMergeTile - 1) / kMinMergeTile + runs_or_segs + 2;
+  const uint64_t nsamp = n / kSampleStride + 2;
   w.splits = kAlign;
-  w.keys = align_up(w.splits + items * sizeof(uint64_t), kAlign);
+  w.samples0 = align_up(w.splits + items * sizeof(uint64_t), kAlign);
+  w.samples1 = align_up(w.samples0 + nsamp * kb, kAlign);
+  w.keys = align_up(w.samples1 + nsamp * kb, kAlign);
   w.vals = align_up(w.keys + n * kb, kAlign);
   w.total = align_up(w.vals + (pairs ? n * 4 : 0), kAlign);
   return w;
@@ -332,7 +337,11 @@ bcf_status run_sort(void* ko, uint32_t* vo, const void* ki, const uint32_t* vi, 
   // alternating backwards from there
   auto buf = [m](int i) { return ((m - i) % 2 == 0) ? 0 : 1; };
 
-  BlockSortArgs ba{ki, vi, kbuf[buf(0)], vbuf[buf(0)], n, mode, m == 0 ? mode : 0};
+  // sample arrays of the two buffers (the final output needs none)
+  void* samp[2] = {plan.passes > 0 ? wsb + wl.samples0 : nullptr,
+                   plan.passes > 0 ? wsb + wl.samples1 : nullptr};
+  BlockSortArgs ba{ki, vi, kbuf[buf(0)], vbuf[buf(0)], n, mode, m == 0 ? mode : 0,
+                   m == 0 ? nullptr : samp[buf(0)]};
   cudaError_t e = timed(0, s, [&] {
     return launch_block_sort(kb, pairs, plan.tune.block_cfg, ba, s);
   });
@@ -352,6 +361,8 @@ bcf_status run_sort(void* ko, uint32_t* vo, const void* ki, const uint32_t* vi, 
     ma.mode_out = i == m ? mode : 0;
     ma.err = err;
     ma.nitems = items;
+    ma.samples_in = samp[buf(i - 1)];
+    ma.samples_out = i == m ? nullptr : samp[buf(i)];
     e = timed(1, s, [&] { return launch_partition(kb, plan.tune.merge_cfg, ma, nullptr, s); });
     if (e != cudaSuccess) return BCF_ECUDA;
     e = timed(2, s, [&] { return launch_merge(kb, pairs, plan.tune.merge_cfg, ma, nullptr, s); });

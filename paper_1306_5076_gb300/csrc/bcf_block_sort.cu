@@ -96,6 +96,10 @@ __global__ void __launch_bounds__(NT) block_sort_kernel(const BlockSortArgs a) {
   K* kout = static_cast<K*>(a.kout) + base;
   uint32_t* vout = PAIRS ? a.vout + base : nullptr;
   const uint32_t p0 = tid * E;
+  // sample of the sorted tile for the next pass's merge-path search (mapped keys)
+  static_assert(kSampleStride % E == 0 && T % kSampleStride == 0, "sample stride");
+  if (a.samples && (p0 % kSampleStride) == 0 && p0 < cnt)
+    static_cast<K*>(a.samples)[(base + p0) / kSampleStride] = f.k[0];
   if (p0 + E <= cnt) {
 #pragma unroll
     for (int q = 0; q < E / V; ++q) {

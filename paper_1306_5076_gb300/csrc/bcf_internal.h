@@ -26,6 +26,11 @@ struct PairList {
   uint32_t pad_;
 };
 
+// Every kSampleStride-th key of each sorted run is also written to a sample
+// array (in mapped key order); the next pass's merge-path search runs on the
+// samples first and then only inside a window of +-kSampleStride keys.
+constexpr uint32_t kSampleStride = 256;
+
 struct BlockSortArgs {
   const void* kin;
   const uint32_t* vin;  // nullptr for keys only
@@ -34,6 +39,7 @@ struct BlockSortArgs {
   uint64_t n;           // elements of the array
   int mode_in;          // key map applied on load (bit0 f32 order, bit1 descending)
   int mode_out;         // inverse key map applied on store
+  void* samples;        // sample array of kout (keys at multiples of kSampleStride), or nullptr
 };
 
 struct MergeArgs {
@@ -48,6 +54,8 @@ struct MergeArgs {
   int mode_out;
   uint32_t* err;        // device error word
   uint64_t nitems;      // work items (tile pieces) of this launch
+  const void* samples_in;  // regular mode: sample array of kin, or nullptr
+  void* samples_out;       // regular mode: sample array of kout, or nullptr
 };
 
 // Tuning configuration: elements per thread and threads per CTA.

@@ -114,6 +114,24 @@ __device__ __forceinline__ uint64_t first_item(const PairParam<IRREG>& pl) {
 // binary search in global memory.  (A warp-cooperative 32-ary search needs
 // ~6 instead of ~27 dependent rounds but reads ~7x more sectors, and was
 // measured slower at every run length.)
+template <typename K, bool MAP>
+__device__ __forceinline__ uint64_t merge_path_bs(const K* A, const K* B, uint64_t d, uint64_t lo,
+                                                  uint64_t hi, int mode) {
+  while (lo < hi) {
+    const uint64_t mid = (lo + hi) >> 1;  // lo <= mid < hi: A[mid] and B[d-1-mid] exist
+    K x = __ldg(A + mid), y = __ldg(B + (d - 1 - mid));
+    if constexpr (MAP) {
+      x = map_key(x, mode);
+      y = map_key(y, mode);
+    }
+    if (x > y)
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  return lo;
+}
+
 template <typename K, bool IRREG, bool MAP>
 __global__ void __launch_bounds__(256) partition_kernel(const MergeArgs a, int Tm,
                                                         const __grid_constant__ PairParam<IRREG> pl) {
@@ -124,21 +142,33 @@ __global__ void __launch_bounds__(256) partition_kernel(const MergeArgs a, int T
   const K* A = static_cast<const K*>(a.kin) + p.src;
   const K* B = A + p.na_tot;
   const uint64_t d = p.d0;
-  uint64_t lo = d > p.nb_tot ? d - p.nb_tot : 0;
-  uint64_t hi = d < p.na_tot ? d : p.na_tot;
-  while (lo < hi) {
-    const uint64_t mid = (lo + hi) >> 1;  // lo <= mid < hi: A[mid] and B[d-1-mid] exist
-    K x = __ldg(A + mid), y = __ldg(B + (d - 1 - mid));
-    if constexpr (MAP) {
-      x = map_key(x, a.mode_in);
-      y = map_key(y, a.mode_in);
+  const uint64_t lo = d > p.nb_tot ? d - p.nb_tot : 0;
+  const uint64_t hi = d < p.na_tot ? d : p.na_tot;
+  if constexpr (!IRREG && !MAP) {
+    if (a.samples_in) {
+      // Merge path of the runs' samples (every S-th key; runs and d are
+      // multiples of S), then the exact search only within +-S of it: the
+      // true split is within S of S times the samples' split.  The result is
+      // checked against the split's defining inequalities; should that fail,
+      // the full search below runs.
+      constexpr uint64_t S = kSampleStride;
+      const K* As = static_cast<const K*>(a.samples_in) + p.src / S;
+      const K* Bs = As + p.na_tot / S;
+      const uint64_t nas = (p.na_tot + S - 1) / S, nbs = (p.nb_tot + S - 1) / S, D = d / S;
+      const uint64_t sa = merge_path_bs<K, false>(As, Bs, D, D > nbs ? D - nbs : 0,
+                                                  D < nas ? D : nas, 0);
+      const uint64_t wlo = sa * S > lo + S ? sa * S - S : lo;
+      const uint64_t whi = sa * S + S < hi ? sa * S + S : hi;
+      const uint64_t i = merge_path_bs<K, false>(A, B, d, wlo < whi ? wlo : whi, whi, 0);
+      const bool left_ok = i == 0 || d - i >= p.nb_tot || !(__ldg(A + i - 1) > __ldg(B + (d - i)));
+      const bool right_ok = i >= p.na_tot || d == i || __ldg(A + i) > __ldg(B + (d - i - 1));
+      if (left_ok && right_ok && i >= lo && i <= hi) {
+        a.splits[item] = i;
+        return;
+      }
     }
-    if (x > y)
-      hi = mid;
-    else
-      lo = mid + 1;
   }
-  a.splits[item] = lo;
+  a.splits[item] = merge_path_bs<K, MAP>(A, B, d, lo, hi, a.mode_in);
 }
 
 // Stage elements [g0, g1) of `src` (absolute indices; src 16-byte aligned)
@@ -294,6 +324,11 @@ __global__ void __launch_bounds__(NT) merge_kernel(const MergeArgs a,
   }
 
   bitonic_merge_str<NT>(f, reinterpret_cast<uint32_t*>(body));
+  if constexpr (!IRREG && !MAP) {
+    // samples of the output run for the next pass's merge-path search
+    if (a.samples_out && ((p.out0 + tid * E) % kSampleStride) == 0 && tid * E < p.d1 - p.d0)
+      static_cast<K*>(a.samples_out)[(p.out0 + tid * E) / kSampleStride] = f.k[0];
+  }
 
   // outputs: BLK layout, thread holds tile slots tid*E .. tid*E+E-1
   K* kout = static_cast<K*>(a.kout) + p.out0;

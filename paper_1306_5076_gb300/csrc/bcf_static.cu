@@ -11,7 +11,7 @@
 // g_static_workspace below, reserved when the library is loaded on a GPU.
 //
 // Costs and rules:
-//  - every GPU that loads this library holds kStaticBytes (about 8 MiB) of
+//  - every GPU that loads this library holds kStaticBytes (about 8.1 MiB) of
 //    device memory until the process exits;
 //  - at most BCF_STATIC_MAX_KEYS keys per call;
 //  - every call shares the one array: calls whose GPU work overlaps (two
@@ -31,10 +31,13 @@ namespace {
 
 // The sort's workspace for BCF_STATIC_MAX_KEYS keys of the widest type (u64),
 // keys only: a 256-byte header, one u64 split per 2048-key merge tile (+2),
-// rounded to 256 bytes, then one copy of the keys.  A spare page on top.
+// two sample arrays of one key per 256 (+2), each rounded to 256 bytes, then
+// one copy of the keys.  A spare page on top.
 constexpr size_t kMaxKeys = BCF_STATIC_MAX_KEYS;
-constexpr size_t kSplitBytes = ((256 + (kMaxKeys / 2048 + 2) * 8) + 255) / 256 * 256;
-constexpr size_t kStaticBytes = kSplitBytes + kMaxKeys * 8 + 4096;
+constexpr size_t round256(size_t x) { return (x + 255) / 256 * 256; }
+constexpr size_t kSplitBytes = round256(256 + (kMaxKeys / 2048 + 2) * 8);
+constexpr size_t kSampleBytes = round256((kMaxKeys / 256 + 2) * 8);
+constexpr size_t kStaticBytes = kSplitBytes + 2 * kSampleBytes + kMaxKeys * 8 + 4096;
 
 static __device__ __align__(256) unsigned char g_static_workspace[kStaticBytes];
 

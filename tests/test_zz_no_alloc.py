@@ -71,7 +71,7 @@ def test_static_matches_workspace_sort_twice_in_a_row(lib):
 
     cases = [("u32", "uniform", _native.BCF_STATIC_MAX_KEYS, False, 0),
              ("f32", "gaussian", 777_777, True, 2),
-             ("u64", "distinct16", 123_457, False, 1)]
+             ("u64", "distinct16", _native.BCF_STATIC_MAX_KEYS, False, 1)]  # widest keys at the limit
     for dtype, dist, n, desc, kt in cases:
         keys = workloads.keys(dist, dtype, n, seed=61 + n)
         expect = _sort_ws(lib, keys, kt, desc)
