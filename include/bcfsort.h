@@ -10,7 +10,8 @@
  * --------------------------------------
  *  - Memory.  Every key / value pointer is DEVICE memory owned by the caller
  *    and must be 16-byte aligned when the element count is non-zero.  Keys are
- *    arrays of the key type (4 bytes for BCF_U32 / BCF_F32, 8 for BCF_U64);
+ *    arrays of the key type (4 bytes for BCF_U32 / BCF_I32 / BCF_F32, 8 for
+ *    BCF_U64 / BCF_I64 / BCF_F64);
  *    values are uint32_t arrays of the same length.  Arrays are contiguous.
  *  - Workspace.  The library allocates nothing on the sort path.  Calls that
  *    need scratch take a caller-provided device workspace `ws` of at least
@@ -25,7 +26,8 @@
  *    A launch failure returns BCF_ECUDA.  Device-side bounded waits that run
  *    out set a device error word that bcf_last_device_error() reports.
  *  - Order.  Keys are compared after an order-preserving map to unsigned
- *    integers: u32 / u64 as-is, f32 under IEEE 754 totalOrder
+ *    integers: u32 / u64 as-is, i32 / i64 in two's-complement order, f32 /
+ *    f64 under IEEE 754 totalOrder
  *    (-NaN < -inf < ... < -0 < +0 < ... < +inf < +NaN).  Keys are returned
  *    bit-for-bit (NaN payloads and the sign of zero survive).  Descending
  *    order reverses the key order; ties ALWAYS keep input order (stable), in
@@ -49,7 +51,18 @@
 extern "C" {
 #endif
 
-typedef enum { BCF_U32 = 0, BCF_U64 = 1, BCF_F32 = 2 } bcf_dtype;
+/* Key types.  The paper sorts unsigned integers (Sec. 4) and is silent on any
+ * other type; the signed and floating-point orders are this library's
+ * extension, each reduced to an unsigned order by a bijective map applied when
+ * a key is first loaded and undone when it is last stored. */
+typedef enum {
+    BCF_U32 = 0, /* uint32_t, natural order */
+    BCF_U64 = 1, /* uint64_t, natural order */
+    BCF_F32 = 2, /* IEEE 754 binary32, totalOrder */
+    BCF_I32 = 3, /* int32_t, two's-complement order */
+    BCF_I64 = 4, /* int64_t, two's-complement order */
+    BCF_F64 = 5  /* IEEE 754 binary64, totalOrder */
+} bcf_dtype;
 
 typedef enum {
     BCF_OK = 0,

@@ -27,14 +27,17 @@
  * The merge step takes the element of the LEFT run unless the right one is
  * strictly smaller, which is what makes it stable.
  *
- * Key order.  u32 and u64: the integers' natural order.  f32: IEEE 754
+ * Key order.  u32 and u64: the integers' natural order.  i32 and i64: C's
+ * signed comparison of the two's-complement values.  f32 and f64: IEEE 754
  * totalOrder (IEEE 754-2008 Sec. 5.10), written as a case analysis on sign and
  * magnitude bits: every negative-signed value precedes every positive-signed
  * one; among positive-signed values a larger magnitude field (exponent and
  * fraction, read as an unsigned integer) is larger; among negative-signed
  * values a larger magnitude field is smaller.  This puts -NaN < -inf < ... <
  * -0 < +0 < ... < +inf < +NaN and orders NaNs by payload.  Keys are moved
- * bit-for-bit; NaN payloads and the sign of zero are preserved.
+ * bit-for-bit; NaN payloads and the sign of zero are preserved.  The paper
+ * sorts unsigned integers only (Sec. 4); the other types are the library's
+ * extension and their orders are the standard ones named here.
  * Descending order reverses the key order only; ties still keep input order.
  *
  * nthreads > 1 is used only to time the oracle on all host cores: each thread
@@ -49,7 +52,8 @@
 #include <stdlib.h>
 #include <string.h>
 
-enum { ORACLE_U32 = 0, ORACLE_U64 = 1, ORACLE_F32 = 2 };
+enum { ORACLE_U32 = 0, ORACLE_U64 = 1, ORACLE_F32 = 2, ORACLE_I32 = 3, ORACLE_I64 = 4,
+       ORACLE_F64 = 5 };
 
 typedef struct {
     const void* keys;
@@ -69,20 +73,40 @@ static int f32_total_less(uint32_t a, uint32_t b)
     return mag_a > mag_b;
 }
 
+/* IEEE 754 totalOrder on binary64 bit patterns: the same case analysis. */
+static int f64_total_less(uint64_t a, uint64_t b)
+{
+    uint64_t neg_a = a >> 63, neg_b = b >> 63;
+    uint64_t abs_a = a & 0x7FFFFFFFFFFFFFFFull, abs_b = b & 0x7FFFFFFFFFFFFFFFull;
+    if (neg_a != neg_b)
+        return neg_a == 1;
+    if (neg_a == 0)
+        return abs_a < abs_b;
+    return abs_a > abs_b;
+}
+
+static size_t key_size(int dtype)
+{
+    return (dtype == ORACLE_U64 || dtype == ORACLE_I64 || dtype == ORACLE_F64) ? 8 : 4;
+}
+
 static uint64_t key_bits(const order_ctx* c, uint64_t i)
 {
-    switch (c->dtype) {
-    case ORACLE_U64: return ((const uint64_t*)c->keys)[i];
-    default:         return ((const uint32_t*)c->keys)[i];
-    }
+    if (key_size(c->dtype) == 8)
+        return ((const uint64_t*)c->keys)[i];
+    return ((const uint32_t*)c->keys)[i];
 }
 
 /* Strict "a goes before b" under the ascending key order of dtype. */
 static int bits_less(int dtype, uint64_t a, uint64_t b)
 {
-    if (dtype == ORACLE_F32)
-        return f32_total_less((uint32_t)a, (uint32_t)b);
-    return a < b;
+    switch (dtype) {
+    case ORACLE_F32: return f32_total_less((uint32_t)a, (uint32_t)b);
+    case ORACLE_F64: return f64_total_less(a, b);
+    case ORACLE_I32: return (int32_t)(uint32_t)a < (int32_t)(uint32_t)b;
+    case ORACLE_I64: return (int64_t)a < (int64_t)b;
+    default:         return a < b;
+    }
 }
 
 /* Strict precedence of the key at index i over the key at index j. */
@@ -184,11 +208,6 @@ static int sort_perm(uint64_t* perm, uint64_t n, const order_ctx* c, int nthread
     return 0;
 }
 
-static size_t key_size(int dtype)
-{
-    return dtype == ORACLE_U64 ? 8 : 4;
-}
-
 static void gather(void* keys_out, uint32_t* vals_out, const void* keys_in,
                    const uint32_t* vals_in, const uint64_t* perm, uint64_t n, int dtype)
 {
@@ -213,7 +232,7 @@ int oracle_key_less(int dtype, uint64_t a, uint64_t b)
 int oracle_sort(void* keys_out, uint32_t* vals_out, const void* keys_in,
                 const uint32_t* vals_in, uint64_t n, int dtype, int descending, int nthreads)
 {
-    if (dtype < ORACLE_U32 || dtype > ORACLE_F32)
+    if (dtype < ORACLE_U32 || dtype > ORACLE_F64)
         return -1;
     if ((vals_out == NULL) != (vals_in == NULL))
         return -1;
@@ -270,3 +289,4 @@ int oracle_segmented_sort(void* keys_out, uint32_t* vals_out, const void* keys_i
     }
     return 0;
 }
+

@@ -15,14 +15,15 @@ from __future__ import annotations
 import ctypes
 
 from . import _native
-from ._native import BCF_F32, BCF_OP_MERGE, BCF_OP_SEGMENTED, BCF_OP_SORT, BCF_U32, BCF_U64
+from ._native import (BCF_F32, BCF_F64, BCF_I32, BCF_I64, BCF_OP_MERGE, BCF_OP_SEGMENTED,
+                      BCF_OP_SORT, BCF_U32, BCF_U64)
 
 __all__ = [
     "BcfError", "bcf_workspace_bytes", "bcf_sort_keys", "bcf_sort_pairs", "bcf_merge_runs",
     "bcf_segmented_sort", "bcf_last_device_error", "bcf_sort_plan", "bcf_profile_enable",
     "bcf_profile_collect", "bcf_version", "bcf_sort_keys_static", "bcf_tuning_set",
     "bcf_tuning_config", "bcf_tuning_supported", "key_dtype_of", "BCF_U32",
-    "BCF_U64", "BCF_F32",
+    "BCF_U64", "BCF_F32", "BCF_I32", "BCF_I64", "BCF_F64",
     "BCF_OP_SORT", "BCF_OP_MERGE", "BCF_OP_SEGMENTED",
 ]
 
@@ -40,16 +41,20 @@ def _check(status: int, what: str) -> None:
 
 
 def key_dtype_of(t) -> int:
-    """C key-type code of a tensor's dtype."""
+    """C key-type code of a tensor's dtype: float32 / float64 sort under IEEE
+    totalOrder, int32 / int64 as signed integers, uint32 / uint64 as unsigned.
+    (To sort the bits of a signed tensor as unsigned, pass ``kt`` explicitly.)"""
     import torch
 
-    if t.dtype == torch.float32:
-        return BCF_F32
-    if t.dtype in (torch.int32, getattr(torch, "uint32", torch.int32)):
-        return BCF_U32
-    if t.dtype in (torch.int64, getattr(torch, "uint64", torch.int64)):
-        return BCF_U64
-    raise TypeError(f"unsupported key dtype {t.dtype}")
+    table = {torch.float32: BCF_F32, torch.float64: BCF_F64, torch.int32: BCF_I32,
+             torch.int64: BCF_I64}
+    for name, code in (("uint32", BCF_U32), ("uint64", BCF_U64)):
+        if hasattr(torch, name):
+            table[getattr(torch, name)] = code
+    try:
+        return table[t.dtype]
+    except KeyError:
+        raise TypeError(f"unsupported key dtype {t.dtype}") from None
 
 
 def _ptr(t):

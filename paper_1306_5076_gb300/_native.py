@@ -12,7 +12,7 @@ import threading
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libbcfsort.so")
 
-BCF_U32, BCF_U64, BCF_F32 = 0, 1, 2
+BCF_U32, BCF_U64, BCF_F32, BCF_I32, BCF_I64, BCF_F64 = 0, 1, 2, 3, 4, 5
 BCF_OP_SORT, BCF_OP_MERGE, BCF_OP_SEGMENTED = 0, 1, 2
 STATUS = {0: "BCF_OK", 1: "BCF_EINVAL", 2: "BCF_ENOMEM", 3: "BCF_ECUDA", 4: "BCF_ETIMEOUT",
           5: "BCF_EUNSUPPORTED"}

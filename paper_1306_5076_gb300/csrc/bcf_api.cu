@@ -31,12 +31,17 @@ namespace {
 constexpr size_t kAlign = 256;
 constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-int key_bytes_of(bcf_dtype kt) { return kt == BCF_U64 ? 8 : 4; }
-bool dtype_ok(int kt) { return kt == BCF_U32 || kt == BCF_U64 || kt == BCF_F32; }
+bool dtype_ok(int kt) { return kt >= BCF_U32 && kt <= BCF_F64; }
+int key_bytes_of(bcf_dtype kt) {
+  return (kt == BCF_U64 || kt == BCF_I64 || kt == BCF_F64) ? 8 : 4;
+}
 
+// The key map of the device code: bit 0 totalOrder (f32 / f64), bit 2
+// two's-complement (i32 / i64), bit 1 descending.
 int mode_of(bcf_dtype kt, const bcf_opts* o) {
   int m = 0;
-  if (kt == BCF_F32) m |= 1;
+  if (kt == BCF_F32 || kt == BCF_F64) m |= 1;
+  if (kt == BCF_I32 || kt == BCF_I64) m |= 4;
   if (o && o->descending) m |= 2;
   return m;
 }

@@ -25,6 +25,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 
 namespace bcf {
 
@@ -36,27 +37,36 @@ constexpr uint32_t kErrTmaTimeout = 1u;
 __host__ __device__ constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x >> 1); }
 
 // ---------------------------------------------------------------- key maps
-// Order-preserving maps from key bits to unsigned integers.  mode bit 0: f32
-// IEEE 754 totalOrder (32-bit keys only), bit 1: descending (bitwise NOT).
-// map(u) for f32: a negative-signed pattern has all its bits inverted, a
-// positive-signed one its sign bit set, so that unsigned order equals
-// totalOrder.  unmap inverts it exactly.
+// Order-preserving maps from key bits to unsigned integers, applied when a
+// key is first loaded and undone when it is last stored.
+//   mode bit 0: IEEE 754 totalOrder (f32 on 32-bit keys, f64 on 64-bit keys):
+//               a negative-signed pattern has all its bits inverted, a
+//               positive-signed one its sign bit set, so that unsigned order
+//               equals totalOrder;
+//   mode bit 2: two's-complement order (i32 / i64): the sign bit is flipped;
+//   mode bit 1: descending (bitwise NOT, after the type's map).
+// Each map is a bijection and unmap inverts it exactly, so keys come back
+// bit-for-bit.
 
-__device__ __forceinline__ uint32_t map_key(uint32_t u, int mode) {
-  if (mode & 1) u ^= (uint32_t)((int32_t)u >> 31) | 0x80000000u;
+template <typename U>
+__device__ __forceinline__ U map_key(U u, int mode) {
+  constexpr int kTop = 8 * sizeof(U) - 1;
+  constexpr U kSign = U(1) << kTop;
+  using S = typename std::conditional<sizeof(U) == 4, int32_t, int64_t>::type;
+  if (mode & 1) u ^= U(S(u) >> kTop) | kSign;
+  if (mode & 4) u ^= kSign;
   if (mode & 2) u = ~u;
   return u;
 }
-__device__ __forceinline__ uint32_t unmap_key(uint32_t m, int mode) {
+template <typename U>
+__device__ __forceinline__ U unmap_key(U m, int mode) {
+  constexpr int kTop = 8 * sizeof(U) - 1;
+  constexpr U kSign = U(1) << kTop;
+  using S = typename std::conditional<sizeof(U) == 4, int32_t, int64_t>::type;
   if (mode & 2) m = ~m;
-  if (mode & 1) m ^= (~(uint32_t)((int32_t)m >> 31)) | 0x80000000u;
+  if (mode & 4) m ^= kSign;
+  if (mode & 1) m ^= U(~U(S(m) >> kTop)) | kSign;
   return m;
-}
-__device__ __forceinline__ uint64_t map_key(uint64_t u, int mode) {
-  return (mode & 2) ? ~u : u;
-}
-__device__ __forceinline__ uint64_t unmap_key(uint64_t m, int mode) {
-  return (mode & 2) ? ~m : m;
 }
 
 template <typename K> struct KeyLimits;

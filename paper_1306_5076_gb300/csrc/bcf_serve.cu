@@ -169,7 +169,9 @@ namespace {
 
 bcf_status cuda_ok(cudaError_t e) { return e == cudaSuccess ? BCF_OK : BCF_ECUDA; }
 
-int key_bytes(bcf_dtype kt) { return kt == BCF_U64 ? 8 : 4; }
+int key_bytes(bcf_dtype kt) {
+  return (kt == BCF_U64 || kt == BCF_I64 || kt == BCF_F64) ? 8 : 4;
+}
 
 cudaEvent_t get_event(bcf_server* s) {
   if (!s->events.empty()) {
@@ -432,7 +434,7 @@ double bcf_server_now(const bcf_server* s) { return s ? now_s(s->t0) : 0.0; }
 bcf_status bcf_server_submit(bcf_server* s, const bcf_request* r) {
   if (!s || !r) return BCF_EINVAL;
   if (r->op != BCF_OP_SORT && r->op != BCF_OP_MERGE) return BCF_EINVAL;
-  if (r->kt != BCF_U32 && r->kt != BCF_U64 && r->kt != BCF_F32) return BCF_EINVAL;
+  if (r->kt < BCF_U32 || r->kt > BCF_F64) return BCF_EINVAL;
   if ((r->vals_in == nullptr) != (r->vals_out == nullptr)) return BCF_EINVAL;
   Req q;
   q.r = *r;

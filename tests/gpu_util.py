@@ -3,7 +3,7 @@ from __future__ import annotations
 
 import numpy as np
 
-KT = {"u32": 0, "u64": 1, "f32": 2}
+KT = {"u32": 0, "u64": 1, "f32": 2, "i32": 3, "i64": 4, "f64": 5}
 
 
 def to_dev(a: np.ndarray, dev="cuda:0"):
@@ -20,8 +20,10 @@ def from_dev(t, like: np.dtype) -> np.ndarray:
 
 
 def kt_of(a: np.ndarray) -> int:
-    return {np.dtype(np.uint32): 0, np.dtype(np.uint64): 1, np.dtype(np.float32): 2}[a.dtype]
+    return {np.dtype(np.uint32): 0, np.dtype(np.uint64): 1, np.dtype(np.float32): 2,
+            np.dtype(np.int32): 3, np.dtype(np.int64): 4, np.dtype(np.float64): 5}[a.dtype]
 
 
 def bits(a: np.ndarray) -> np.ndarray:
-    return a.view(np.uint32) if a.dtype == np.float32 else a
+    """Bit patterns as unsigned integers of the key width (exact comparison)."""
+    return a.view(np.uint32 if a.dtype.itemsize == 4 else np.uint64)

@@ -3,10 +3,10 @@
 Nothing here is shared with ``oracle/`` or the CUDA library.  The key order is
 re-derived from its definitions in a different formulation:
 
-* integers: Python's integer ``<``;
-* binary32: IEEE 754-2008 Sec. 5.10 totalOrder written as the standard's case
-  analysis on numeric value, sign of zero, and NaN sign / kind / payload (the
-  oracle instead compares sign and magnitude bit fields).
+* integers: Python's integer ``<`` on the unsigned or two's-complement value;
+* binary32 / binary64: IEEE 754-2008 Sec. 5.10 totalOrder written as the
+  standard's case analysis on numeric value, sign of zero, and NaN sign / kind /
+  payload (the oracle instead compares sign and magnitude bit fields).
 
 The brute-force sorts (stable selection sort, stable insertion sort) are the
 textbook algorithms written in plain Python.
@@ -22,11 +22,18 @@ def f32_value(bits: int) -> float:
     return struct.unpack("<f", struct.pack("<I", bits & 0xFFFFFFFF))[0]
 
 
-def ieee_total_order_lt(a_bits: int, b_bits: int) -> bool:
-    """totalOrder(a, b) and a != b, for binary32 bit patterns."""
-    a, b = f32_value(a_bits), f32_value(b_bits)
+def f64_value(bits: int) -> float:
+    return struct.unpack("<d", struct.pack("<Q", bits & 0xFFFFFFFFFFFFFFFF))[0]
+
+
+def ieee_total_order_lt(a_bits: int, b_bits: int, width: int = 32) -> bool:
+    """totalOrder(a, b) and a != b, for binary32 (width 32) or binary64 (width
+    64) bit patterns."""
+    value = f32_value if width == 32 else f64_value
+    frac_bits = 23 if width == 32 else 52  # the quiet bit is the top fraction bit
+    a, b = value(a_bits), value(b_bits)
     a_nan, b_nan = a != a, b != b
-    sa, sb = a_bits >> 31 & 1, b_bits >> 31 & 1
+    sa, sb = a_bits >> (width - 1) & 1, b_bits >> (width - 1) & 1
     if not a_nan and not b_nan:
         if a < b:
             return True
@@ -36,8 +43,9 @@ def ieee_total_order_lt(a_bits: int, b_bits: int) -> bool:
     if a_nan and b_nan:
         if sa != sb:
             return sa == 1
-        ka = (a_bits >> 22 & 1, a_bits & 0x3FFFFF)  # (quiet bit, payload)
-        kb = (b_bits >> 22 & 1, b_bits & 0x3FFFFF)
+        pmask = (1 << (frac_bits - 1)) - 1
+        ka = (a_bits >> (frac_bits - 1) & 1, a_bits & pmask)  # (quiet bit, payload)
+        kb = (b_bits >> (frac_bits - 1) & 1, b_bits & pmask)
         return ka < kb if sa == 0 else ka > kb
     if a_nan:
         return sa == 1  # -NaN is below every number, +NaN above
@@ -45,9 +53,15 @@ def ieee_total_order_lt(a_bits: int, b_bits: int) -> bool:
 
 
 def lt_for(dtype, descending: bool = False):
-    """Strict precedence on raw key bits of ``dtype`` (numpy dtype or str)."""
+    """Strict precedence on the keys :func:`as_bits` gives for ``dtype``: raw
+    bit patterns for floats, integer values (signed for i32 / i64) otherwise."""
     dt = np.dtype(dtype)
-    base = ieee_total_order_lt if dt == np.float32 else (lambda a, b: a < b)
+    if dt == np.float32:
+        base = ieee_total_order_lt
+    elif dt == np.float64:
+        base = lambda a, b: ieee_total_order_lt(a, b, 64)  # noqa: E731
+    else:
+        base = lambda a, b: a < b  # noqa: E731
     if descending:
         return lambda a, b: base(b, a)
     return base
@@ -56,7 +70,14 @@ def lt_for(dtype, descending: bool = False):
 def as_bits(keys: np.ndarray) -> list[int]:
     if keys.dtype == np.float32:
         return [int(x) for x in keys.view(np.uint32)]
+    if keys.dtype == np.float64:
+        return [int(x) for x in keys.view(np.uint64)]
     return [int(x) for x in keys]
+
+
+def raw_bits(keys: np.ndarray) -> np.ndarray:
+    """The keys' bit patterns as an unsigned array of the same width."""
+    return keys.view(np.uint32 if keys.dtype.itemsize == 4 else np.uint64)
 
 
 def stable_selection_sort(items, lt):
@@ -101,31 +122,36 @@ def check_sorted_stable(keys_in, vals_in, keys_out, vals_out, descending=False):
     assert keys_out.size == n and vals_out.size == n
     perm = vals_out.astype(np.int64)
     assert np.array_equal(np.sort(perm), np.arange(n)), "payloads are not a permutation"
-    kin = keys_in.view(np.uint32) if keys_in.dtype == np.float32 else keys_in
-    kout = keys_out.view(np.uint32) if keys_out.dtype == np.float32 else keys_out
+    kin, kout = raw_bits(keys_in), raw_bits(keys_out)
     assert np.array_equal(kin[perm], kout), "key/payload pairing broken"
     r = order_rank(keys_out)
-    if descending:
-        r = -r
-    d = np.diff(r)
-    assert np.all(d >= 0), "output not sorted"
-    ties = d == 0
+    lo, hi = (r[1:], r[:-1]) if descending else (r[:-1], r[1:])  # no int64 overflow
+    assert np.all(lo <= hi), "output not sorted"
+    ties = lo == hi
     assert np.all(np.diff(perm)[ties] > 0), "equal keys out of input order (unstable)"
 
 
 def order_rank(keys: np.ndarray) -> np.ndarray:
     """A vectorised int64 rank that is strictly monotone in the key order.
 
-    u32: the value.  u64: the value with its top bit flipped, viewed as int64.
-    f32: negative-signed patterns rank by descending magnitude below every
-    positive-signed pattern, which rank by ascending magnitude.  The f32 rank
-    is itself checked against :func:`ieee_total_order_lt` in the pin tests.
+    u32 / i32 / i64: the value.  u64: the value with its top bit flipped,
+    viewed as int64.  f32 / f64: negative-signed patterns rank by descending
+    magnitude below every positive-signed pattern, which rank by ascending
+    magnitude.  The float ranks are themselves checked against
+    :func:`ieee_total_order_lt` in the pin tests.
     """
     if keys.dtype == np.float32:
         b = keys.view(np.uint32).astype(np.int64)
         sign = b >> 31
         mag = b & 0x7FFFFFFF
         return np.where(sign == 1, -1 - mag, mag)
+    if keys.dtype == np.float64:
+        b = keys.view(np.uint64)
+        sign = (b >> np.uint64(63)).astype(np.int64)
+        mag = (b & np.uint64(0x7FFFFFFFFFFFFFFF)).astype(np.int64)
+        return np.where(sign == 1, -1 - mag, mag)
+    if keys.dtype == np.int64:
+        return keys.copy()
     if keys.dtype == np.uint64:
         # map to a signed int64 with the same order by flipping the top bit
         return (keys ^ np.uint64(1 << 63)).view(np.int64)

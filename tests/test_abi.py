@@ -54,7 +54,8 @@ def test_status_strings_and_version(lib):
 
 
 def test_workspace_bytes_scale_with_input(lib):
-    from paper_1306_5076_gb300 import BCF_F32, BCF_OP_MERGE, BCF_OP_SORT, BCF_U32, BCF_U64
+    from paper_1306_5076_gb300 import (BCF_F32, BCF_F64, BCF_I32, BCF_I64, BCF_OP_MERGE,
+                                       BCF_OP_SORT, BCF_U32, BCF_U64)
 
     n = 1 << 20
     keys = lib.bcf_workspace_bytes(BCF_OP_SORT, n, 0, BCF_U32, 0)
@@ -63,6 +64,10 @@ def test_workspace_bytes_scale_with_input(lib):
     assert keys >= 4 * n and pairs >= 8 * n and wide >= 8 * n
     assert keys % 256 == 0 and pairs % 256 == 0
     assert lib.bcf_workspace_bytes(BCF_OP_SORT, n, 0, BCF_F32, 0) == keys
+    # the signed and double key types take the space of their width
+    for kt, same in ((BCF_I32, keys), (BCF_I64, wide), (BCF_F64, wide)):
+        assert lib.bcf_workspace_bytes(BCF_OP_SORT, n, 0, kt, 0) == same
+    assert lib.bcf_workspace_bytes(BCF_OP_SORT, n, 0, 6, 0) == 0
     assert lib.bcf_workspace_bytes(BCF_OP_MERGE, n, 256, BCF_U32, 0) >= keys
     assert lib.bcf_workspace_bytes(9, n, 0, BCF_U32, 0) == 0
     assert lib.bcf_workspace_bytes(BCF_OP_SORT, n, 0, 7, 0) == 0
@@ -73,7 +78,7 @@ def test_plan_pass_count_is_lemma_2(lib, n):
     """Lemma 2: one base-case pass plus ceil(log2(n / T)) merge passes."""
     from paper_1306_5076_gb300 import _native
 
-    for kt in (0, 1, 2):
+    for kt in range(6):
         for has_vals in (0, 1):
             p = _native.BcfPlan()
             assert lib.bcf_sort_plan(n, kt, has_vals, ctypes.byref(p)) == 0
@@ -81,7 +86,7 @@ def test_plan_pass_count_is_lemma_2(lib, n):
             expect = 0 if runs <= 1 else math.ceil(math.log2(runs))
             assert p.merge_passes == expect
             assert p.launches == (0 if n == 0 else 1 + 2 * expect)
-            kb = 8 if kt == 1 else 4
+            kb = 8 if kt in (1, 4, 5) else 4
             assert p.bytes_per_pass == 2 * n * (kb + 4 * has_vals)
             assert p.merge_tile <= 2 * p.block_tile
 
@@ -91,8 +96,10 @@ def test_host_side_argument_errors_return_before_launch(lib):
 
     opts = ctypes.byref(_native.BcfOpts(0, 1))
     EINVAL = 1
-    # bad dtype
+    # bad dtype (one past the last key type, and a negative code)
     assert lib.bcf_sort_keys(None, None, 0, 9, opts, None, 0, None) == EINVAL
+    assert lib.bcf_sort_keys(None, None, 0, 6, opts, None, 0, None) == EINVAL
+    assert lib.bcf_sort_keys(None, None, 0, -1, opts, None, 0, None) == EINVAL
     # n == 0 is a no-op
     assert lib.bcf_sort_keys(None, None, 0, 0, opts, None, 0, None) == 0
     # null pointers with n > 0

@@ -43,7 +43,7 @@ def make_runs(r, dtype, lens, descending=False, alphabet=None):
         else:
             k = workloads.keys("uniform", dtype, int(m), seed=int(r.integers(1 << 30)))
         rank = order_rank(k)
-        order = np.argsort(-rank if descending else rank, kind="stable")
+        order = np.argsort(~rank if descending else rank, kind="stable")  # ~: no overflow
         parts.append(k[order])
     offs = np.zeros(len(lens) + 1, np.uint64)
     offs[1:] = np.cumsum(lens)
@@ -70,7 +70,7 @@ def check(bcf, keys, offs, vals, descending, inplace=False):
         assert np.array_equal(gv, ev)
 
 
-@pytest.mark.parametrize("dtype", ["u32", "u64", "f32"])
+@pytest.mark.parametrize("dtype", list(workloads.DTYPES))
 @pytest.mark.parametrize("descending", [False, True])
 def test_random_uneven_runs(bcf, dtype, descending):
     r = workloads.rng(21)

@@ -62,7 +62,7 @@ def check(bcf, keys, offs, vals, descending=False, inplace=False):
         assert np.array_equal(gv, ev)
 
 
-@pytest.mark.parametrize("dtype", ["u32", "u64", "f32"])
+@pytest.mark.parametrize("dtype", list(workloads.DTYPES))
 @pytest.mark.parametrize("descending", [False, True])
 def test_mixed_size_classes(bcf, dtype, descending):
     r = workloads.rng(31)

@@ -146,3 +146,49 @@ def test_submit_errors(bcf):
         srv.submit(tag=1, kt=0, n=1 << 20, keys_in=x.data_ptr(), keys_out=x.data_ptr())
     assert ei.value.status == 2
     srv.close()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_mixed_key_types_and_directions(bcf, mode):
+    """Requests of every key type and both directions, interleaved in one burst:
+    batches are formed per (key type, direction, payload), and every result
+    equals the oracle's."""
+    from paper_1306_5076_gb300 import serve
+    from tests.gpu_util import bits, kt_of, to_dev
+
+    r = workloads.rng(53)
+    count = 150
+    kinds = list(workloads.DTYPES)
+    reqs = []
+    for i in range(count):
+        dtype = kinds[int(r.integers(0, len(kinds)))]
+        n = int(workloads.log_uniform_sizes(r, 1, 1, 1 << 15)[0])
+        keys = workloads.keys("uniform" if i % 3 else "distinct16", dtype, n, seed=600 + i)
+        vals = workloads.row_index(n) if r.random() < 0.4 else None
+        desc = bool(r.random() < 0.5)
+        kd = to_dev(keys)
+        vd = None if vals is None else to_dev(vals)
+        reqs.append(dict(keys=keys, vals=vals, desc=desc, kd=kd, vd=vd,
+                         ko=torch.empty_like(kd), vo=None if vd is None else torch.empty_like(vd)))
+    arena = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    srv = serve.Server(arena, mode=mode, streams=4, small_max=1 << 14)
+
+    def make(i):
+        q = reqs[i]
+        kw = dict(kt=kt_of(q["keys"]), n=q["keys"].size, keys_in=q["kd"].data_ptr(),
+                  keys_out=q["ko"].data_ptr(), descending=q["desc"])
+        if q["vd"] is not None:
+            kw.update(vals_in=q["vd"].data_ptr(), vals_out=q["vo"].data_ptr())
+        return kw
+
+    res = serve.replay(srv, [0.0] * count, make)
+    torch.cuda.synchronize()
+    srv.close()
+    assert all(s == 0 for s in res["status"])
+    for i, q in enumerate(reqs):
+        ek, ev = oracle.sort(q["keys"], q["vals"], descending=q["desc"])
+        gk = from_dev(q["ko"], q["keys"].dtype)
+        assert np.array_equal(bits(gk), bits(ek)), f"request {i} ({q['keys'].dtype}) keys differ"
+        if ev is not None:
+            assert np.array_equal(from_dev(q["vo"], np.uint32), ev), f"request {i} values differ"

@@ -64,7 +64,7 @@ SIZES = [0, 1, 2, 31, 1000, 4095, 4096, 4097, 8191, 8192, 8193, 3 * 8192 + 17, 6
          (1 << 17) + 123, (1 << 20) + 5]
 
 
-@pytest.mark.parametrize("dtype", ["u32", "u64", "f32"])
+@pytest.mark.parametrize("dtype", list(workloads.DTYPES))
 @pytest.mark.parametrize("n", SIZES)
 def test_uniform_keys_and_pairs_all_sizes(bcf, dtype, n):
     keys = workloads.keys("uniform", dtype, n, seed=100 + n)
@@ -78,7 +78,7 @@ def test_uniform_keys_and_pairs_all_sizes(bcf, dtype, n):
         assert_same(gk, gv, ek, ev)
 
 
-@pytest.mark.parametrize("dtype", ["u32", "u64", "f32"])
+@pytest.mark.parametrize("dtype", list(workloads.DTYPES))
 @pytest.mark.parametrize("dist", workloads.DISTRIBUTIONS)
 def test_workload_distributions(bcf, dtype, dist):
     n = (1 << 18) + 4321
@@ -106,7 +106,9 @@ def test_extreme_keys_tie_with_pads(bcf):
     """Real keys equal to the network's +inf/-inf pads must sort by position."""
     n = 3 * 8192 + 77
     r = workloads.rng(5)
-    for dtype, lo, hi in (("u32", 0, 0xFFFFFFFF), ("u64", 0, 2**64 - 1)):
+    i32, i64 = np.iinfo(np.int32), np.iinfo(np.int64)
+    for dtype, lo, hi in (("u32", 0, 0xFFFFFFFF), ("u64", 0, 2**64 - 1),
+                          ("i32", i32.min, i32.max), ("i64", i64.min, i64.max)):
         dt = workloads.DTYPES[dtype]
         keys = np.where(r.random(n) < 0.5, dt(lo), dt(hi)).astype(dt)
         vals = workloads.row_index(n)
@@ -114,29 +116,47 @@ def test_extreme_keys_tie_with_pads(bcf):
             ek, ev = oracle.sort(keys, vals, descending=desc)
             gk, gv = gpu_sort(bcf, keys, vals, descending=desc)
             assert_same(gk, gv, ek, ev)
-    # f32 patterns that map to the extremes of the order: -NaN max and +NaN max
-    keys = np.where(r.random(n) < 0.5, 0xFFFFFFFF, 0x7FFFFFFF).astype(np.uint32).view(np.float32)
+    # float patterns that map to the extremes of the order: -NaN max and +NaN max
+    for ut, ft, lo, hi in ((np.uint32, np.float32, 0xFFFFFFFF, 0x7FFFFFFF),
+                           (np.uint64, np.float64, 2**64 - 1, 2**63 - 1)):
+        keys = np.where(r.random(n) < 0.5, ut(lo), ut(hi)).astype(ut).view(ft)
+        vals = workloads.row_index(n)
+        for desc in (False, True):
+            ek, ev = oracle.sort(keys, vals, descending=desc)
+            gk, gv = gpu_sort(bcf, keys, vals, descending=desc)
+            assert_same(gk, gv, ek, ev)
+
+
+@pytest.mark.parametrize("width", [32, 64])
+def test_float_golden_total_order(bcf, width):
+    from tests.test_oracle_pins import FLOAT, read_golden
+
+    g = read_golden(width)
+    r = workloads.rng(9)
+    keys = g[r.integers(0, g.size, size=50_000)].view(FLOAT[width][0])
+    vals = workloads.row_index(keys.size)
+    for desc in (False, True):
+        ek, ev = oracle.sort(keys, vals, descending=desc)
+        gk, gv = gpu_sort(bcf, keys, vals, descending=desc)
+        assert_same(gk, gv, ek, ev)
+        # every golden pattern appears, in golden order (reversed if descending)
+        seen = np.unique(bits(gk), return_index=True)
+        order = np.argsort(seen[1])
+        assert np.array_equal(seen[0][order], g[::-1] if desc else g)
+
+
+@pytest.mark.parametrize("dtype", ["i32", "i64"])
+def test_signed_keys_around_zero(bcf, dtype):
+    """Small signed values on both sides of zero: an unsigned compare would
+    put every negative key after every positive one."""
+    n = 3 * 8192 + 5
+    r = workloads.rng(10)
+    keys = r.integers(-50, 50, size=n).astype(workloads.DTYPES[dtype])
     vals = workloads.row_index(n)
     for desc in (False, True):
         ek, ev = oracle.sort(keys, vals, descending=desc)
         gk, gv = gpu_sort(bcf, keys, vals, descending=desc)
         assert_same(gk, gv, ek, ev)
-
-
-def test_f32_golden_total_order(bcf):
-    from tests.test_oracle_pins import read_golden
-
-    g = read_golden()
-    r = workloads.rng(9)
-    keys = g[r.integers(0, g.size, size=50_000)].view(np.float32)
-    vals = workloads.row_index(keys.size)
-    ek, ev = oracle.sort(keys, vals)
-    gk, gv = gpu_sort(bcf, keys, vals)
-    assert_same(gk, gv, ek, ev)
-    # every golden pattern appears in golden order
-    seen = np.unique(gk.view(np.uint32), return_index=True)
-    order = np.argsort(seen[1])
-    assert np.array_equal(seen[0][order], g)
 
 
 def test_all_equal_and_sorted_inputs(bcf):

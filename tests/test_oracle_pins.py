@@ -7,8 +7,10 @@ What fixes the expected results here:
 * a stable insertion sort (textbook) for random n <= 1000;
 * a library routine for the special cases it covers: numpy's stable argsort
   (integers, and floats without NaN or -0) and heapq.merge for merging;
-* IEEE 754 totalOrder: the hand-listed golden vector tests/golden/f32_total_order.txt
-  and the standard's case analysis in tests/pins.py;
+* IEEE 754 totalOrder: the hand-listed golden vectors
+  tests/golden/f32_total_order.txt and f64_total_order.txt, and the standard's
+  case analysis in tests/pins.py;
+* two's-complement order (i32 / i64): Python's integers and numpy's signed sort;
 * closed forms of the paper's data sets (Sec. 4): sorted -> identity,
   reversed distinct keys -> reversal, 0-1 -> zero count, k copies -> k-blocks;
 * invariants: sorted, permutation of the input, stable.
@@ -30,66 +32,93 @@ import oracle
 import workloads
 from tests import pins
 
-GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "f32_total_order.txt")
+GOLDEN_DIR = os.path.join(os.path.dirname(__file__), "golden")
+FLOAT = {32: (np.float32, np.uint32), 64: (np.float64, np.uint64)}
 
 
-def read_golden():
+def read_golden(width=32):
     out = []
-    with open(GOLDEN) as f:
+    with open(os.path.join(GOLDEN_DIR, f"f{width}_total_order.txt")) as f:
         for line in f:
             line = line.strip()
             if line and not line.startswith("#"):
                 out.append(int(line.split()[0], 16))
-    return np.array(out, dtype=np.uint32)
+    return np.array(out, dtype=FLOAT[width][1])
 
 
 def _keys(values, dtype):
     if dtype == "f32":
         return np.array(values, dtype=np.uint32).view(np.float32)
+    if dtype == "f64":
+        return np.array(values, dtype=np.uint64).view(np.float64)
     return np.array(values, dtype=workloads.DTYPES[dtype])
 
 
 # ---------------------------------------------------------------- key order
 
-def test_golden_list_is_in_ieee_total_order():
-    g = [int(x) for x in read_golden()]
+@pytest.mark.parametrize("width", [32, 64])
+def test_golden_list_is_in_ieee_total_order(width):
+    g = [int(x) for x in read_golden(width)]
+    assert len(g) == 28
     for i in range(len(g)):
         for j in range(len(g)):
-            assert pins.ieee_total_order_lt(g[i], g[j]) == (i < j), (hex(g[i]), hex(g[j]))
+            assert pins.ieee_total_order_lt(g[i], g[j], width) == (i < j), (hex(g[i]), hex(g[j]))
 
 
-def check_golden_order(lib):
-    g = read_golden()
+def check_golden_order(lib, width=32):
+    g = read_golden(width)
+    ft = FLOAT[width][0]
     for i in range(len(g)):
         for j in range(len(g)):
-            assert oracle.key_less(np.float32, int(g[i]), int(g[j]), lib=lib) == (i < j)
+            assert oracle.key_less(ft, int(g[i]), int(g[j]), lib=lib) == (i < j)
     r = workloads.rng(11)
     for _ in range(20):
         shuffled = g[r.permutation(g.size)]
-        ko, _ = oracle.sort(shuffled.view(np.float32), lib=lib)
-        assert np.array_equal(ko.view(np.uint32), g)
-        kd, _ = oracle.sort(shuffled.view(np.float32), descending=True, lib=lib)
-        assert np.array_equal(kd.view(np.uint32), g[::-1])
+        ko, _ = oracle.sort(shuffled.view(ft), lib=lib)
+        assert np.array_equal(ko.view(g.dtype), g)
+        kd, _ = oracle.sort(shuffled.view(ft), descending=True, lib=lib)
+        assert np.array_equal(kd.view(g.dtype), g[::-1])
 
 
-def test_oracle_f32_golden_order(oracle_lib):
-    check_golden_order(oracle_lib)
+@pytest.mark.parametrize("width", [32, 64])
+def test_oracle_float_golden_order(oracle_lib, width):
+    check_golden_order(oracle_lib, width)
 
 
-def test_oracle_f32_order_matches_ieee_case_analysis(oracle_lib):
+@pytest.mark.parametrize("width", [32, 64])
+def test_oracle_float_order_matches_ieee_case_analysis(oracle_lib, width):
+    ft, ut = FLOAT[width]
     r = workloads.rng(12)
-    bits = r.integers(0, 2**32, size=3000, dtype=np.uint64).astype(np.uint32)
-    bits[:28] = read_golden()
+    bits = r.integers(0, 2**width, size=3000, dtype=np.uint64).astype(ut)
+    bits[:28] = read_golden(width)
+    # also pairs that differ only in sign, or only in the lowest bit
+    bits[100:200:2] = bits[101:201:2] ^ ut(1 << (width - 1))
+    bits[200:300:2] = bits[201:301:2] ^ ut(1)
     for a, b in zip(bits[:-1], bits[1:]):
         a, b = int(a), int(b)
-        assert oracle.key_less(np.float32, a, b) == pins.ieee_total_order_lt(a, b)
-        assert oracle.key_less(np.float32, b, a) == pins.ieee_total_order_lt(b, a)
+        assert oracle.key_less(ft, a, b) == pins.ieee_total_order_lt(a, b, width)
+        assert oracle.key_less(ft, b, a) == pins.ieee_total_order_lt(b, a, width)
 
 
-def test_order_rank_helper_matches_ieee():
-    g = read_golden()
-    r = pins.order_rank(g.view(np.float32))
-    assert np.all(np.diff(r) > 0)
+@pytest.mark.parametrize("width", [32, 64])
+def test_order_rank_helper_matches_ieee(width):
+    g = read_golden(width)
+    r = pins.order_rank(g.view(FLOAT[width][0]))
+    assert np.all(r[1:] > r[:-1])
+
+
+@pytest.mark.parametrize("dtype,width", [(np.int32, 32), (np.int64, 64)])
+def test_oracle_signed_order_matches_python_integers(oracle_lib, dtype, width):
+    """Two's-complement order: the oracle's comparison of raw bit patterns
+    agrees with Python's ``<`` on the values the patterns encode."""
+    lo, hi = -(1 << (width - 1)), (1 << (width - 1)) - 1
+    special = [lo, lo + 1, -2, -1, 0, 1, 2, hi - 1, hi]
+    r = workloads.rng(18)
+    vals = special + [int(x) for x in r.integers(lo, hi, size=2000, dtype=np.int64,
+                                                  endpoint=True)]
+    mask = (1 << width) - 1
+    for a, b in itertools.chain(itertools.product(special, special), zip(vals[:-1], vals[1:])):
+        assert oracle.key_less(dtype, a & mask, b & mask, lib=oracle_lib) == (a < b), (a, b)
 
 
 # ---------------------------------------------------------------- brute force
@@ -114,6 +143,10 @@ ALPHABETS = {
     "u64": [2**63 + 5, 3, 2**64 - 1],
     # -0.0, +0.0 and a quiet NaN: ties, signed zeros and NaN placement
     "f32": [0x80000000, 0x00000000, 0x7FC00000],
+    # a positive value, -1 and the most negative value: unsigned order differs
+    "i32": [5, -1, -(2**31)],
+    "i64": [5, -1, -(2**63)],
+    "f64": [0x8000000000000000, 0x0000000000000000, 0x7FF8000000000000],
 }
 
 
@@ -131,7 +164,7 @@ def check_ternary_sequences(lib, dtype, descending, max_n=7):
             assert [int(v) for v in vo] == [v for _, v in exp]
 
 
-@pytest.mark.parametrize("dtype", ["u32", "u64", "f32"])
+@pytest.mark.parametrize("dtype", ["u32", "u64", "f32", "i32", "i64", "f64"])
 @pytest.mark.parametrize("descending", [False, True])
 def test_all_ternary_sequences_stable(oracle_lib, dtype, descending):
     check_ternary_sequences(oracle_lib, dtype, descending, max_n=7 if dtype == "u32" else 6)
@@ -144,7 +177,7 @@ def random_bits(r, dtype, n, alphabet):
     return workloads.keys("uniform", dtype, n, seed=int(r.integers(1 << 30)))
 
 
-@pytest.mark.parametrize("dtype", ["u32", "u64", "f32"])
+@pytest.mark.parametrize("dtype", ["u32", "u64", "f32", "i32", "i64", "f64"])
 def test_insertion_sort_random(oracle_lib, dtype):
     r = workloads.rng(13)
     for case in range(6):
@@ -161,7 +194,7 @@ def test_insertion_sort_random(oracle_lib, dtype):
 
 # ---------------------------------------------------------------- library special cases
 
-@pytest.mark.parametrize("dtype", ["u32", "u64"])
+@pytest.mark.parametrize("dtype", ["u32", "u64", "i32", "i64"])
 def test_matches_numpy_stable_argsort_integers(oracle_lib, dtype):
     r = workloads.rng(14)
     for n, alpha in [(100_000, None), (50_000, 97)]:
@@ -170,21 +203,23 @@ def test_matches_numpy_stable_argsort_integers(oracle_lib, dtype):
         ko, vo = oracle.sort(keys, idx)
         order = np.argsort(keys, kind="stable")
         assert np.array_equal(ko, keys[order]) and np.array_equal(vo, order.astype(np.uint32))
-        # descending: stable argsort of the order-reversing bijection max - key
-        rev = np.iinfo(keys.dtype).max - keys
+        # descending: stable argsort of the order-reversing bijection ~key
+        # (max - key for unsigned, -1 - key for two's complement)
+        rev = ~keys
         order_d = np.argsort(rev, kind="stable")
         kd, vd = oracle.sort(keys, idx, descending=True)
         assert np.array_equal(kd, keys[order_d]) and np.array_equal(vd, order_d.astype(np.uint32))
 
 
-def test_matches_numpy_stable_argsort_finite_floats(oracle_lib):
+@pytest.mark.parametrize("ft", [np.float32, np.float64])
+def test_matches_numpy_stable_argsort_finite_floats(oracle_lib, ft):
     r = workloads.rng(15)
-    vals = r.normal(0, 1e3, size=60_000).astype(np.float32)
+    vals = r.normal(0, 1e3, size=60_000).astype(ft)
     vals = np.round(vals)  # many ties
     vals[vals == 0] = 1.0  # numpy treats -0 == +0; totalOrder does not
     ko, vo = oracle.sort(vals, np.arange(vals.size, dtype=np.uint32))
     order = np.argsort(vals, kind="stable")
-    assert np.array_equal(ko.view(np.uint32), vals[order].view(np.uint32))
+    assert np.array_equal(pins.raw_bits(ko), pins.raw_bits(vals[order]))
     assert np.array_equal(vo, order.astype(np.uint32))
 
 
@@ -218,7 +253,7 @@ def test_closed_forms_paper_data_sets(oracle_lib):
         assert short.size == 0 or short[0] == n - k * (counts.size - 1)
 
 
-@pytest.mark.parametrize("dtype", ["u32", "u64", "f32"])
+@pytest.mark.parametrize("dtype", list(workloads.DTYPES))
 @pytest.mark.parametrize("dist", workloads.DISTRIBUTIONS)
 def test_invariants_on_workload_distributions(oracle_lib, dtype, dist):
     n = (1 << 14) + 77
@@ -233,7 +268,7 @@ def test_invariants_on_workload_distributions(oracle_lib, dtype, dist):
 
 
 def test_multithreaded_equals_single_thread(oracle_lib):
-    for dtype in ("u32", "u64", "f32"):
+    for dtype in workloads.DTYPES:
         keys = workloads.keys("distinct16", dtype, (1 << 17) + 3, seed=5)
         idx = np.arange(keys.size, dtype=np.uint32)
         k1, v1 = oracle.sort(keys, idx, nthreads=1)
@@ -268,14 +303,15 @@ def check_merge_runs(lib, dtype="u32", descending=False):
         for run in runs:
             tagged.append([(b, pos + i) for i, b in enumerate(run)])
             pos += len(run)
-        rank = (lambda b: pins.order_rank(_keys([b], dtype))[0]) if dtype == "f32" else int
+        rank = ((lambda b: pins.order_rank(_keys([b], dtype))[0]) if dtype in ("f32", "f64")
+                else int)
         sign = -1 if descending else 1
         exp = list(heapq.merge(*tagged, key=lambda t: sign * int(rank(t[0]))))
         assert pins.as_bits(ko) == [b for b, _ in exp]
         assert [int(v) for v in vo] == [p for _, p in exp]
 
 
-@pytest.mark.parametrize("dtype", ["u32", "u64", "f32"])
+@pytest.mark.parametrize("dtype", list(workloads.DTYPES))
 @pytest.mark.parametrize("descending", [False, True])
 def test_merge_runs_matches_heapq_merge(oracle_lib, dtype, descending):
     check_merge_runs(oracle_lib, dtype, descending)
@@ -283,7 +319,7 @@ def test_merge_runs_matches_heapq_merge(oracle_lib, dtype, descending):
 
 def test_segmented_sort_brute_force(oracle_lib):
     r = workloads.rng(17)
-    for dtype in ("u32", "u64", "f32"):
+    for dtype in workloads.DTYPES:
         sizes = r.integers(0, 30, size=40)
         sizes[::7] = 0
         sizes[::11] = 1
@@ -303,7 +339,7 @@ def test_segmented_sort_brute_force(oracle_lib):
 
 
 def test_empty_and_single(oracle_lib):
-    for dtype in ("u32", "u64", "f32"):
+    for dtype in workloads.DTYPES:
         e = np.zeros(0, workloads.DTYPES[dtype])
         ko, vo = oracle.sort(e, np.zeros(0, np.uint32))
         assert ko.size == 0 and vo.size == 0
@@ -326,6 +362,16 @@ MUTANTS = {
     "desc_reverses_ties": (r"return c->descending \? bits_less\(c->dtype, b, a\) : "
                            r"bits_less\(c->dtype, a, b\);",
                            "return bits_less(c->dtype, a, b);"),
+    # f64 negatives ordered by ascending magnitude, and the f64 sign rule inverted
+    "f64_negative_magnitude": (r"return abs_a > abs_b;", "return abs_a < abs_b;"),
+    "f64_sign": (r"return neg_a == 1;", "return neg_a == 0;"),
+    # signed keys compared as unsigned bit patterns
+    "i32_unsigned": (r"return \(int32_t\)\(uint32_t\)a < \(int32_t\)\(uint32_t\)b;",
+                     "return (uint32_t)a < (uint32_t)b;"),
+    "i64_unsigned": (r"return \(int64_t\)a < \(int64_t\)b;", "return a < b;"),
+    # 64-bit floats read through the 32-bit key path
+    "f64_as_32bit": (r"dtype == ORACLE_I64 \|\| dtype == ORACLE_F64\) \? 8 : 4",
+                     "dtype == ORACLE_I64) ? 8 : 4"),
     # right-run tail dropped
     "drop_tail": (r"while \(j < nr\) out\[o\+\+\] = right\[j\+\+\];",
                   "while (j + 1 < nr) out[o++] = right[j++]; if (j < nr) out[o++] = left[0];"),
@@ -335,7 +381,10 @@ MUTANTS = {
 def _pins_fail(lib, mutant):
     checks = [
         lambda: check_golden_order(lib),
+        lambda: check_golden_order(lib, 64),
         lambda: check_all_permutations(lib, 6),
+        lambda: check_ternary_sequences(lib, "i32", False, 3),
+        lambda: check_ternary_sequences(lib, "i64", False, 3),
         lambda: check_ternary_sequences(lib, "u32", False, 5),
         lambda: check_ternary_sequences(lib, "f32", True, 4),
         lambda: check_merge_runs(lib, "u32", False),

@@ -10,7 +10,7 @@ Distributions follow the paper's data sets (Sec. 4: random keys in
 [0, 10^6], distinct = a shuffle of 1..n, 0-1, and defined duplicates = k copies
 of n/k keys) plus the large-sort workload family: uniform, Gaussian, sorted,
 reverse sorted, 16 distinct values and Zipf(1.1) over 2^20 symbols, for u32,
-u64 and f32 keys.  Payloads are the u32 row index.  Every generator takes an
+u64 and f32 keys and the signed / double extension types i32, i64 and f64.  Payloads are the u32 row index.  Every generator takes an
 explicit seed; the recipe of each is stated in its docstring.
 """
 from __future__ import annotations
@@ -19,7 +19,8 @@ import math
 
 import numpy as np
 
-DTYPES = {"u32": np.uint32, "u64": np.uint64, "f32": np.float32}
+DTYPES = {"u32": np.uint32, "u64": np.uint64, "f32": np.float32, "i32": np.int32,
+          "i64": np.int64, "f64": np.float64}
 DISTRIBUTIONS = ("uniform", "gaussian", "sorted", "reverse", "distinct16", "zipf")
 PAPER_SETS = ("random1e6", "distinct", "zero_one", "dup2", "dup16", "dup2250")
 
@@ -40,10 +41,26 @@ def large_sort_seed(dist: str, dtype: str, n: int) -> int:
 
 
 def _uniform_bits(g, n, dtype):
-    if dtype == "u64":
-        return g.integers(0, 2**64, size=n, dtype=np.uint64, endpoint=False)
+    """Uniform random bit patterns of the key width, viewed as ``dtype``."""
+    if DTYPES[dtype]().itemsize == 8:
+        u = g.integers(0, 2**64, size=n, dtype=np.uint64, endpoint=False)
+        return u.view(DTYPES[dtype])
     u = g.integers(0, 2**32, size=n, dtype=np.uint64).astype(np.uint32)
-    return u.view(np.float32) if dtype == "f32" else u
+    return u.view(DTYPES[dtype])
+
+
+def _from_u32(u: np.ndarray, dtype: str) -> np.ndarray:
+    """u32 workload values carried to ``dtype`` by a monotone map: u64 widens,
+    f32 rounds to float32, i32 / i64 / f64 subtract 2^31 (so half the values are
+    negative)."""
+    if dtype == "u32":
+        return u
+    if dtype == "u64":
+        return u.astype(np.uint64)
+    if dtype == "f32":
+        return u.astype(np.float32)
+    s = u.astype(np.int64) - (1 << 31)
+    return s.astype(DTYPES[dtype])
 
 
 def sorted_uniform_u64(g, n: int, hi: float) -> np.ndarray:
@@ -65,13 +82,14 @@ def sorted_uniform_u64(g, n: int, hi: float) -> np.ndarray:
 
 
 def sorted_keys(g, n: int, dtype: str) -> np.ndarray:
-    """Non-decreasing keys of ``dtype`` (f32: float32 of sorted u32 values)."""
-    if dtype == "u64":
-        return sorted_uniform_u64(g, n, 2.0**64)
+    """Non-decreasing keys of ``dtype``: u64 sorted over [0, 2^64), i64 the same
+    values with the top bit flipped (x - 2^63); the other types are the sorted
+    u32 values carried over by :func:`_from_u32`."""
+    if dtype in ("u64", "i64"):
+        u = sorted_uniform_u64(g, n, 2.0**64)
+        return u if dtype == "u64" else (u ^ np.uint64(1 << 63)).view(np.int64)
     u = sorted_uniform_u64(g, n, 2.0**32).astype(np.uint32)
-    if dtype == "f32":
-        return u.astype(np.float32)
-    return u
+    return _from_u32(u, dtype)
 
 
 def gaussian_u32(g, n: int) -> np.ndarray:
@@ -92,17 +110,19 @@ def zipf_ranks(g, n: int, s: float = 1.1, symbols: int = 1 << 20) -> np.ndarray:
 def keys(dist: str, dtype: str, n: int, seed: int | None = None) -> np.ndarray:
     """Keys of the large-sort workload family (``dist`` in DISTRIBUTIONS).
 
-    uniform   : u32 / u64 uniform over the full range; f32 = uniform random
-                32-bit patterns (NaNs, infinities, subnormals and both zeros
-                included, to exercise the total order).
+    uniform   : uniform random bit patterns of the key width (u32 / u64 /
+                i32 / i64 over their full range; f32 / f64 with NaNs,
+                infinities, subnormals and both zeros included, to exercise
+                the total order).
     gaussian  : u32 = rint(N(2^31, 2^28)) clamped; u64 = the same values
-                widened; f32 = float32 of the same values (many ties).
-    sorted    : non-decreasing by construction (exponential spacings); f32 =
-                float32 of sorted u32 values.
+                widened; f32 = float32 of the same values (many ties); i32 /
+                i64 / f64 = the same values minus 2^31.
+    sorted    : non-decreasing by construction (exponential spacings).
     reverse   : ``sorted`` read backwards.
     distinct16: 16 values drawn from the uniform law, each element picks one.
     zipf      : rank r ~ Zipf(1.1) over 2^20 symbols, key = (r-1)*golden mod
-                2^32 (u32) or 2^64 (u64); f32 = float32 of the u32 key.
+                2^64 (u64; its bits for i64) or mod 2^32 (u32; f32 = float32
+                of it; i32 = its bits; f64 = its value minus 2^31).
     """
     if seed is None:
         seed = large_sort_seed(dist, dtype, n)
@@ -110,10 +130,7 @@ def keys(dist: str, dtype: str, n: int, seed: int | None = None) -> np.ndarray:
     if dist == "uniform":
         return _uniform_bits(g, n, dtype)
     if dist == "gaussian":
-        u = gaussian_u32(g, n)
-        if dtype == "u64":
-            return u.astype(np.uint64)
-        return u.astype(np.float32) if dtype == "f32" else u
+        return _from_u32(gaussian_u32(g, n), dtype)
     if dist == "sorted":
         return sorted_keys(g, n, dtype)
     if dist == "reverse":
@@ -123,10 +140,10 @@ def keys(dist: str, dtype: str, n: int, seed: int | None = None) -> np.ndarray:
         return pool[g.integers(0, 16, size=n)]
     if dist == "zipf":
         r = zipf_ranks(g, n) - 1
-        if dtype == "u64":
-            return r * np.uint64(_GOLDEN64)  # wraps mod 2^64
+        if dtype in ("u64", "i64"):
+            return (r * np.uint64(_GOLDEN64)).view(DTYPES[dtype])  # wraps mod 2^64
         u = ((r * np.uint64(_GOLDEN32)) & np.uint64(0xFFFFFFFF)).astype(np.uint32)
-        return u.astype(np.float32) if dtype == "f32" else u
+        return u.view(np.int32) if dtype == "i32" else _from_u32(u, dtype)
     raise ValueError(f"unknown distribution {dist!r}")
 
 
@@ -232,3 +249,4 @@ def request_trace(rate_hz: float = 2000.0, duration_s: float = 10.0, lo: int = 1
     n = log_uniform_sizes(g, t.size, lo, hi)
     pairs = g.random(t.size) < pairs_fraction
     return {"t": t, "n": n, "pairs": pairs}
+
