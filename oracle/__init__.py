@@ -14,6 +14,8 @@ Each function states the definition it computes:
 * :func:`merge_runs` -- "merge sorted sequences" (Sec. 3.2, Algorithm 6): the
   stable sort of the runs concatenated in run order.
 * :func:`segmented_sort` -- :func:`sort` applied to every segment.
+* :func:`colored_prefix_sums` -- d independent prefix sums, one per color
+  (Appendix A), modulo 2^32, inclusive or exclusive.
 
 Every function is pinned by ``tests/test_oracle_pins.py``; none is unpinned.
 """
@@ -68,6 +70,8 @@ def load(path: str | None = None):
         lib.oracle_segmented_sort.restype = i32
         lib.oracle_key_less.argtypes = [i32, u64, u64]
         lib.oracle_key_less.restype = i32
+        lib.oracle_colored_prefix_sums.argtypes = [vp, vp, vp, u64, u32, i32]
+        lib.oracle_colored_prefix_sums.restype = i32
         if path is None:
             _lib = lib
         return lib
@@ -140,3 +144,18 @@ def key_less(dtype, a: int, b: int, lib=None) -> bool:
     lib = lib or load()
     return bool(lib.oracle_key_less(_DTYPE_CODE[np.dtype(dtype)], int(a), int(b)))
 
+
+def colored_prefix_sums(values, colors, d: int, exclusive: bool = False, lib=None):
+    """``out[i]`` = sum (mod 2^32) of ``values[j]`` over ``j <= i`` (``j < i`` if
+    exclusive) with ``colors[j] == colors[i]``."""
+    lib = lib or load()
+    values = np.ascontiguousarray(values, dtype=np.uint32)
+    colors = np.ascontiguousarray(colors, dtype=np.uint8)
+    if values.shape != colors.shape:
+        raise ValueError("oracle: values and colors differ in length")
+    out = np.empty_like(values)
+    rc = lib.oracle_colored_prefix_sums(_ptr(out), _ptr(values), _ptr(colors), values.size,
+                                        int(d), int(bool(exclusive)))
+    if rc != 0:
+        raise RuntimeError("oracle_colored_prefix_sums failed (color >= d or bad d)")
+    return out

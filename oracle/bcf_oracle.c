@@ -21,6 +21,8 @@
  *                 sort of the runs concatenated in index order.
  *   segmented     the sort above applied to every segment [off[i], off[i+1])
  *                 independently.
+ *   colored prefix sums (Appendix A): d independent prefix sums, one per
+ *                 color, over a sequence of (value, color) elements.
  *
  * Method.  A top-down merge sort over a permutation array with one auxiliary
  * buffer (the textbook mergesort the paper builds on, Sec. 3 and Knuth vol. 3).
@@ -290,3 +292,33 @@ int oracle_segmented_sort(void* keys_out, uint32_t* vals_out, const void* keys_i
     return 0;
 }
 
+/* ---- colored prefix sums ------------------------------------------------ */
+
+/* Colored prefix sums (Appendix A; the experiment of Sec. 2.2): every element
+ * i carries a value v[i] and a color c[i] in [0, d); out[i] is the sum of the
+ * values of the elements of color c[i] at positions <= i (inclusive) or < i
+ * (exclusive), i.e. d independent prefix sums, one per color.  Sums are taken
+ * modulo 2^32 (unsigned 32-bit arithmetic).  Plain definition, one running
+ * sum per color.  Returns 0, or -1 for a color >= d or d outside [1, 256]. */
+int oracle_colored_prefix_sums(uint32_t* out, const uint32_t* values, const uint8_t* colors,
+                               uint64_t n, uint32_t d, int exclusive)
+{
+    if (d < 1 || d > 256)
+        return -1;
+    uint32_t acc[256];
+    for (uint32_t c = 0; c < d; ++c)
+        acc[c] = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+        uint32_t c = colors[i];
+        if (c >= d)
+            return -1;
+        if (exclusive) {
+            out[i] = acc[c];
+            acc[c] += values[i];
+        } else {
+            acc[c] += values[i];
+            out[i] = acc[c];
+        }
+    }
+    return 0;
+}

@@ -250,3 +250,28 @@ def request_trace(rate_hz: float = 2000.0, duration_s: float = 10.0, lo: int = 1
     pairs = g.random(t.size) < pairs_fraction
     return {"t": t, "n": n, "pairs": pairs}
 
+
+def colored_elements(n: int, d: int, seed: int = 6000, law: str = "uniform"):
+    """Inputs of the colored prefix sums (Appendix A): ``values`` uniform u32
+    over the full range (so sums wrap modulo 2^32) and ``colors`` u8 in [0, d).
+
+    law "uniform": every color equally likely; "skewed": color c drawn with
+    probability proportional to 2^-c (a few colors dominate); "runs": runs of
+    one color with geometric lengths (mean 64).
+    """
+    g = rng(seed)
+    values = g.integers(0, 2**32, size=n, dtype=np.uint64).astype(np.uint32)
+    if law == "uniform":
+        colors = g.integers(0, d, size=n)
+    elif law == "skewed":
+        p = 2.0 ** -np.arange(d)
+        colors = g.choice(d, size=n, p=p / p.sum())
+    elif law == "runs":
+        lens = g.geometric(1.0 / 64, size=n // 8 + 2)
+        cols = g.integers(0, d, size=lens.size)
+        colors = np.repeat(cols, lens)[:n]
+        if colors.size < n:
+            colors = np.concatenate([colors, np.zeros(n - colors.size, np.int64)])
+    else:
+        raise ValueError(f"unknown color law {law!r}")
+    return values, colors.astype(np.uint8)
