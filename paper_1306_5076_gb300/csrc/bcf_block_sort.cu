@@ -101,21 +101,13 @@ __global__ void __launch_bounds__(NT) block_sort_kernel(const BlockSortArgs a) {
   if (a.samples && (p0 % kSampleStride) == 0 && p0 < cnt)
     static_cast<K*>(a.samples)[(base + p0) / kSampleStride] = f.k[0];
   if (p0 + E <= cnt) {
+    // base and p0 are multiples of 32 bytes: the base pointers decide alignment
+    if constexpr (MAP) {
 #pragma unroll
-    for (int q = 0; q < E / V; ++q) {
-      KV kv;
-      K* kp = reinterpret_cast<K*>(&kv);
-#pragma unroll
-      for (int c = 0; c < V; ++c)
-        kp[c] = MAP ? unmap_key(f.k[q * V + c], mode_out) : f.k[q * V + c];
-      *reinterpret_cast<KV*>(kout + p0 + q * V) = kv;
+      for (int e = 0; e < E; ++e) f.k[e] = unmap_key(f.k[e], mode_out);  // last use of f.k
     }
-    if constexpr (PAIRS) {
-#pragma unroll
-      for (int q = 0; q < E / 4; ++q)
-        *reinterpret_cast<uint4*>(vout + p0 + 4 * q) =
-            make_uint4(f.v[4 * q], f.v[4 * q + 1], f.v[4 * q + 2], f.v[4 * q + 3]);
-    }
+    store_run<E>(kout + p0, f.k, is_aligned32(a.kout));
+    if constexpr (PAIRS) store_run<E>(vout + p0, f.v, is_aligned32(a.vout));
   } else {
 #pragma unroll
     for (int e = 0; e < E; ++e) {

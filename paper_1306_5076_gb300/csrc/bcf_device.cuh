@@ -156,6 +156,47 @@ __device__ __forceinline__ uint64_t lds_pred(const uint64_t* p, bool pred, uint6
   return v;
 }
 
+// 32-byte global stores (sm_100 and later): each thread writes one whole
+// 32-byte sector, so a warp storing its threads' consecutive runs touches
+// full sectors only, with half the store instructions of 16-byte vectors.
+// `p` must be 32-byte aligned.
+__device__ __forceinline__ void st_global_32B(uint32_t* p, const uint32_t* x) {
+  asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(x[0]),
+               "r"(x[1]), "r"(x[2]), "r"(x[3]), "r"(x[4]), "r"(x[5]), "r"(x[6]), "r"(x[7])
+               : "memory");
+}
+__device__ __forceinline__ void st_global_32B(uint64_t* p, const uint64_t* x) {
+  asm volatile("st.global.v4.b64 [%0], {%1, %2, %3, %4};" ::"l"(p), "l"(x[0]), "l"(x[1]),
+               "l"(x[2]), "l"(x[3])
+               : "memory");
+}
+
+// Stores E consecutive elements x[0..E) of one thread at p (E * sizeof(K) a
+// multiple of 32): 32-byte stores when p is 32-byte aligned, else 16-byte.
+template <int E, typename K>
+__device__ __forceinline__ void store_run(K* p, const K* x, bool aligned32) {
+  constexpr int V32 = 32 / sizeof(K), V16 = 16 / sizeof(K);
+  static_assert((E * sizeof(K)) % 32 == 0, "run must be whole 32-byte sectors");
+  if (aligned32) {
+#pragma unroll
+    for (int q = 0; q < E / V32; ++q) st_global_32B(p + q * V32, x + q * V32);
+  } else {
+    using KV = typename std::conditional<sizeof(K) == 4, uint4, ulonglong2>::type;
+#pragma unroll
+    for (int q = 0; q < E / V16; ++q) {
+      KV kv;
+      K* kp = reinterpret_cast<K*>(&kv);
+#pragma unroll
+      for (int c = 0; c < V16; ++c) kp[c] = x[q * V16 + c];
+      *reinterpret_cast<KV*>(p + q * V16) = kv;
+    }
+  }
+}
+
+__device__ __forceinline__ bool is_aligned32(const void* p) {
+  return (reinterpret_cast<uintptr_t>(p) & 31u) == 0;
+}
+
 // ---------------------------------------------------------------- elements
 
 // Padded shared-memory index of logical word k (one pad word per 32 words).

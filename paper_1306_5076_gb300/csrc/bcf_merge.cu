@@ -337,22 +337,13 @@ __global__ void __launch_bounds__(NT) merge_kernel(const MergeArgs a,
   const uint32_t cnt = static_cast<uint32_t>(p.d1 - p.d0);
   const int mode_out = MAP ? a.mode_out : 0;
   if (s0 >= front && s0 + E <= front + cnt) {
-    using KV = typename std::conditional<sizeof(K) == 4, uint4, ulonglong2>::type;
+    // out0 and s0 are multiples of 32 bytes: the base pointers decide alignment
+    if constexpr (MAP) {
 #pragma unroll
-    for (int q = 0; q < E / static_cast<int>(VK); ++q) {
-      KV kv;
-      K* kp = reinterpret_cast<K*>(&kv);
-#pragma unroll
-      for (int c = 0; c < static_cast<int>(VK); ++c)
-        kp[c] = MAP ? unmap_key(f.k[q * VK + c], mode_out) : f.k[q * VK + c];
-      *reinterpret_cast<KV*>(kout + s0 + q * VK) = kv;
+      for (int e = 0; e < E; ++e) f.k[e] = unmap_key(f.k[e], mode_out);  // last use of f.k
     }
-    if constexpr (PAIRS) {
-#pragma unroll
-      for (int q = 0; q < E / 4; ++q)
-        *reinterpret_cast<uint4*>(vout + s0 + 4 * q) =
-            make_uint4(f.v[4 * q], f.v[4 * q + 1], f.v[4 * q + 2], f.v[4 * q + 3]);
-    }
+    store_run<E>(kout + s0, f.k, is_aligned32(a.kout));
+    if constexpr (PAIRS) store_run<E>(vout + s0, f.v, is_aligned32(a.vout));
   } else {
 #pragma unroll
     for (int e = 0; e < E; ++e) {

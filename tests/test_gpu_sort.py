@@ -219,3 +219,34 @@ def test_full_size_bench_config_against_oracle(bcf):
 
     exp, _ = oracle.sort(keys, nthreads=os.cpu_count() or 8)
     assert np.array_equal(got, exp)
+
+
+@pytest.mark.parametrize("dtype", ["u32", "u64", "f64"])
+@pytest.mark.parametrize("n", [8192, 3 * 16384 + 40, (1 << 20) + 8])
+def test_outputs_16_but_not_32_byte_aligned(bcf, dtype, n):
+    """The ABI asks for 16-byte alignment only: outputs (and inputs) that start
+    16 bytes past a 32-byte boundary take the 16-byte store path."""
+    keys = workloads.keys("uniform", dtype, n, seed=77)
+    vals = workloads.row_index(n)
+    per16 = 16 // keys.dtype.itemsize  # elements in 16 bytes
+    kin = torch.zeros(n + 2 * per16, dtype=to_dev(keys[:1]).dtype, device="cuda")
+    vin = torch.zeros(n + 8, dtype=torch.int32, device="cuda")
+    kin[per16:per16 + n] = to_dev(keys)
+    vin[4:4 + n] = to_dev(vals)
+    kout = torch.zeros_like(kin)
+    vout = torch.zeros_like(vin)
+    ki, ko = kin[per16:per16 + n], kout[per16:per16 + n]
+    vi, vo = vin[4:4 + n], vout[4:4 + n]
+    assert ko.data_ptr() % 32 == 16 and vo.data_ptr() % 32 == 16
+    kt = kt_of(keys)
+    for desc in (False, True):
+        bcf.bcf_sort_pairs(ko, vo, ki, vi, kt=kt, descending=desc)
+        torch.cuda.synchronize()
+        ek, ev = oracle.sort(keys, vals, descending=desc)
+        assert_same(from_dev(ko, keys.dtype), from_dev(vo, np.uint32), ek, ev)
+        bcf.bcf_sort_keys(ko, ki, kt=kt, descending=desc)
+        torch.cuda.synchronize()
+        assert_same(from_dev(ko, keys.dtype), None, ek, None)
+    # nothing written outside the output slices
+    assert not kout[:per16].any() and not kout[per16 + n:].any()
+    assert not vout[:4].any() and not vout[4 + n:].any()
