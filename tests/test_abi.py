@@ -68,6 +68,13 @@ def test_workspace_bytes_scale_with_input(lib):
     for kt, same in ((BCF_I32, keys), (BCF_I64, wide), (BCF_F64, wide)):
         assert lib.bcf_workspace_bytes(BCF_OP_SORT, n, 0, kt, 0) == same
     assert lib.bcf_workspace_bytes(BCF_OP_SORT, n, 0, 6, 0) == 0
+    # colored prefix sums: one look-back word per (tile, color); u32 values only
+    from paper_1306_5076_gb300 import BCF_OP_CPS
+    cps = lib.bcf_workspace_bytes(BCF_OP_CPS, n, 16, BCF_U32, 0)
+    assert cps >= (n // 4096) * 16 * 8 and cps % 256 == 0
+    assert lib.bcf_workspace_bytes(BCF_OP_CPS, n, 0, BCF_U32, 0) == 0
+    assert lib.bcf_workspace_bytes(BCF_OP_CPS, n, 65, BCF_U32, 0) == 0
+    assert lib.bcf_workspace_bytes(BCF_OP_CPS, n, 16, BCF_U64, 0) == 0
     assert lib.bcf_workspace_bytes(BCF_OP_MERGE, n, 256, BCF_U32, 0) >= keys
     assert lib.bcf_workspace_bytes(9, n, 0, BCF_U32, 0) == 0
     assert lib.bcf_workspace_bytes(BCF_OP_SORT, n, 0, 7, 0) == 0
@@ -118,6 +125,12 @@ def test_host_side_argument_errors_return_before_launch(lib):
     assert lib.bcf_merge_runs(None, None, None, None, offs, 0, 0, opts, None, 0, None) == EINVAL
     assert lib.bcf_merge_runs(ctypes.c_void_p(0x10000), None, ctypes.c_void_p(0x20000), None,
                               offs, 2, 0, opts, None, 0, None) == EINVAL
+    # colored prefix sums: d outside 1..64, layout unknown, null pointers
+    assert lib.bcf_colored_prefix_sums(None, None, None, 10, 0, 0, 0, None, 0, None) == EINVAL
+    assert lib.bcf_colored_prefix_sums(None, None, None, 10, 65, 0, 0, None, 0, None) == EINVAL
+    assert lib.bcf_colored_prefix_sums(None, None, None, 10, 4, 0, 2, None, 0, None) == EINVAL
+    assert lib.bcf_colored_prefix_sums(None, None, None, 10, 4, 0, 0, None, 0, None) == EINVAL
+    assert lib.bcf_colored_prefix_sums(None, None, None, 0, 4, 0, 0, None, 0, None) == 0
     # merge: values on one side only
     good = (ctypes.c_uint64 * 2)(0, 4)
     assert lib.bcf_merge_runs(ctypes.c_void_p(0x10000), ctypes.c_void_p(0x30000),
@@ -150,5 +163,5 @@ def test_committed_tuning_table_rows_are_valid(lib):
         bcf.bcf_tuning_set([r])  # raises BcfError(EINVAL) for an unbuilt configuration
     bcf.bcf_tuning_set(None)
     with pytest.raises(bcf.BcfError):
-        bcf.bcf_tuning_set([dict(op=0, key_bytes=4, has_vals=1, n_min=0, n_max=10, block_cfg=1,
-                                 merge_cfg=0, seg_cfg=0)])  # E = 32 is not built for pairs
+        bcf.bcf_tuning_set([dict(op=0, key_bytes=8, has_vals=1, n_min=0, n_max=10, block_cfg=1,
+                                 merge_cfg=0, seg_cfg=0)])  # no E = 32 for 64-bit pairs
