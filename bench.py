@@ -275,6 +275,102 @@ def serving_bench(torch, dev, seconds, rate=2000.0, seed=5000):
             "offered_keys_per_s": float(sizes.sum()) / seconds, **res}
 
 
+def timed_ms(torch, stream, fn, warmup=3, reps=10):
+    """Mean CUDA-event time of fn() on `stream` (inputs larger than L2)."""
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def key_types_bench(torch, dev, bcf, peak, log2n=LOG2N):
+    """Keys-only and pairs sorts of 2^log2n uniform keys of every key type:
+    whole-sort time and the merge pass against the HBM roofline."""
+    import numpy as np
+
+    import workloads
+
+    n = 1 << log2n
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    codes = {"u32": bcf.BCF_U32, "i32": bcf.BCF_I32, "f32": bcf.BCF_F32, "u64": bcf.BCF_U64,
+             "i64": bcf.BCF_I64, "f64": bcf.BCF_F64}
+    for name, kt in codes.items():
+        for pairs in (False, True):
+            if pairs and name not in ("u32", "u64"):
+                continue
+            keys = workloads.keys("uniform", name, n)
+            kb = keys.dtype.itemsize
+            kd = torch.from_numpy(keys.view(np.int32 if kb == 4 else np.int64)).to(dev)
+            ko = torch.empty_like(kd)
+            vd = torch.arange(n, dtype=torch.int32, device=dev) if pairs else None
+            vo = torch.empty_like(vd) if pairs else None
+            ws = torch.empty(bcf.bcf_workspace_bytes(bcf.BCF_OP_SORT, n, 0, kt, pairs),
+                             dtype=torch.uint8, device=dev)
+            if pairs:
+                fn = lambda: bcf.bcf_sort_pairs(ko, vo, kd, vd, kt=kt, ws=ws, stream=stream)  # noqa: E731
+            else:
+                fn = lambda: bcf.bcf_sort_keys(ko, kd, kt=kt, ws=ws, stream=stream)  # noqa: E731
+            fn()
+            torch.cuda.synchronize()
+            bcf.bcf_profile_collect()
+            bcf.bcf_profile_enable(True)
+            ms = timed_ms(torch, stream, fn, warmup=2, reps=5)
+            bcf.bcf_profile_enable(False)
+            prof = bcf.bcf_profile_collect()
+            m = prof["merge"]
+            merge_ms = m["total_ms"] / max(m["launches"], 1)
+            plan = bcf.bcf_sort_plan(n, kt, pairs)
+            gbs = plan["bytes_per_pass"] / (merge_ms * 1e-3) / 1e9
+            out[name + ("+u32" if pairs else "")] = {
+                "ms": ms, "keys_per_s": n / (ms * 1e-3), "merge_pass_ms": merge_ms,
+                "merge_pass_gbs": gbs, "merge_pass_frac": gbs / peak,
+                "block_sort_ms": prof["block_sort"]["total_ms"] / max(
+                    prof["block_sort"]["launches"], 1),
+                "merge_passes": plan["merge_passes"]}
+            del kd, ko, vd, vo, ws
+            torch.cuda.empty_cache()
+    return {"n": n, "distribution": "uniform", "results": out}
+
+
+def cps_bench(torch, dev, bcf, peak, log2n=29, colors=(1, 2, 4, 8, 16, 32, 64)):
+    """Colored prefix sums (Appendix A, the paper's Fig. 2 experiment): time
+    against the number of colors, conflict-free layout vs the row-per-thread
+    layout.  Algorithmic bytes: 4 (value) + 1 (color) + 4 (output) per element."""
+    import workloads
+
+    n = 1 << log2n
+    stream = torch.cuda.current_stream(dev)
+    vals_np, _ = workloads.colored_elements(n, 1, seed=29)
+    vd = torch.from_numpy(vals_np.view("int32")).to(dev)
+    od = torch.empty_like(vd)
+    ws = torch.empty(bcf.bcf_workspace_bytes(bcf.BCF_OP_CPS, n, max(colors), bcf.BCF_U32, 0),
+                     dtype=torch.uint8, device=dev)
+    res = {"banked": {}, "rows": {}}
+    for d in colors:
+        g = torch.Generator(device=dev)
+        g.manual_seed(d)
+        cd = torch.randint(0, d, (n,), dtype=torch.uint8, device=dev, generator=g)
+        for name, layout in (("banked", bcf.BCF_CPS_BANKED), ("rows", bcf.BCF_CPS_ROWS)):
+            ms = timed_ms(torch, stream, lambda: bcf.bcf_colored_prefix_sums(
+                od, vd, cd, d, layout=layout, ws=ws, stream=stream))
+            gbs = 9 * n / (ms * 1e-3) / 1e9
+            res[name][str(d)] = {"ms": ms, "elements_per_s": n / (ms * 1e-3), "gbs": gbs,
+                                 "frac": gbs / peak}
+        del cd
+    if bcf.bcf_last_device_error() != 0:
+        raise RuntimeError("colored prefix sums: device error word set")
+    return {"n": n, "values": "uniform u32", "colors": "uniform u8 in [0, d)",
+            "bytes_per_element": 9, **res}
+
+
 def run_gpu(args, world, rank, local, pg):
     import numpy as np
     import torch
@@ -366,17 +462,23 @@ def run_gpu(args, world, rank, local, pg):
     ok_e2e = bool(torch.equal(host_out, ko.cpu()))
 
     serving = None
+    ws = None  # the timed sorts are done: free the workspace for what follows
+    torch.cuda.empty_cache()
     if args.serve_seconds > 0:
-        del ws
         # the workload's trace (2000 req/s), then the same request mix at 8x the
         # rate, past what one launch chain per request can sustain
         serving = {"nominal": serving_bench(torch, dev, args.serve_seconds),
                    "stress_8x": serving_bench(torch, dev, min(2.0, args.serve_seconds),
                                               rate=16000.0)}
 
+    peak, peak_kind = measured_peaks()
+    extras = None
+    if not args.no_extras:
+        extras = {"key_types": key_types_bench(torch, dev, bcf, peak),
+                  "colored_prefix_sums": cps_bench(torch, dev, bcf, peak)}
+
     if rank != 0:
         return 0
-    peak, peak_kind = measured_peaks()
     m = prof["merge"]
     merge_ms = m["total_ms"] / max(m["launches"], 1)
     achieved = plan["bytes_per_pass"] / (merge_ms * 1e-3) / 1e9
@@ -428,6 +530,8 @@ def run_gpu(args, world, rank, local, pg):
         line["cpu_baseline"] = cpu
     if serving is not None:
         line["serving"] = serving
+    if extras is not None:
+        line.update(extras)
     print(json.dumps(line))
     return 0
 
@@ -439,6 +543,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the other key types and the colored prefix sums")
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="length of the served-vs-plain request trace (0: skip)")
     ap.add_argument("--log2n", type=int, default=LOG2N,

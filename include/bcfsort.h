@@ -73,19 +73,38 @@ typedef enum {
     BCF_EUNSUPPORTED = 5  /* valid request this build does not handle (e.g. too many segments) */
 } bcf_status;
 
+/* Sorting algorithms (bcf_opts.algorithm).  Both give the identical, stable
+ * result; they differ in speed by input distribution. */
+enum {
+    BCF_ALGO_MERGE = 0,        /* block sort + ceil(log2(n / T)) merge passes (Sec. 3.2) */
+    BCF_ALGO_PIVOT_BUCKETS = 1 /* BCFMergesortPB (Sec. 3.2, "Duplicate keys"): the block
+                                * sort, then a distribution into 255 splitter buckets
+                                * plus one bucket per splitter for the keys equal to it;
+                                * the equal buckets are final, the others are sorted by
+                                * the segmented sort.  Fastest on duplicate-heavy keys;
+                                * needs bcf_workspace_bytes(BCF_OP_SORT_PB, ...) and
+                                * n < 2^32 (larger n takes the merge path). */
+};
+
 typedef struct {
     int descending;      /* 0: ascending, 1: descending (ties keep input order) */
     int stable_required; /* accepted for API symmetry; output is always stable */
-} bcf_opts;              /* a NULL bcf_opts* means ascending */
+    int algorithm;       /* BCF_ALGO_MERGE (default) or BCF_ALGO_PIVOT_BUCKETS */
+} bcf_opts;              /* a NULL bcf_opts* means ascending, BCF_ALGO_MERGE */
 
 /* Operation codes for bcf_workspace_bytes. */
-enum { BCF_OP_SORT = 0, BCF_OP_MERGE = 1, BCF_OP_SEGMENTED = 2 };
+enum { BCF_OP_SORT = 0, BCF_OP_MERGE = 1, BCF_OP_SEGMENTED = 2, BCF_OP_CPS = 3,
+       BCF_OP_SORT_PB = 4 };
 
 /*
  * Workspace size in bytes for an operation.
  *   op        BCF_OP_SORT: sort n keys (pairs if has_vals);
  *             BCF_OP_MERGE: merge nseg_or_k runs totalling n keys;
- *             BCF_OP_SEGMENTED: nseg_or_k segments totalling n keys.
+ *             BCF_OP_SEGMENTED: nseg_or_k segments totalling n keys;
+ *             BCF_OP_CPS: colored prefix sums of n elements with nseg_or_k
+ *             colors (kt must be BCF_U32, has_vals 0);
+ *             BCF_OP_SORT_PB: sort n keys with BCF_ALGO_PIVOT_BUCKETS (pairs if
+ *             has_vals; also enough for BCF_ALGO_MERGE).
  * Returns 0 for an unknown op or dtype.  The size is about one extra copy of
  * the keys (+ values) -- the merge is not in place, as in the paper (Sec. 4
  * remarks that BCFMergesort needs less extra space than its competitors) --
@@ -153,7 +172,9 @@ const char* bcf_status_string(bcf_status status);
 /*
  * Synchronise `stream`, then read and clear the current device's error word.
  * Returns BCF_ETIMEOUT if a kernel's bounded wait ran out since the last call,
- * BCF_ECUDA if the synchronisation failed, else BCF_OK.
+ * BCF_EINVAL if the only error seen was a color >= d in
+ * bcf_colored_prefix_sums, BCF_ECUDA if the synchronisation failed, else
+ * BCF_OK.
  */
 bcf_status bcf_last_device_error(cudaStream_t stream);
 
@@ -174,11 +195,14 @@ bcf_status bcf_sort_plan(uint64_t n, bcf_dtype kt, int has_vals, bcf_plan* plan)
  * Per-kernel timing of the library's own launches, for benchmarking.  When
  * enabled, the library brackets every kernel it launches with CUDA events on
  * the launch stream (events are created once, on first use).  Kinds:
- * 0 block sort, 1 merge-path partition, 2 merge pass, 3 segmented sort.
+ * 0 block sort, 1 merge-path partition, 2 merge pass, 3 segmented sort,
+ * 4 colored prefix sums, 5 pivot-bucket distribution (sampling, splitters,
+ * bucket counts, scatter).
  */
+#define BCF_PROFILE_KINDS 6
 typedef struct {
-    uint32_t launches[4];
-    double total_ms[4];
+    uint32_t launches[BCF_PROFILE_KINDS];
+    double total_ms[BCF_PROFILE_KINDS];
 } bcf_profile;
 
 bcf_status bcf_profile_enable(int on);
@@ -187,6 +211,36 @@ bcf_status bcf_profile_collect(bcf_profile* out);
 
 /* Version string of the library. */
 const char* bcf_version(void);
+
+/* ---- colored prefix sums ------------------------------------------------ */
+
+/*
+ * Colored prefix sums: the paper's demonstration that bank conflicts decide
+ * the runtime (Sec. 2.2, Fig. 2; algorithm in Appendix A).  Element i has a
+ * value values[i] and a color colors[i] in [0, d); out[i] is the sum, modulo
+ * 2^32, of values[j] over the j <= i (exclusive: j < i) with colors[j] ==
+ * colors[i] -- d independent prefix sums in one pass over the data.
+ *   out       device, n uint32_t; may equal `values` exactly (in place)
+ *   values    device, n uint32_t
+ *   colors    device, n uint8_t, each < d
+ *   d         number of colors, 1..64 (the paper stops at 16 for lack of
+ *             shared memory; one CTA holds d x 256 counters)
+ *   exclusive 0: inclusive sums; 1: exclusive
+ *   layout    BCF_CPS_BANKED: every thread keeps its per-color counters in
+ *             its own shared-memory bank (the paper's conflict-free layout);
+ *             BCF_CPS_ROWS: a thread's d counters are contiguous, so lanes
+ *             collide on banks as d grows (the paper's conflicting baseline,
+ *             kept for that comparison).  Results are identical.
+ *   ws        workspace of bcf_workspace_bytes(BCF_OP_CPS, n, d, BCF_U32, 0)
+ *             bytes (per-tile, per-color look-back words); cleared by the call
+ * Pointers must be 16-byte aligned.  A color >= d is a precondition
+ * violation: that element adds nothing, its output is 0, and
+ * bcf_last_device_error() then returns BCF_EINVAL.
+ */
+enum { BCF_CPS_BANKED = 0, BCF_CPS_ROWS = 1 };
+bcf_status bcf_colored_prefix_sums(uint32_t* out, const uint32_t* values, const uint8_t* colors,
+                                   uint64_t n, uint32_t d, int exclusive, int layout, void* ws,
+                                   size_t ws_bytes, cudaStream_t stream);
 
 /* ---- tuning --------------------------------------------------------------- */
 

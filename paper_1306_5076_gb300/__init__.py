@@ -15,8 +15,9 @@ from __future__ import annotations
 import ctypes
 
 from . import _native
-from ._native import (BCF_F32, BCF_F64, BCF_I32, BCF_I64, BCF_OP_MERGE, BCF_OP_SEGMENTED,
-                      BCF_OP_SORT, BCF_U32, BCF_U64)
+from ._native import (BCF_ALGO_MERGE, BCF_ALGO_PIVOT_BUCKETS, BCF_CPS_BANKED, BCF_CPS_ROWS,
+                      BCF_F32, BCF_F64, BCF_I32, BCF_I64, BCF_OP_CPS, BCF_OP_MERGE,
+                      BCF_OP_SEGMENTED, BCF_OP_SORT, BCF_OP_SORT_PB, BCF_U32, BCF_U64)
 
 __all__ = [
     "BcfError", "bcf_workspace_bytes", "bcf_sort_keys", "bcf_sort_pairs", "bcf_merge_runs",
@@ -24,7 +25,9 @@ __all__ = [
     "bcf_profile_collect", "bcf_version", "bcf_sort_keys_static", "bcf_tuning_set",
     "bcf_tuning_config", "bcf_tuning_supported", "key_dtype_of", "BCF_U32",
     "BCF_U64", "BCF_F32", "BCF_I32", "BCF_I64", "BCF_F64",
-    "BCF_OP_SORT", "BCF_OP_MERGE", "BCF_OP_SEGMENTED",
+    "BCF_OP_SORT", "BCF_OP_MERGE", "BCF_OP_SEGMENTED", "BCF_OP_CPS",
+    "bcf_colored_prefix_sums", "BCF_CPS_BANKED", "BCF_CPS_ROWS", "BCF_OP_SORT_PB",
+    "BCF_ALGO_MERGE", "BCF_ALGO_PIVOT_BUCKETS",
 ]
 
 
@@ -74,8 +77,15 @@ def _stream(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def _opts(descending: bool):
-    return ctypes.byref(_native.BcfOpts(int(bool(descending)), 1))
+_ALGORITHMS = {"merge": 0, "pivot_buckets": 1}
+
+
+def _opts(descending: bool, algorithm: str = "merge"):
+    try:
+        algo = _ALGORITHMS[algorithm]
+    except KeyError:
+        raise ValueError(f"unknown algorithm {algorithm!r} (merge, pivot_buckets)") from None
+    return ctypes.byref(_native.BcfOpts(int(bool(descending)), 1, algo))
 
 
 def _workspace(op, n, k, kt, has_vals, ws, device):
@@ -91,26 +101,34 @@ def bcf_workspace_bytes(op: int, n: int, nseg_or_k: int, kt: int, has_vals: bool
     return int(_native.load().bcf_workspace_bytes(op, n, nseg_or_k, kt, int(bool(has_vals))))
 
 
-def bcf_sort_keys(keys_out, keys_in, *, descending=False, ws=None, stream=None, kt=None):
-    """Sort ``keys_in`` into ``keys_out`` (may be the same tensor)."""
+def _sort_op(algorithm: str) -> int:
+    return BCF_OP_SORT_PB if algorithm == "pivot_buckets" else BCF_OP_SORT
+
+
+def bcf_sort_keys(keys_out, keys_in, *, descending=False, ws=None, stream=None, kt=None,
+                  algorithm="merge"):
+    """Sort ``keys_in`` into ``keys_out`` (may be the same tensor).  ``algorithm``:
+    "merge" (block sort + merge passes) or "pivot_buckets" (BCFMergesortPB)."""
     kt = key_dtype_of(keys_in) if kt is None else kt
     n = keys_in.numel()
-    ws, wsb = _workspace(BCF_OP_SORT, n, 0, kt, False, ws, keys_in.device)
-    _check(_native.load().bcf_sort_keys(_ptr(keys_out), _ptr(keys_in), n, kt, _opts(descending),
+    opts = _opts(descending, algorithm)
+    ws, wsb = _workspace(_sort_op(algorithm), n, 0, kt, False, ws, keys_in.device)
+    _check(_native.load().bcf_sort_keys(_ptr(keys_out), _ptr(keys_in), n, kt, opts,
                                         _ptr(ws), wsb, _stream(stream)), "bcf_sort_keys")
     return keys_out
 
 
 def bcf_sort_pairs(keys_out, vals_out, keys_in, vals_in, *, descending=False, ws=None,
-                   stream=None, kt=None):
-    """Stable sort of (key, value) pairs."""
+                   stream=None, kt=None, algorithm="merge"):
+    """Stable sort of (key, value) pairs (``algorithm`` as for :func:`bcf_sort_keys`)."""
     kt = key_dtype_of(keys_in) if kt is None else kt
     n = keys_in.numel()
     if vals_in.numel() != n or vals_out.numel() != n or keys_out.numel() != n:
         raise ValueError("bcf_sort_pairs: length mismatch")
-    ws, wsb = _workspace(BCF_OP_SORT, n, 0, kt, True, ws, keys_in.device)
+    opts = _opts(descending, algorithm)
+    ws, wsb = _workspace(_sort_op(algorithm), n, 0, kt, True, ws, keys_in.device)
     _check(_native.load().bcf_sort_pairs(_ptr(keys_out), _ptr(vals_out), _ptr(keys_in),
-                                         _ptr(vals_in), n, kt, _opts(descending), _ptr(ws), wsb,
+                                         _ptr(vals_in), n, kt, opts, _ptr(ws), wsb,
                                          _stream(stream)), "bcf_sort_pairs")
     return keys_out, vals_out
 
@@ -144,6 +162,28 @@ def bcf_segmented_sort(keys_out, vals_out, keys_in, vals_in, seg_offsets, *, des
     return keys_out, vals_out
 
 
+def bcf_colored_prefix_sums(out, values, colors, d: int, *, exclusive=False,
+                            layout=BCF_CPS_BANKED, ws=None, stream=None):
+    """Colored prefix sums (Appendix A): ``out[i]`` = sum mod 2^32 of ``values[j]``
+    over ``j <= i`` (``j < i`` if exclusive) with ``colors[j] == colors[i]``.
+    ``values`` / ``out`` are 4-byte integer CUDA tensors, ``colors`` a uint8 CUDA
+    tensor with entries < d (1 <= d <= 64)."""
+    n = values.numel()
+    if colors.numel() != n or out.numel() != n:
+        raise ValueError("bcf_colored_prefix_sums: out, values and colors differ in length")
+    if values.element_size() != 4 or out.element_size() != 4 or colors.element_size() != 1:
+        raise TypeError("bcf_colored_prefix_sums: 4-byte values/out and 1-byte colors expected")
+    need = _native.load().bcf_workspace_bytes(BCF_OP_CPS, n, d, BCF_U32, 0)
+    if need == 0 and n > 0:
+        raise BcfError(1, "bcf_colored_prefix_sums: d must be in 1..64")
+    ws, wsb = _workspace(BCF_OP_CPS, n, d, BCF_U32, False, ws, values.device)
+    _check(_native.load().bcf_colored_prefix_sums(_ptr(out), _ptr(values), _ptr(colors), n, d,
+                                                  int(bool(exclusive)), int(layout), _ptr(ws),
+                                                  wsb, _stream(stream)),
+           "bcf_colored_prefix_sums")
+    return out
+
+
 def bcf_last_device_error(stream=None) -> int:
     return int(_native.load().bcf_last_device_error(_stream(stream)))
 
@@ -162,7 +202,8 @@ def bcf_profile_enable(on: bool = True) -> None:
 def bcf_profile_collect() -> dict:
     p = _native.BcfProfile()
     _check(_native.load().bcf_profile_collect(ctypes.byref(p)), "bcf_profile_collect")
-    kinds = ("block_sort", "partition", "merge", "segmented")
+    kinds = ("block_sort", "partition", "merge", "segmented", "colored_prefix_sums",
+             "pivot_buckets")
     return {k: {"launches": int(p.launches[i]), "total_ms": float(p.total_ms[i])}
             for i, k in enumerate(kinds)}
 

@@ -13,13 +13,16 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libbcfsort.so")
 
 BCF_U32, BCF_U64, BCF_F32, BCF_I32, BCF_I64, BCF_F64 = 0, 1, 2, 3, 4, 5
-BCF_OP_SORT, BCF_OP_MERGE, BCF_OP_SEGMENTED = 0, 1, 2
+BCF_CPS_BANKED, BCF_CPS_ROWS = 0, 1
+BCF_OP_SORT, BCF_OP_MERGE, BCF_OP_SEGMENTED, BCF_OP_CPS, BCF_OP_SORT_PB = 0, 1, 2, 3, 4
+BCF_ALGO_MERGE, BCF_ALGO_PIVOT_BUCKETS = 0, 1
 STATUS = {0: "BCF_OK", 1: "BCF_EINVAL", 2: "BCF_ENOMEM", 3: "BCF_ECUDA", 4: "BCF_ETIMEOUT",
           5: "BCF_EUNSUPPORTED"}
 
 
 class BcfOpts(ctypes.Structure):
-    _fields_ = [("descending", ctypes.c_int), ("stable_required", ctypes.c_int)]
+    _fields_ = [("descending", ctypes.c_int), ("stable_required", ctypes.c_int),
+                ("algorithm", ctypes.c_int)]
 
 
 class BcfPlan(ctypes.Structure):
@@ -34,8 +37,12 @@ class BcfTuningEntry(ctypes.Structure):
                 ("block_cfg", ctypes.c_int), ("merge_cfg", ctypes.c_int), ("seg_cfg", ctypes.c_int)]
 
 
+BCF_PROFILE_KINDS = 6
+
+
 class BcfProfile(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_uint32 * 4), ("total_ms", ctypes.c_double * 4)]
+    _fields_ = [("launches", ctypes.c_uint32 * BCF_PROFILE_KINDS),
+                ("total_ms", ctypes.c_double * BCF_PROFILE_KINDS)]
 
 
 BCF_SERVE_BATCHED, BCF_SERVE_PLAIN = 0, 1
@@ -84,6 +91,7 @@ SIGNATURES = {
     "bcf_profile_collect": (_i32, [ctypes.POINTER(BcfProfile)]),
     "bcf_version": (ctypes.c_char_p, []),
     "bcf_sort_keys_static": (_i32, [_vp, _vp, _u64, _i32, ctypes.POINTER(BcfOpts), _vp]),
+    "bcf_colored_prefix_sums": (_i32, [_vp, _vp, _vp, _u64, _u32, _i32, _i32, _vp, _sz, _vp]),
     "bcf_tuning_set": (_i32, [ctypes.POINTER(BcfTuningEntry), _i32]),
     "bcf_tuning_config": (_i32, [_i32, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "bcf_tuning_supported": (_i32, [_i32, _i32, _i32, _i32]),

@@ -496,7 +496,8 @@ bcf_status run_merge(void* ko, uint32_t* vo, const void* ki, const uint32_t* vi,
 
 bcf_status run_segmented(void* ko, uint32_t* vo, const void* ki, const uint32_t* vi,
                          const uint64_t* off, uint64_t nseg, uint64_t n, bcf_dtype kt,
-                         const bcf_opts* o, void* ws, size_t ws_bytes, cudaStream_t s) {
+                         const bcf_opts* o, void* ws, size_t ws_bytes, cudaStream_t s,
+                         bool skip_odd = false) {
   const bool pairs = vo != nullptr || vi != nullptr;
   if (pairs && (!vo || !vi)) return BCF_EINVAL;
   bcf_status st = check_common(ko, vo, ki, vi, n, kt, pairs);
@@ -522,6 +523,7 @@ bcf_status run_segmented(void* ko, uint32_t* vo, const void* ki, const uint32_t*
   L.nseg = nseg;
   L.n = n;
   L.mode = mode_of(kt, o);
+  L.skip_odd = skip_odd ? 1 : 0;
   L.queue = wsb + wl.queue;
   L.capacity = wl.capacity;
   L.items_left = reinterpret_cast<uint32_t*>(wsb + wl.items);
@@ -533,6 +535,176 @@ bcf_status run_segmented(void* ko, uint32_t* vo, const void* ki, const uint32_t*
     return BCF_ECUDA;
   const int cfg = seg_cfg_for(kb, pairs, n);
   const cudaError_t e = timed(3, s, [&] { return launch_segmented(kb, pairs, cfg, L, s); });
+  return from_cuda(e);
+}
+
+// ---------------------------------------------------------------- pivot buckets
+
+// [header | block-sorted keys | their payloads | samples | sorted samples |
+//  workspace of the sample sort | splitters | m | piece sizes | piece offsets |
+//  scan workspace | bucket boundaries | segmented-sort workspace]
+struct PbLayout {
+  size_t xk, xv, samples, ssorted, ssort_ws, ssort_bytes, splitters, nsplit, counts, offsets, cps,
+      cps_bytes, seg_off, seg, seg_bytes, total;
+  uint64_t ns, ntiles;
+  uint32_t T;
+};
+PbLayout pb_layout(uint64_t n, int kb, bool pairs) {
+  PbLayout w;
+  const Plan plan = make_plan(n, kb, pairs);
+  w.T = plan.T;
+  w.ns = (n + kPbSampleStride - 1) / kPbSampleStride;
+  w.ntiles = (n + plan.T - 1) / plan.T;
+  w.xk = kAlign;
+  w.xv = align_up(w.xk + n * kb, kAlign);
+  w.samples = align_up(w.xv + (pairs ? n * 4 : 0), kAlign);
+  w.ssorted = align_up(w.samples + w.ns * kb, kAlign);
+  w.ssort_ws = align_up(w.ssorted + w.ns * kb, kAlign);
+  w.ssort_bytes = ws_layout(w.ns, 0, kb, false).total;
+  w.splitters = align_up(w.ssort_ws + w.ssort_bytes, kAlign);
+  w.nsplit = align_up(w.splitters + kPbSplitters * kb, kAlign);
+  w.counts = align_up(w.nsplit + sizeof(uint32_t), kAlign);
+  const uint64_t pieces = static_cast<uint64_t>(kPbBuckets) * w.ntiles;
+  w.offsets = align_up(w.counts + pieces * 4, kAlign);
+  w.cps = align_up(w.offsets + pieces * 4, kAlign);
+  w.cps_bytes = kAlign + align_up(((pieces + kCpsTile - 1) / kCpsTile) * 8, kAlign);
+  w.seg_off = align_up(w.cps + w.cps_bytes, kAlign);
+  w.seg = align_up(w.seg_off + (kPbBuckets + 1) * sizeof(uint64_t), kAlign);
+  w.seg_bytes = seg_layout(n, kPbBuckets, kb, pairs).total;
+  w.total = align_up(w.seg + w.seg_bytes, kAlign);
+  const size_t merge_need = ws_layout(n, 0, kb, pairs).total;  // the fallback's
+  if (w.total < merge_need) w.total = merge_need;
+  return w;
+}
+
+// Pivot buckets pay off once there are several tiles; offsets are 32-bit.
+bool pb_applies(uint64_t n, int kb, bool pairs) {
+  const Plan plan = make_plan(n, kb, pairs);
+  return n > 2ull * plan.T && n < 0xFFFFFFFFull;
+}
+
+bcf_status run_sort_pb(void* ko, uint32_t* vo, const void* ki, const uint32_t* vi, uint64_t n,
+                       bcf_dtype kt, const bcf_opts* o, void* ws, size_t ws_bytes,
+                       cudaStream_t s, bool pairs) {
+  bcf_status st = check_common(ko, vo, ki, vi, n, kt, pairs);
+  if (st != BCF_OK || n == 0) return st;
+  const int kb = key_bytes_of(kt);
+  if (!pb_applies(n, kb, pairs)) return run_sort(ko, vo, ki, vi, n, kt, o, ws, ws_bytes, s, pairs);
+  const PbLayout wl = pb_layout(n, kb, pairs);
+  st = check_ws(ws, ws_bytes, wl.total, ko, vo, ki, vi, n, kb);
+  if (st != BCF_OK) return st;
+  const int mode = mode_of(kt, o);
+  uint32_t* err = error_word_ptr();
+  if (!err) return BCF_ECUDA;
+  char* wsb = static_cast<char*>(ws);
+  const Plan plan = make_plan(n, kb, pairs);
+
+  PbArgs a{};
+  a.kin = ki;
+  a.n = n;
+  a.mode = mode;
+  a.samples = wsb + wl.samples;
+  a.ns = wl.ns;
+  a.sorted_samples = wsb + wl.ssorted;
+  a.splitters = wsb + wl.splitters;
+  a.nsplit = reinterpret_cast<uint32_t*>(wsb + wl.nsplit);
+  a.x = wsb + wl.xk;
+  a.xv = pairs ? reinterpret_cast<const uint32_t*>(wsb + wl.xv) : nullptr;
+  a.T = wl.T;
+  a.ntiles = wl.ntiles;
+  a.counts = reinterpret_cast<uint32_t*>(wsb + wl.counts);
+  a.offsets = reinterpret_cast<const uint32_t*>(wsb + wl.offsets);
+  a.kout = ko;
+  a.vout = vo;
+  a.seg_off = reinterpret_cast<uint64_t*>(wsb + wl.seg_off);
+  auto step = [&](int which) {
+    return from_cuda(timed(5, s, [&] { return launch_pb(which, kb, pairs, a, s); }));
+  };
+
+  // 1-2. splitters from a sorted sample of every 256th key (mapped order)
+  if ((st = step(kPbStepSample)) != BCF_OK) return st;
+  const bcf_dtype ukt = kb == 4 ? BCF_U32 : BCF_U64;  // the samples are mapped already
+  st = run_sort(wsb + wl.ssorted, nullptr, wsb + wl.samples, nullptr, wl.ns, ukt, nullptr,
+                wsb + wl.ssort_ws, wl.ssort_bytes, s, false);
+  if (st != BCF_OK) return st;
+  if ((st = step(kPbStepSplitters)) != BCF_OK) return st;
+  // 3. block sort into the workspace, keys kept mapped
+  BlockSortArgs ba{ki, vi, wsb + wl.xk, pairs ? reinterpret_cast<uint32_t*>(wsb + wl.xv) : nullptr,
+                   n, mode, 0, nullptr};
+  if (timed(0, s, [&] { return launch_block_sort(kb, pairs, plan.tune.block_cfg, ba, s); }) !=
+      cudaSuccess)
+    return BCF_ECUDA;
+  // 4. piece sizes of every (bucket, tile); 5. their exclusive prefix sum
+  if ((st = step(kPbStepCount)) != BCF_OK) return st;
+  if (cudaMemsetAsync(wsb + wl.cps, 0, wl.cps_bytes, s) != cudaSuccess) return BCF_ECUDA;
+  CpsArgs c{};
+  c.out = reinterpret_cast<uint32_t*>(wsb + wl.offsets);
+  c.values = a.counts;
+  c.colors = nullptr;
+  c.n = static_cast<uint64_t>(kPbBuckets) * wl.ntiles;
+  c.d = 1;
+  c.exclusive = 1;
+  c.ntiles = (c.n + kCpsTile - 1) / kCpsTile;
+  c.counter = reinterpret_cast<uint32_t*>(wsb + wl.cps);
+  c.status = reinterpret_cast<unsigned long long*>(wsb + wl.cps + kAlign);
+  c.err = err;
+  if (timed(4, s, [&] { return launch_cps(c, 0, s); }) != cudaSuccess) return BCF_ECUDA;
+  // 6. every piece to its bucket: equal buckets are final
+  if ((st = step(kPbStepScatter)) != BCF_OK) return st;
+  if ((st = step(kPbStepSegOffsets)) != BCF_OK) return st;
+  // 7. the open buckets, sorted in place (odd = equal buckets skipped)
+  return run_segmented(ko, vo, ko, vo, a.seg_off, kPbBuckets, n, kt, o, wsb + wl.seg,
+                       wl.seg_bytes, s, true);
+}
+
+// ---------------------------------------------------------------- colored prefix sums
+
+struct CpsLayout {
+  size_t counter, status, total;
+  uint64_t ntiles;
+};
+CpsLayout cps_layout(uint64_t n, uint32_t d) {
+  CpsLayout w;
+  w.ntiles = (n + kCpsTile - 1) / kCpsTile;
+  w.counter = 0;
+  w.status = kAlign;
+  w.total = align_up(w.status + w.ntiles * d * sizeof(unsigned long long), kAlign);
+  return w;
+}
+
+bcf_status run_cps(uint32_t* out, const uint32_t* values, const uint8_t* colors, uint64_t n,
+                   uint32_t d, int exclusive, int layout, void* ws, size_t ws_bytes,
+                   cudaStream_t s) {
+  if (d < 1 || d > kCpsMaxColors || (layout != BCF_CPS_BANKED && layout != BCF_CPS_ROWS))
+    return BCF_EINVAL;
+  if (n == 0) return BCF_OK;
+  if (!out || !values || !colors) return BCF_EINVAL;
+  if (!aligned16(out) || !aligned16(values) || !aligned16(colors)) return BCF_EINVAL;
+  if (n > (1ull << 42)) return BCF_EUNSUPPORTED;
+  const Span so{out, n * 4}, sv{values, n * 4}, sc{colors, n};
+  if (bad_overlap(so, sv) || overlap(so, sc)) return BCF_EINVAL;
+  const CpsLayout wl = cps_layout(n, d);
+  if (ws_bytes < wl.total || !ws) return BCF_ENOMEM;
+  if (!aligned16(ws)) return BCF_EINVAL;
+  const Span sw{ws, wl.total};
+  if (overlap(sw, so) || overlap(sw, sv) || overlap(sw, sc)) return BCF_EINVAL;
+  uint32_t* err = error_word_ptr();
+  if (!err) return BCF_ECUDA;
+  // tile ticket and every status word start at zero ("nothing published")
+  if (cudaMemsetAsync(ws, 0, wl.total, s) != cudaSuccess) return BCF_ECUDA;
+  char* wsb = static_cast<char*>(ws);
+  CpsArgs a{};
+  a.out = out;
+  a.values = values;
+  a.colors = colors;
+  a.n = n;
+  a.d = d;
+  a.exclusive = exclusive ? 1 : 0;
+  a.ntiles = wl.ntiles;
+  a.status = reinterpret_cast<unsigned long long*>(wsb + wl.status);
+  a.counter = reinterpret_cast<uint32_t*>(wsb + wl.counter);
+  a.err = err;
+  const cudaError_t e = timed(4, s, [&] { return launch_cps(a, layout, s); });
   return from_cuda(e);
 }
 
@@ -552,18 +724,30 @@ size_t bcf_workspace_bytes(int op, uint64_t n, uint64_t nseg_or_k, bcf_dtype kt,
     case BCF_OP_SORT: return ws_layout(n, 0, kb, has_vals != 0).total;
     case BCF_OP_MERGE: return ws_layout(n, nseg_or_k, kb, has_vals != 0).total;
     case BCF_OP_SEGMENTED: return seg_layout(n, nseg_or_k, kb, has_vals != 0).total;
+    case BCF_OP_SORT_PB: return pb_layout(n, kb, has_vals != 0).total;
+    case BCF_OP_CPS:
+      if (kt != BCF_U32 || has_vals || nseg_or_k < 1 || nseg_or_k > kCpsMaxColors) return 0;
+      return cps_layout(n, static_cast<uint32_t>(nseg_or_k)).total;
     default: return 0;
   }
 }
 
 bcf_status bcf_sort_keys(void* keys_out, const void* keys_in, uint64_t n, bcf_dtype kt,
                          const bcf_opts* opts, void* ws, size_t ws_bytes, cudaStream_t stream) {
+  if (opts && opts->algorithm == BCF_ALGO_PIVOT_BUCKETS)
+    return run_sort_pb(keys_out, nullptr, keys_in, nullptr, n, kt, opts, ws, ws_bytes, stream,
+                       false);
+  if (opts && opts->algorithm != BCF_ALGO_MERGE) return BCF_EINVAL;
   return run_sort(keys_out, nullptr, keys_in, nullptr, n, kt, opts, ws, ws_bytes, stream, false);
 }
 
 bcf_status bcf_sort_pairs(void* keys_out, uint32_t* vals_out, const void* keys_in,
                           const uint32_t* vals_in, uint64_t n, bcf_dtype kt,
                           const bcf_opts* opts, void* ws, size_t ws_bytes, cudaStream_t stream) {
+  if (opts && opts->algorithm == BCF_ALGO_PIVOT_BUCKETS)
+    return run_sort_pb(keys_out, vals_out, keys_in, vals_in, n, kt, opts, ws, ws_bytes, stream,
+                       true);
+  if (opts && opts->algorithm != BCF_ALGO_MERGE) return BCF_EINVAL;
   return run_sort(keys_out, vals_out, keys_in, vals_in, n, kt, opts, ws, ws_bytes, stream, true);
 }
 
@@ -586,6 +770,12 @@ bcf_status bcf_segmented_sort(void* keys_out, uint32_t* vals_out, const void* ke
                        opts, ws, ws_bytes, stream);
 }
 
+bcf_status bcf_colored_prefix_sums(uint32_t* out, const uint32_t* values, const uint8_t* colors,
+                                   uint64_t n, uint32_t d, int exclusive, int layout, void* ws,
+                                   size_t ws_bytes, cudaStream_t stream) {
+  return run_cps(out, values, colors, n, d, exclusive, layout, ws, ws_bytes, stream);
+}
+
 const char* bcf_status_string(bcf_status s) {
   switch (s) {
     case BCF_OK: return "BCF_OK";
@@ -605,7 +795,8 @@ bcf_status bcf_last_device_error(cudaStream_t stream) {
   if (v != 0) {
     const uint32_t zero = 0;
     if (cudaMemcpyToSymbol(g_error_word, &zero, sizeof(zero)) != cudaSuccess) return BCF_ECUDA;
-    return BCF_ETIMEOUT;
+    // a color >= d alone is an invalid argument; any other bit is a wait that ran out
+    return v == kErrBadColor ? BCF_EINVAL : BCF_ETIMEOUT;
   }
   return BCF_OK;
 }
@@ -638,7 +829,7 @@ bcf_status bcf_profile_collect(bcf_profile* out) {
     float ms = 0.f;
     if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess)
       st = BCF_ECUDA;
-    if (r.kind >= 0 && r.kind < 4) {
+    if (r.kind >= 0 && r.kind < BCF_PROFILE_KINDS) {
       out->launches[r.kind] += 1;
       out->total_ms[r.kind] += ms;
     }

@@ -92,6 +92,7 @@ struct SegLaunch {
   const uint64_t* off;   // device, nseg + 1
   uint64_t nseg, n;
   int mode;
+  int skip_odd;          // leave odd-indexed segments untouched (pivot buckets)
   void* queue;           // work descriptors, `capacity` of them, cleared to 0
   uint64_t capacity;
   uint32_t* items_left;  // nseg
@@ -111,5 +112,60 @@ cudaError_t launch_partition(int key_bytes, int cfg, const MergeArgs& a, const P
                              cudaStream_t s);
 cudaError_t launch_merge(int key_bytes, bool pairs, int cfg, const MergeArgs& a,
                          const PairList* pl, cudaStream_t s);
+
+// Colored prefix sums (Appendix A).  One tile of kCpsTile elements per CTA,
+// tiles taken in order from `counter`; `status` holds one word per (tile,
+// color) for the look-back across tiles and must be zero before the launch.
+constexpr int kCpsThreads = 256;
+constexpr int kCpsPerThread = 16;  // elements per thread and step
+constexpr int kCpsSteps = 4;       // steps per tile: each thread owns 64 consecutive elements
+constexpr int kCpsTile = kCpsThreads * kCpsPerThread * kCpsSteps;
+constexpr uint32_t kCpsMaxColors = 64;
+constexpr uint32_t kErrBadColor = 8u;          // device error bit: a color >= d
+constexpr uint32_t kErrLookbackTimeout = 16u;  // device error bit: look-back wait ran out
+struct CpsArgs {
+  uint32_t* out;
+  const uint32_t* values;
+  const uint8_t* colors;  // nullptr: every element has color 0 (a plain scan, d = 1)
+  uint64_t n;
+  uint32_t d;            // colors, 1..kCpsMaxColors
+  int exclusive;
+  uint64_t ntiles;
+  unsigned long long* status;  // ntiles * d words
+  uint32_t* counter;     // next tile
+  uint32_t* err;
+};
+// layout 0: one shared-memory bank per thread (the paper's conflict-free
+// layout); layout 1: each thread's d counters contiguous (the conflicting one).
+cudaError_t launch_cps(const CpsArgs& a, int layout, cudaStream_t s);
+size_t cps_smem_bytes(uint32_t d);
+
+// Pivot buckets (BCFMergesortPB, Sec. 3.2): P - 1 splitters from every
+// kPbSampleStride-th key; buckets open(0), equal(s_0), open(1), ..., open(m).
+constexpr uint32_t kPbSampleStride = 256;
+constexpr uint32_t kPbP = 256;
+constexpr uint32_t kPbSplitters = kPbP - 1;
+constexpr uint32_t kPbBuckets = 2 * kPbSplitters + 1;
+enum { kPbStepSample, kPbStepSplitters, kPbStepCount, kPbStepScatter, kPbStepSegOffsets };
+struct PbArgs {
+  const void* kin;            // user keys (original bits)
+  uint64_t n;
+  int mode;                   // key map of the sort
+  void* samples;              // ns mapped keys
+  uint64_t ns;
+  const void* sorted_samples; // the samples, sorted
+  void* splitters;            // up to kPbSplitters mapped keys
+  uint32_t* nsplit;           // m
+  const void* x;              // block-sorted tiles (mapped keys)
+  const uint32_t* xv;         // their payloads, or nullptr
+  uint32_t T;                 // block tile
+  uint64_t ntiles;
+  uint32_t* counts;           // kPbBuckets * ntiles piece sizes, bucket-major
+  const uint32_t* offsets;    // their exclusive prefix sum: piece output positions
+  void* kout;                 // final output (original bits)
+  uint32_t* vout;
+  uint64_t* seg_off;          // kPbBuckets + 1 bucket boundaries
+};
+cudaError_t launch_pb(int step, int key_bytes, bool pairs, const PbArgs& a, cudaStream_t s);
 
 }  // namespace bcf

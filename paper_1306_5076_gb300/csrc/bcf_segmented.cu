@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(1024) plan_kernel(const SegArgs a, uint32_t T,
   for (uint64_t c = 0; c < a.nseg; c += 1024) {
     const uint64_t s = c + threadIdx.x;
     SegGeo g{};
-    if (s < a.nseg) g = seg_geo(a.off, s, a.n, T);
+    if (s < a.nseg) g = seg_geo(a.off, s, a.n, T, a.skip_odd != 0);
     const unsigned long long tiles = g.tiles;
     const unsigned long long tiny = g.tiny ? 1 : 0;
     const unsigned long long tot = tiles + static_cast<unsigned long long>(g.passes) * g.pieces;
@@ -145,6 +145,7 @@ cudaError_t launch_segmented(int key_bytes, bool pairs, int cfg, const SegLaunch
   a.nseg = L.nseg;
   a.n = L.n;
   a.mode = L.mode;
+  a.skip_odd = L.skip_odd;
   a.queue = static_cast<SegWork*>(L.queue);
   a.capacity = L.capacity;
   a.items_left = L.items_left;

@@ -41,13 +41,18 @@ struct SegGeo {
   bool tiny;
 };
 
-__device__ __forceinline__ SegGeo seg_geo(const uint64_t* off, uint64_t s, uint64_t n, uint32_t T) {
+// skip_odd: segments with an odd index are left as they are (treated as
+// empty); used by the pivot-bucket sort, whose odd buckets hold keys equal to
+// a splitter and are final after the distribution.
+__device__ __forceinline__ SegGeo seg_geo(const uint64_t* off, uint64_t s, uint64_t n, uint32_t T,
+                                          bool skip_odd) {
   SegGeo g;
   uint64_t lo = __ldcg(off + s), hi = __ldcg(off + s + 1);
   // memory safety for malformed offsets: clamp into [0, n] and make hi >= lo
   lo = lo < n ? lo : n;
   hi = hi < n ? hi : n;
   hi = hi > lo ? hi : lo;
+  if (skip_odd && (s & 1u)) hi = lo;
   g.lo = lo;
   g.hi = hi;
   const uint64_t size = hi - lo;
@@ -68,6 +73,7 @@ struct SegArgs {
   const uint64_t* off;
   uint64_t nseg, n;
   int mode;
+  int skip_odd;  // odd-indexed segments are left untouched
   SegWork* queue;
   uint64_t capacity;
   uint32_t* items_left;
@@ -363,13 +369,13 @@ __global__ void __launch_bounds__(NT) seg_worker(const SegArgs a) {
       const uint64_t t = w.arg * kPerGroup + (tid >> 5);
       if (t < __ldcg(&a.ctl->n_tiny)) {
         const uint32_t s = __ldcg(a.tiny_list + t);
-        const SegGeo g = seg_geo(a.off, s, a.n, T);
+        const SegGeo g = seg_geo(a.off, s, a.n, T, a.skip_odd != 0);
         warp_sort_segment<K, PAIRS, MAP>(a, g.lo, g.hi);
       }
       __syncthreads();
       continue;
     }
-    const SegGeo g = seg_geo(a.off, w.seg, a.n, T);
+    const SegGeo g = seg_geo(a.off, w.seg, a.n, T, a.skip_odd != 0);
     if (type == kWTile)
       sort_tile_item<K, PAIRS, E, NT, MAP>(a, g, w.arg, sm);
     else

@@ -63,8 +63,12 @@ extern "C" bcf_status bcf_sort_keys_static(void* keys_out, const void* keys_in, 
                                            bcf_dtype kt, const bcf_opts* opts,
                                            cudaStream_t stream) {
   if (n > kMaxKeys) return BCF_EUNSUPPORTED;
-  if (n == 0) return bcf_sort_keys(keys_out, keys_in, 0, kt, opts, nullptr, 0, stream);
+  // the static array is sized for the merge path: the algorithm choice is ignored
+  bcf_opts o{};
+  if (opts) o = *opts;
+  o.algorithm = BCF_ALGO_MERGE;
+  if (n == 0) return bcf_sort_keys(keys_out, keys_in, 0, kt, &o, nullptr, 0, stream);
   void* ws = static_workspace();
   if (!ws) return BCF_ECUDA;
-  return bcf_sort_keys(keys_out, keys_in, n, kt, opts, ws, kStaticBytes, stream);
+  return bcf_sort_keys(keys_out, keys_in, n, kt, &o, ws, kStaticBytes, stream);
 }

@@ -71,10 +71,17 @@ def test_workspace_bytes_scale_with_input(lib):
     # colored prefix sums: one look-back word per (tile, color); u32 values only
     from paper_1306_5076_gb300 import BCF_OP_CPS
     cps = lib.bcf_workspace_bytes(BCF_OP_CPS, n, 16, BCF_U32, 0)
-    assert cps >= (n // 4096) * 16 * 8 and cps % 256 == 0
+    assert cps >= (n // 16384) * 16 * 8 and cps % 256 == 0
     assert lib.bcf_workspace_bytes(BCF_OP_CPS, n, 0, BCF_U32, 0) == 0
     assert lib.bcf_workspace_bytes(BCF_OP_CPS, n, 65, BCF_U32, 0) == 0
     assert lib.bcf_workspace_bytes(BCF_OP_CPS, n, 16, BCF_U64, 0) == 0
+    # pivot buckets: the block-sorted copy, the segmented-sort scratch and small
+    # tables; always at least the merge path's (its fall-back) workspace
+    from paper_1306_5076_gb300 import BCF_OP_SORT_PB
+    for kt, hv in ((BCF_U32, 0), (BCF_U32, 1), (BCF_U64, 0)):
+        pb = lib.bcf_workspace_bytes(BCF_OP_SORT_PB, n, 0, kt, hv)
+        assert pb >= 2 * lib.bcf_workspace_bytes(BCF_OP_SORT, n, 0, kt, hv) - (1 << 20)
+        assert pb >= lib.bcf_workspace_bytes(BCF_OP_SORT, 10, 0, kt, hv)
     assert lib.bcf_workspace_bytes(BCF_OP_MERGE, n, 256, BCF_U32, 0) >= keys
     assert lib.bcf_workspace_bytes(9, n, 0, BCF_U32, 0) == 0
     assert lib.bcf_workspace_bytes(BCF_OP_SORT, n, 0, 7, 0) == 0
@@ -101,7 +108,7 @@ def test_plan_pass_count_is_lemma_2(lib, n):
 def test_host_side_argument_errors_return_before_launch(lib):
     from paper_1306_5076_gb300 import _native
 
-    opts = ctypes.byref(_native.BcfOpts(0, 1))
+    opts = ctypes.byref(_native.BcfOpts(0, 1, 0))
     EINVAL = 1
     # bad dtype (one past the last key type, and a negative code)
     assert lib.bcf_sort_keys(None, None, 0, 9, opts, None, 0, None) == EINVAL
@@ -116,6 +123,10 @@ def test_host_side_argument_errors_return_before_launch(lib):
                              0, None) == EINVAL
     # partial overlap of output and input
     assert lib.bcf_sort_keys(ctypes.c_void_p(0x10000), ctypes.c_void_p(0x10010), 100, 0, opts,
+                             None, 0, None) == EINVAL
+    # unknown algorithm
+    bad_algo = ctypes.byref(_native.BcfOpts(0, 1, 7))
+    assert lib.bcf_sort_keys(ctypes.c_void_p(0x10000), ctypes.c_void_p(0x20000), 10, 0, bad_algo,
                              None, 0, None) == EINVAL
     # pairs need both value pointers
     assert lib.bcf_sort_pairs(ctypes.c_void_p(0x10000), None, ctypes.c_void_p(0x20000), None, 10,
@@ -141,7 +152,7 @@ def test_host_side_argument_errors_return_before_launch(lib):
 def test_workspace_too_small_is_enomem(lib):
     from paper_1306_5076_gb300 import _native
 
-    opts = ctypes.byref(_native.BcfOpts(0, 1))
+    opts = ctypes.byref(_native.BcfOpts(0, 1, 0))
     n = 1 << 20  # needs merge passes, hence a workspace
     assert lib.bcf_sort_keys(ctypes.c_void_p(0x100000000), ctypes.c_void_p(0x200000000), n, 0,
                              opts, ctypes.c_void_p(0x300000000), 1024, None) == 2
