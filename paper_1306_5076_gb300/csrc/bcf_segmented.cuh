@@ -181,6 +181,31 @@ __device__ __forceinline__ void warp_sort_segment(const SegArgs& a, uint64_t lo,
   }
 }
 
+// Stores a thread's E consecutive tile slots k0 .. k0+E-1 (BLK layout) of
+// which [front, front + cnt) are real: 32-byte vector stores when all E are
+// real and the buffers are 32-byte aligned (tiles start at multiples of T),
+// else one store per real slot.
+template <int E, typename K, typename F>
+__device__ __forceinline__ void store_slots(K* kdst, uint32_t* vdst, F& f, uint32_t k0,
+                                            uint32_t front, uint32_t cnt, const void* kbase,
+                                            const uint32_t* vbase) {
+  constexpr bool PAIRS = F::W > F::KW;
+  if (k0 >= front && k0 + E <= front + cnt && is_aligned32(kbase) &&
+      (!PAIRS || is_aligned32(vbase))) {
+    store_run<E>(kdst + k0, f.k, true);
+    if constexpr (PAIRS) store_run<E>(vdst + k0, f.v, true);
+    return;
+  }
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const uint32_t k = k0 + e;
+    if (k >= front && k < front + cnt) {
+      kdst[k] = f.k[e];
+      if constexpr (PAIRS) vdst[k] = f.v[e];
+    }
+  }
+}
+
 // ---------------------------------------------------------------- tile sort
 
 template <typename K, bool PAIRS, int E, int NT, bool MAP>
@@ -214,14 +239,14 @@ __device__ __forceinline__ void sort_tile_item(const SegArgs& a, const SegGeo& g
   K* kout = static_cast<K*>(to_out ? a.kout : a.kbuf) + base;
   uint32_t* vout = PAIRS ? (to_out ? a.vout : a.vbuf) + base : nullptr;
   const bool last = g.passes == 0;
+  if constexpr (MAP) {
+    if (last) {
 #pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const uint32_t k = tid * E + e;
-    if (k >= front && k < front + cnt) {
-      kout[k] = (MAP && last) ? unmap_key(f.k[e], a.mode) : f.k[e];
-      if constexpr (PAIRS) vout[k] = f.v[e];
+      for (int e = 0; e < E; ++e) f.k[e] = unmap_key(f.k[e], a.mode);  // last use of f.k
     }
   }
+  store_slots<E>(kout, vout, f, tid * E, front, cnt, to_out ? a.kout : a.kbuf,
+                 PAIRS ? (to_out ? a.vout : a.vbuf) : nullptr);
 }
 
 // ---------------------------------------------------------------- merge piece
@@ -310,14 +335,14 @@ __device__ __forceinline__ void merge_piece_item(const SegArgs& a, const SegGeo&
   uint32_t* vdst = PAIRS ? (dst_out ? a.vout : a.vbuf) + gt * T : nullptr;
   const bool last = pass == g.passes;
   const uint32_t cnt = static_cast<uint32_t>(pe - ps);
+  if constexpr (MAP) {
+    if (last) {
 #pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const uint32_t k = tid * E + e;
-    if (k >= front && k < front + cnt) {
-      dst[k] = (MAP && last) ? unmap_key(f.k[e], a.mode) : f.k[e];
-      if constexpr (PAIRS) vdst[k] = f.v[e];
+      for (int e = 0; e < E; ++e) f.k[e] = unmap_key(f.k[e], a.mode);  // last use of f.k
     }
   }
+  store_slots<E>(dst, vdst, f, tid * E, front, cnt, dst_out ? a.kout : a.kbuf,
+                 PAIRS ? (dst_out ? a.vout : a.vbuf) : nullptr);
 }
 
 // ---------------------------------------------------------------- worker
