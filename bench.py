@@ -371,6 +371,88 @@ def cps_bench(torch, dev, bcf, peak, log2n=29, colors=(1, 2, 4, 8, 16, 32, 64)):
             "bytes_per_element": 9, **res}
 
 
+def pb_bench(torch, dev, bcf, log2n=LOG2N):
+    """Pivot buckets (BCFMergesortPB) against the merge passes on the paper's
+    duplicate-heavy inputs and on distinct keys: whole-sort time, 2^log2n u32
+    keys, keys only and pairs."""
+    import numpy as np
+
+    import workloads
+
+    n = 1 << log2n
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    for name in ("distinct16", "zipf", "zero_one", "dup16", "uniform"):
+        keys = (workloads.paper_keys(name, n) if name in workloads.PAPER_SETS
+                else workloads.keys(name, "u32", n))
+        kd = torch.from_numpy(keys.view(np.int32)).to(dev)
+        ko = torch.empty_like(kd)
+        for pairs in (False, True):
+            vd = torch.arange(n, dtype=torch.int32, device=dev) if pairs else None
+            vo = torch.empty_like(vd) if pairs else None
+            ws = torch.empty(bcf.bcf_workspace_bytes(bcf.BCF_OP_SORT_PB, n, 0, bcf.BCF_U32, pairs),
+                             dtype=torch.uint8, device=dev)
+            row = {}
+            for algo in ("merge", "pivot_buckets"):
+                if pairs:
+                    fn = lambda: bcf.bcf_sort_pairs(ko, vo, kd, vd, kt=bcf.BCF_U32, ws=ws,  # noqa: E731
+                                                    stream=stream, algorithm=algo)
+                else:
+                    fn = lambda: bcf.bcf_sort_keys(ko, kd, kt=bcf.BCF_U32, ws=ws,  # noqa: E731
+                                                   stream=stream, algorithm=algo)
+                ms = timed_ms(torch, stream, fn, warmup=2, reps=5)
+                row[algo] = {"ms": ms, "keys_per_s": n / (ms * 1e-3)}
+            row["speedup"] = row["merge"]["ms"] / row["pivot_buckets"]["ms"]
+            out[name + ("+u32" if pairs else "")] = row
+            del vd, vo, ws
+            torch.cuda.empty_cache()
+        del kd, ko
+    return {"n": n, "key": "u32", "results": out}
+
+
+def profile_case(args):
+    """A small case of one path, for ncu captures (inputs larger than L2, a
+    few launches): 'cps' = colored prefix sums of 2^26 elements, 16 colors,
+    both layouts, two launches each; 'pb' = pivot-bucket sort of 2^26
+    16-distinct u32 keys, twice."""
+    import numpy as np
+    import torch
+
+    import paper_1306_5076_gb300 as bcf
+    import workloads
+
+    dev = torch.device("cuda", 0)
+    bcf._native.load()
+    n = 1 << 26
+    if args.profile_case == "cps":
+        vals, cols = workloads.colored_elements(n, 16, seed=26)
+        vd = torch.from_numpy(vals.view(np.int32)).to(dev)
+        cd = torch.from_numpy(cols).to(dev)
+        od = torch.empty_like(vd)
+        for layout in (bcf.BCF_CPS_BANKED, bcf.BCF_CPS_ROWS):
+            for _ in range(2):
+                bcf.bcf_colored_prefix_sums(od, vd, cd, 16, layout=layout)
+    elif args.profile_case == "pb":
+        keys = workloads.keys("distinct16", "u32", n)
+        kd = torch.from_numpy(keys.view(np.int32)).to(dev)
+        ko = torch.empty_like(kd)
+        for _ in range(2):
+            bcf.bcf_sort_keys(ko, kd, kt=bcf.BCF_U32, algorithm="pivot_buckets")
+    else:
+        keys, offs = workloads.segments(20_000, 1 << 14, "u32", seed=4000)
+        n = keys.size
+        kd = torch.from_numpy(keys.view(np.int32)).to(dev)
+        ko = torch.empty_like(kd)
+        od = torch.from_numpy(offs.astype(np.int64)).to(dev)
+        for _ in range(2):
+            bcf.bcf_segmented_sort(ko, None, kd, None, od, kt=bcf.BCF_U32)
+    torch.cuda.synchronize()
+    if bcf.bcf_last_device_error() != 0:
+        raise RuntimeError("device error word set")
+    print(json.dumps({"profile_case": args.profile_case, "n": n, "ok": True}))
+    return 0
+
+
 def run_gpu(args, world, rank, local, pg):
     import numpy as np
     import torch
@@ -437,21 +519,39 @@ def run_gpu(args, world, rank, local, pg):
     ok_multiset = bool((fi.sum() == ku.sum()).item() and
                        ((fi * fi) % 1000000007).sum().item() == ((ku * ku) % 1000000007).sum().item())
 
-    # ---- end to end from pinned host memory
-    e2e_steps = max(1, min(args.steps, 5))
-    for _ in range(2):
-        kd.copy_(host_in, non_blocking=True)
-        step()
-        host_out.copy_(ko, non_blocking=True)
+    # ---- end to end through the public host-buffer call: every step copies its
+    # input in from pinned host memory, sorts it and copies the result out
+    # (bcf_sort_keys_host).  Steps go round-robin to E2E_STREAMS streams with
+    # their own workspaces, so one step's copy-in, another's sort and a third's
+    # copy-out overlap (copy engines both ways, SMs).
+    E2E_STREAMS = 3
+    e2e_steps = max(E2E_STREAMS, min(args.steps, 12))
+    del ws
+    torch.cuda.empty_cache()
+    side = [torch.cuda.Stream(dev) for _ in range(E2E_STREAMS)]
+    wss = [torch.empty(bcf.bcf_workspace_bytes(bcf._native.BCF_OP_SORT_HOST, N, 0, bcf.BCF_U32,
+                                               False), dtype=torch.uint8, device=dev)
+           for _ in range(E2E_STREAMS)]
+    houts = [host_out] + [torch.empty_like(host_in).pin_memory() for _ in range(E2E_STREAMS - 1)]
+
+    def e2e_step(i):
+        j = i % E2E_STREAMS
+        bcf.bcf_sort_keys_host(houts[j], host_in, kt=bcf.BCF_U32, ws=wss[j], stream=side[j],
+                               device=dev)
+
+    for i in range(E2E_STREAMS):  # warm-up
+        e2e_step(i)
     torch.cuda.synchronize()
     barrier()
     h0 = torch.cuda.Event(enable_timing=True)
     h1 = torch.cuda.Event(enable_timing=True)
     h0.record(stream)
-    for _ in range(e2e_steps):
-        kd.copy_(host_in, non_blocking=True)
-        step()
-        host_out.copy_(ko, non_blocking=True)
+    for st in side:
+        st.wait_event(h0)
+    for i in range(e2e_steps):
+        e2e_step(i)
+    for st in side:
+        stream.wait_stream(st)
     h1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = h0.elapsed_time(h1) / e2e_steps
@@ -459,11 +559,12 @@ def run_gpu(args, world, rank, local, pg):
         t = torch.tensor([e2e_ms], device=dev)
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
         e2e_ms = float(t.item())
-    ok_e2e = bool(torch.equal(host_out, ko.cpu()))
+    # every stream's last result equals the device-timed sort's output
+    ok_e2e = all(bool(torch.equal(h, ko.cpu())) for h in houts)
+    del wss
+    torch.cuda.empty_cache()
 
     serving = None
-    ws = None  # the timed sorts are done: free the workspace for what follows
-    torch.cuda.empty_cache()
     if args.serve_seconds > 0:
         # the workload's trace (2000 req/s), then the same request mix at 8x the
         # rate, past what one launch chain per request can sustain
@@ -475,7 +576,8 @@ def run_gpu(args, world, rank, local, pg):
     extras = None
     if not args.no_extras:
         extras = {"key_types": key_types_bench(torch, dev, bcf, peak),
-                  "colored_prefix_sums": cps_bench(torch, dev, bcf, peak)}
+                  "colored_prefix_sums": cps_bench(torch, dev, bcf, peak),
+                  "pivot_buckets": pb_bench(torch, dev, bcf)}
 
     if rank != 0:
         return 0
@@ -522,7 +624,9 @@ def run_gpu(args, world, rank, local, pg):
                           "merge": merge_ms},
         "gpu_launches": launches,
         "e2e": {"value": world * N / (e2e_ms * 1e-3), "unit": "keys/s",
-                "h2d_bytes_per_step": N * KEY_BYTES, "d2h_bytes_per_step": N * KEY_BYTES},
+                "h2d_bytes_per_step": N * KEY_BYTES, "d2h_bytes_per_step": N * KEY_BYTES,
+                "api": "bcf_sort_keys_host, pinned host buffers", "streams": E2E_STREAMS,
+                "steps": e2e_steps},
         "clocks": clk,
         "checks": {"sorted": ok_sorted, "multiset": ok_multiset, "e2e_roundtrip": ok_e2e},
     }
@@ -543,8 +647,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", choices=["cps", "pb", "seg"],
+                    help="run only a small case of one path (for ncu captures) and exit")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the other key types and the colored prefix sums")
+                    help="skip the other key types, the colored prefix sums and the "
+                         "pivot-bucket comparison")
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="length of the served-vs-plain request trace (0: skip)")
     ap.add_argument("--log2n", type=int, default=LOG2N,
@@ -555,6 +662,8 @@ def main():
     N = 1 << args.log2n
     if args.warmup < 3:
         args.warmup = 3
+    if args.profile_case:
+        return profile_case(args)
     world, rank, local, pg = dist_setup(args)
     try:
         if args.impl == "reference":

@@ -94,7 +94,7 @@ typedef struct {
 
 /* Operation codes for bcf_workspace_bytes. */
 enum { BCF_OP_SORT = 0, BCF_OP_MERGE = 1, BCF_OP_SEGMENTED = 2, BCF_OP_CPS = 3,
-       BCF_OP_SORT_PB = 4 };
+       BCF_OP_SORT_PB = 4, BCF_OP_SORT_HOST = 5, BCF_OP_SORT_HOST_PB = 6 };
 
 /*
  * Workspace size in bytes for an operation.
@@ -104,7 +104,9 @@ enum { BCF_OP_SORT = 0, BCF_OP_MERGE = 1, BCF_OP_SEGMENTED = 2, BCF_OP_CPS = 3,
  *             BCF_OP_CPS: colored prefix sums of n elements with nseg_or_k
  *             colors (kt must be BCF_U32, has_vals 0);
  *             BCF_OP_SORT_PB: sort n keys with BCF_ALGO_PIVOT_BUCKETS (pairs if
- *             has_vals; also enough for BCF_ALGO_MERGE).
+ *             has_vals; also enough for BCF_ALGO_MERGE);
+ *             BCF_OP_SORT_HOST / BCF_OP_SORT_HOST_PB: bcf_sort_*_host with the
+ *             merge / pivot-bucket algorithm.
  * Returns 0 for an unknown op or dtype.  The size is about one extra copy of
  * the keys (+ values) -- the merge is not in place, as in the paper (Sec. 4
  * remarks that BCFMergesort needs less extra space than its competitors) --
@@ -211,6 +213,32 @@ bcf_status bcf_profile_collect(bcf_profile* out);
 
 /* Version string of the library. */
 const char* bcf_version(void);
+
+/* ---- sorting host buffers --------------------------------------------------- */
+
+/*
+ * Sort n keys (pairs: key-value pairs) that live in HOST memory: copy in, sort,
+ * copy out, all enqueued asynchronously on `stream`.  The host buffers must
+ * stay valid, and the input unchanged, until the stream has passed the call.
+ * Page-locked (pinned) host buffers give full copy bandwidth and let the copies
+ * of calls on different streams overlap each other and other calls' sorting.
+ * With BCF_ALGO_MERGE the input is copied in eight pieces on a library-owned
+ * copy stream, and the block sort of each piece starts as soon as it has
+ * landed.  The result is the one bcf_sort_keys / bcf_sort_pairs give.
+ *   keys_out_host, vals_out_host   host, n keys / values, written (may equal the inputs)
+ *   keys_in_host, vals_in_host     host, n keys / values
+ *   ws        device workspace of bcf_workspace_bytes(BCF_OP_SORT_HOST, n, 0, kt,
+ *             has_vals) bytes (BCF_OP_SORT_HOST_PB with BCF_ALGO_PIVOT_BUCKETS):
+ *             device copies of the input and output plus the sort's workspace
+ * Errors: as bcf_sort_keys; a null host pointer with n > 0 is BCF_EINVAL.
+ */
+bcf_status bcf_sort_keys_host(void* keys_out_host, const void* keys_in_host, uint64_t n,
+                              bcf_dtype kt, const bcf_opts* opts, void* ws, size_t ws_bytes,
+                              cudaStream_t stream);
+bcf_status bcf_sort_pairs_host(void* keys_out_host, uint32_t* vals_out_host,
+                               const void* keys_in_host, const uint32_t* vals_in_host, uint64_t n,
+                               bcf_dtype kt, const bcf_opts* opts, void* ws, size_t ws_bytes,
+                               cudaStream_t stream);
 
 /* ---- colored prefix sums ------------------------------------------------ */
 

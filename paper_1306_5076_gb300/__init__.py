@@ -27,7 +27,7 @@ __all__ = [
     "BCF_U64", "BCF_F32", "BCF_I32", "BCF_I64", "BCF_F64",
     "BCF_OP_SORT", "BCF_OP_MERGE", "BCF_OP_SEGMENTED", "BCF_OP_CPS",
     "bcf_colored_prefix_sums", "BCF_CPS_BANKED", "BCF_CPS_ROWS", "BCF_OP_SORT_PB",
-    "BCF_ALGO_MERGE", "BCF_ALGO_PIVOT_BUCKETS",
+    "BCF_ALGO_MERGE", "BCF_ALGO_PIVOT_BUCKETS", "bcf_sort_keys_host", "bcf_sort_pairs_host",
 ]
 
 
@@ -116,6 +116,53 @@ def bcf_sort_keys(keys_out, keys_in, *, descending=False, ws=None, stream=None, 
     _check(_native.load().bcf_sort_keys(_ptr(keys_out), _ptr(keys_in), n, kt, opts,
                                         _ptr(ws), wsb, _stream(stream)), "bcf_sort_keys")
     return keys_out
+
+
+def _host_ptr(t):
+    if t is None:
+        return None
+    if t.is_cuda:
+        raise ValueError("bcfsort: host-buffer calls take CPU tensors")
+    if not t.is_contiguous():
+        raise ValueError("bcfsort: tensors must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def bcf_sort_keys_host(keys_out, keys_in, *, descending=False, ws=None, stream=None, kt=None,
+                       algorithm="merge", device=None):
+    """Sort keys held in host memory (CPU tensors, ideally pinned): copy in, sort
+    and copy out, asynchronously on ``stream``; the copy-in overlaps the block
+    sort.  ``ws``: a device workspace of ``bcf_workspace_bytes(BCF_OP_SORT_HOST,
+    ...)`` bytes (allocated if None)."""
+    import torch
+
+    kt = key_dtype_of(keys_in) if kt is None else kt
+    n = keys_in.numel()
+    op = _native.BCF_OP_SORT_HOST_PB if algorithm == "pivot_buckets" else _native.BCF_OP_SORT_HOST
+    device = device or torch.device("cuda", torch.cuda.current_device())
+    ws, wsb = _workspace(op, n, 0, kt, False, ws, device)
+    _check(_native.load().bcf_sort_keys_host(_host_ptr(keys_out), _host_ptr(keys_in), n, kt,
+                                             _opts(descending, algorithm), _ptr(ws), wsb,
+                                             _stream(stream)), "bcf_sort_keys_host")
+    return keys_out
+
+
+def bcf_sort_pairs_host(keys_out, vals_out, keys_in, vals_in, *, descending=False, ws=None,
+                        stream=None, kt=None, algorithm="merge", device=None):
+    """Stable sort of (key, value) pairs held in host memory (see
+    :func:`bcf_sort_keys_host`)."""
+    import torch
+
+    kt = key_dtype_of(keys_in) if kt is None else kt
+    n = keys_in.numel()
+    op = _native.BCF_OP_SORT_HOST_PB if algorithm == "pivot_buckets" else _native.BCF_OP_SORT_HOST
+    device = device or torch.device("cuda", torch.cuda.current_device())
+    ws, wsb = _workspace(op, n, 0, kt, True, ws, device)
+    _check(_native.load().bcf_sort_pairs_host(_host_ptr(keys_out), _host_ptr(vals_out),
+                                              _host_ptr(keys_in), _host_ptr(vals_in), n, kt,
+                                              _opts(descending, algorithm), _ptr(ws), wsb,
+                                              _stream(stream)), "bcf_sort_pairs_host")
+    return keys_out, vals_out
 
 
 def bcf_sort_pairs(keys_out, vals_out, keys_in, vals_in, *, descending=False, ws=None,

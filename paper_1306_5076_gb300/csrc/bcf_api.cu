@@ -318,9 +318,18 @@ bcf_status from_cuda(cudaError_t e) { return e == cudaSuccess ? BCF_OK : BCF_ECU
 
 // ---------------------------------------------------------------- sort
 
+// Input that arrives in pieces (bcf_sort_*_host): `before_tiles(t0, t1, s)`
+// is called before the block sort of tiles [t0, t1) is launched on `s` and
+// makes `s` wait until those tiles' input has landed.
+struct ChunkedInput {
+  uint64_t chunk_tiles;
+  bcf_status (*before_tiles)(void* ctx, uint64_t t0, uint64_t t1, cudaStream_t s);
+  void* ctx;
+};
+
 bcf_status run_sort(void* ko, uint32_t* vo, const void* ki, const uint32_t* vi, uint64_t n,
                     bcf_dtype kt, const bcf_opts* o, void* ws, size_t ws_bytes, cudaStream_t s,
-                    bool pairs) {
+                    bool pairs, const ChunkedInput* chunked = nullptr) {
   bcf_status st = check_common(ko, vo, ki, vi, n, kt, pairs);
   if (st != BCF_OK || n == 0) return st;
   const int kb = key_bytes_of(kt);
@@ -345,12 +354,22 @@ bcf_status run_sort(void* ko, uint32_t* vo, const void* ki, const uint32_t* vi, 
   // sample arrays of the two buffers (the final output needs none)
   void* samp[2] = {plan.passes > 0 ? wsb + wl.samples0 : nullptr,
                    plan.passes > 0 ? wsb + wl.samples1 : nullptr};
-  BlockSortArgs ba{ki, vi, kbuf[buf(0)], vbuf[buf(0)], n, mode, m == 0 ? mode : 0,
-                   m == 0 ? nullptr : samp[buf(0)]};
-  cudaError_t e = timed(0, s, [&] {
-    return launch_block_sort(kb, pairs, plan.tune.block_cfg, ba, s);
-  });
-  if (e != cudaSuccess) return BCF_ECUDA;
+  // the base case, in one launch or (input arriving in pieces) one launch per
+  // chunk of whole tiles; a chunk's sample slots start at its first key / 256
+  const uint64_t tiles = (n + plan.T - 1) / plan.T;
+  const uint64_t step_tiles = chunked ? chunked->chunk_tiles : tiles;
+  cudaError_t e = cudaSuccess;
+  for (uint64_t t0 = 0; t0 < tiles; t0 += step_tiles) {
+    const uint64_t t1 = t0 + step_tiles < tiles ? t0 + step_tiles : tiles;
+    const uint64_t off = t0 * plan.T, len = (t1 * plan.T < n ? t1 * plan.T : n) - off;
+    if (chunked && (st = chunked->before_tiles(chunked->ctx, t0, t1, s)) != BCF_OK) return st;
+    void* sp = m == 0 ? nullptr : static_cast<char*>(samp[buf(0)]) + (off / kSampleStride) * kb;
+    BlockSortArgs ba{static_cast<const char*>(ki) + off * kb, vi ? vi + off : nullptr,
+                     static_cast<char*>(kbuf[buf(0)]) + off * kb,
+                     vbuf[buf(0)] ? vbuf[buf(0)] + off : nullptr, len, mode, m == 0 ? mode : 0, sp};
+    e = timed(0, s, [&] { return launch_block_sort(kb, pairs, plan.tune.block_cfg, ba, s); });
+    if (e != cudaSuccess) return BCF_ECUDA;
+  }
   uint64_t* splits = reinterpret_cast<uint64_t*>(wsb + wl.splits);
   const uint64_t items = (n + plan.Tm - 1) / plan.Tm;
   for (int i = 1; i <= m; ++i) {
@@ -657,6 +676,132 @@ bcf_status run_sort_pb(void* ko, uint32_t* vo, const void* ki, const uint32_t* v
                        wl.seg_bytes, s, true);
 }
 
+// ---------------------------------------------------------------- host buffers
+
+// [header | device keys in | values in | keys out | values out | sort workspace]
+struct HostLayout {
+  size_t kin, vin, kout, vout, sort, sort_bytes, total;
+};
+HostLayout host_layout(uint64_t n, int kb, bool pairs, bool pb) {
+  HostLayout w;
+  w.kin = kAlign;
+  w.vin = align_up(w.kin + n * kb, kAlign);
+  w.kout = align_up(w.vin + (pairs ? n * 4 : 0), kAlign);
+  w.vout = align_up(w.kout + n * kb, kAlign);
+  w.sort = align_up(w.vout + (pairs ? n * 4 : 0), kAlign);
+  w.sort_bytes = pb ? pb_layout(n, kb, pairs).total : ws_layout(n, 0, kb, pairs).total;
+  w.total = align_up(w.sort + w.sort_bytes, kAlign);
+  return w;
+}
+
+// One copy stream per device, shared by all host-buffer calls (the copy
+// engines are shared anyway), and a pool of timing-free events.  A stream
+// wait takes the event's state at the time of the call, so an event can be
+// recorded again by a later call.
+struct CopyEngine {
+  std::mutex mu;
+  cudaStream_t stream[64] = {};
+  std::vector<cudaEvent_t> events[64];
+  size_t next[64] = {};
+};
+CopyEngine& copy_engine() {
+  static CopyEngine c;
+  return c;
+}
+cudaStream_t copy_stream(int dev) {
+  CopyEngine& c = copy_engine();
+  std::lock_guard<std::mutex> lk(c.mu);
+  if (!c.stream[dev] && cudaStreamCreateWithFlags(&c.stream[dev], cudaStreamNonBlocking) !=
+                            cudaSuccess)
+    c.stream[dev] = nullptr;
+  return c.stream[dev];
+}
+cudaEvent_t copy_event(int dev) {
+  constexpr size_t kPool = 64;
+  CopyEngine& c = copy_engine();
+  std::lock_guard<std::mutex> lk(c.mu);
+  auto& ev = c.events[dev];
+  if (ev.size() < kPool) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    ev.push_back(e);
+    return e;
+  }
+  return ev[c.next[dev]++ % kPool];
+}
+
+struct HostChunks {
+  const char* hk;
+  const uint32_t* hv;
+  char* dk;
+  uint32_t* dv;
+  uint64_t n, T;
+  int kb, dev;
+  cudaStream_t cs;
+};
+// Copies the input of tiles [t0, t1) on the copy stream and makes `s` wait
+// for it.
+bcf_status copy_in_tiles(void* ctx, uint64_t t0, uint64_t t1, cudaStream_t s) {
+  HostChunks& h = *static_cast<HostChunks*>(ctx);
+  const uint64_t off = t0 * h.T, end = t1 * h.T < h.n ? t1 * h.T : h.n;
+  if (cudaMemcpyAsync(h.dk + off * h.kb, h.hk + off * h.kb, (end - off) * h.kb,
+                      cudaMemcpyHostToDevice, h.cs) != cudaSuccess)
+    return BCF_ECUDA;
+  if (h.hv && cudaMemcpyAsync(h.dv + off, h.hv + off, (end - off) * 4, cudaMemcpyHostToDevice,
+                              h.cs) != cudaSuccess)
+    return BCF_ECUDA;
+  cudaEvent_t ev = copy_event(h.dev);
+  if (!ev || cudaEventRecord(ev, h.cs) != cudaSuccess || cudaStreamWaitEvent(s, ev, 0) != cudaSuccess)
+    return BCF_ECUDA;
+  return BCF_OK;
+}
+
+bcf_status run_sort_host(void* hko, uint32_t* hvo, const void* hki, const uint32_t* hvi,
+                         uint64_t n, bcf_dtype kt, const bcf_opts* o, void* ws, size_t ws_bytes,
+                         cudaStream_t s, bool pairs) {
+  if (!dtype_ok(kt)) return BCF_EINVAL;
+  if (n == 0) return BCF_OK;
+  if (!hko || !hki || (pairs && (!hvo || !hvi))) return BCF_EINVAL;
+  const int kb = key_bytes_of(kt);
+  const bool pb = o && o->algorithm == BCF_ALGO_PIVOT_BUCKETS;
+  if (o && o->algorithm != BCF_ALGO_MERGE && !pb) return BCF_EINVAL;
+  const HostLayout wl = host_layout(n, kb, pairs, pb);
+  if (ws_bytes < wl.total || !ws) return BCF_ENOMEM;
+  if (!aligned16(ws)) return BCF_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return BCF_ECUDA;
+  char* wsb = static_cast<char*>(ws);
+  char* dki = wsb + wl.kin;
+  uint32_t* dvi = pairs ? reinterpret_cast<uint32_t*>(wsb + wl.vin) : nullptr;
+  char* dko = wsb + wl.kout;
+  uint32_t* dvo = pairs ? reinterpret_cast<uint32_t*>(wsb + wl.vout) : nullptr;
+  bcf_status st;
+  if (pb) {  // the distribution needs the whole input first: one copy in
+    if (cudaMemcpyAsync(dki, hki, n * kb, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        (pairs && cudaMemcpyAsync(dvi, hvi, n * 4, cudaMemcpyHostToDevice, s) != cudaSuccess))
+      return BCF_ECUDA;
+    st = run_sort_pb(dko, dvo, dki, dvi, n, kt, o, wsb + wl.sort, wl.sort_bytes, s, pairs);
+  } else {
+    // copy in on the copy stream, in 8 pieces of whole tiles; each piece's
+    // block sort starts as soon as it has landed
+    cudaStream_t cs = copy_stream(dev);
+    cudaEvent_t start = copy_event(dev);
+    if (!cs || !start || cudaEventRecord(start, s) != cudaSuccess ||
+        cudaStreamWaitEvent(cs, start, 0) != cudaSuccess)  // the workspace is free by then
+      return BCF_ECUDA;
+    const Plan plan = make_plan(n, kb, pairs);
+    const uint64_t tiles = (n + plan.T - 1) / plan.T;
+    HostChunks h{static_cast<const char*>(hki), hvi, dki, dvi, n, plan.T, kb, dev, cs};
+    ChunkedInput ci{(tiles + 7) / 8, copy_in_tiles, &h};
+    st = run_sort(dko, dvo, dki, dvi, n, kt, o, wsb + wl.sort, wl.sort_bytes, s, pairs, &ci);
+  }
+  if (st != BCF_OK) return st;
+  if (cudaMemcpyAsync(hko, dko, n * kb, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      (pairs && cudaMemcpyAsync(hvo, dvo, n * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess))
+    return BCF_ECUDA;
+  return BCF_OK;
+}
+
 // ---------------------------------------------------------------- colored prefix sums
 
 struct CpsLayout {
@@ -725,6 +870,8 @@ size_t bcf_workspace_bytes(int op, uint64_t n, uint64_t nseg_or_k, bcf_dtype kt,
     case BCF_OP_MERGE: return ws_layout(n, nseg_or_k, kb, has_vals != 0).total;
     case BCF_OP_SEGMENTED: return seg_layout(n, nseg_or_k, kb, has_vals != 0).total;
     case BCF_OP_SORT_PB: return pb_layout(n, kb, has_vals != 0).total;
+    case BCF_OP_SORT_HOST: return host_layout(n, kb, has_vals != 0, false).total;
+    case BCF_OP_SORT_HOST_PB: return host_layout(n, kb, has_vals != 0, true).total;
     case BCF_OP_CPS:
       if (kt != BCF_U32 || has_vals || nseg_or_k < 1 || nseg_or_k > kCpsMaxColors) return 0;
       return cps_layout(n, static_cast<uint32_t>(nseg_or_k)).total;
@@ -768,6 +915,21 @@ bcf_status bcf_segmented_sort(void* keys_out, uint32_t* vals_out, const void* ke
   if ((vals_out == nullptr) != (vals_in == nullptr)) return BCF_EINVAL;
   return run_segmented(keys_out, vals_out, keys_in, vals_in, seg_offsets_dev, nseg, n_total, kt,
                        opts, ws, ws_bytes, stream);
+}
+
+bcf_status bcf_sort_keys_host(void* keys_out_host, const void* keys_in_host, uint64_t n,
+                              bcf_dtype kt, const bcf_opts* opts, void* ws, size_t ws_bytes,
+                              cudaStream_t stream) {
+  return run_sort_host(keys_out_host, nullptr, keys_in_host, nullptr, n, kt, opts, ws, ws_bytes,
+                       stream, false);
+}
+
+bcf_status bcf_sort_pairs_host(void* keys_out_host, uint32_t* vals_out_host,
+                               const void* keys_in_host, const uint32_t* vals_in_host, uint64_t n,
+                               bcf_dtype kt, const bcf_opts* opts, void* ws, size_t ws_bytes,
+                               cudaStream_t stream) {
+  return run_sort_host(keys_out_host, vals_out_host, keys_in_host, vals_in_host, n, kt, opts, ws,
+                       ws_bytes, stream, true);
 }
 
 bcf_status bcf_colored_prefix_sums(uint32_t* out, const uint32_t* values, const uint8_t* colors,

@@ -129,62 +129,109 @@ __global__ void __launch_bounds__(kPbThreads) pb_count_kernel(const PbArgs a) {
     a.counts[static_cast<uint64_t>(b) * a.ntiles + tile] = bucket_size(b, m, s_lo, s_hi, cnt);
 }
 
-// One CTA per tile: element i of the sorted tile goes to the output position
-// of its bucket's piece plus its rank inside the piece.
+// One CTA per tile: every piece of the sorted tile (its slots of one bucket)
+// is copied to its output position.  Pieces are cut into work items of
+// kPbChunk slots, dealt to the warps in turn, so a few long pieces (duplicate
+// keys) keep every warp busy; each lane keeps four loads in flight.
+constexpr uint32_t kPbChunk = 1024;
+
 template <typename K, bool PAIRS, bool MAP>
 __global__ void __launch_bounds__(kPbThreads) pb_scatter_kernel(const PbArgs a) {
-  __shared__ uint32_t s_start[kPbBuckets + 1];
-  __shared__ uint32_t s_off[kPbBuckets];
-  __shared__ uint32_t warp_sums[kPbThreads / 32];
+  __shared__ uint32_t s_start[kPbBuckets + 1];  // tile-local piece starts
+  __shared__ uint32_t s_item[kPbBuckets + 1];   // first work item of each piece
+  __shared__ uint32_t s_off[kPbBuckets];        // output position of each piece
+  __shared__ uint32_t warp_sums[2][kPbThreads / 32];
   const uint32_t tid = threadIdx.x, lane = tid & 31u, w = tid >> 5;
   const uint64_t tile = blockIdx.x;
   const uint64_t base = tile * a.T;
   const uint64_t rem = a.n - base;
   const uint32_t cnt = rem < a.T ? static_cast<uint32_t>(rem) : a.T;
-  // tile-local piece starts: exclusive scan of the piece sizes over the
-  // buckets, two buckets per thread
+  // exclusive scans over the buckets (two per thread) of the piece sizes and
+  // of the work items per piece
   constexpr uint32_t kPer = (kPbBuckets + kPbThreads - 1) / kPbThreads;
-  uint32_t c[kPer], sum = 0;
+  uint32_t c[kPer], sum = 0, items = 0;
 #pragma unroll
   for (uint32_t q = 0; q < kPer; ++q) {
     const uint32_t b = tid * kPer + q;
     c[q] = b < kPbBuckets ? a.counts[static_cast<uint64_t>(b) * a.ntiles + tile] : 0u;
     if (b < kPbBuckets) s_off[b] = a.offsets[static_cast<uint64_t>(b) * a.ntiles + tile];
     sum += c[q];
+    items += (c[q] + kPbChunk - 1) / kPbChunk;
   }
-  uint32_t incl = sum;
+  uint32_t incl = sum, iincl = items;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-    if (lane >= static_cast<uint32_t>(o)) incl += y;
+    const uint32_t z = __shfl_up_sync(0xFFFFFFFFu, iincl, o);
+    if (lane >= static_cast<uint32_t>(o)) {
+      incl += y;
+      iincl += z;
+    }
   }
-  if (lane == 31) warp_sums[w] = incl;
+  if (lane == 31) {
+    warp_sums[0][w] = incl;
+    warp_sums[1][w] = iincl;
+  }
   __syncthreads();
-  uint32_t run = incl - sum;
-  for (uint32_t q = 0; q < w; ++q) run += warp_sums[q];
+  uint32_t run = incl - sum, irun = iincl - items, total_items = 0;
+  for (uint32_t q = 0; q < kPbThreads / 32; ++q) {
+    if (q < w) {
+      run += warp_sums[0][q];
+      irun += warp_sums[1][q];
+    }
+    total_items += warp_sums[1][q];
+  }
 #pragma unroll
   for (uint32_t q = 0; q < kPer; ++q) {
     const uint32_t b = tid * kPer + q;
-    if (b < kPbBuckets) s_start[b] = run;
+    if (b < kPbBuckets) {
+      s_start[b] = run;
+      s_item[b] = irun;
+    }
     run += c[q];
+    irun += (c[q] + kPbChunk - 1) / kPbChunk;
   }
-  if (tid == 0) s_start[kPbBuckets] = cnt;
+  if (tid == 0) {
+    s_start[kPbBuckets] = cnt;
+    s_item[kPbBuckets] = total_items;
+  }
   __syncthreads();
   const K* x = static_cast<const K*>(a.x) + base;
   const uint32_t* xv = PAIRS ? a.xv + base : nullptr;
   K* kout = static_cast<K*>(a.kout);
-  for (uint32_t i = tid; i < cnt; i += kPbThreads) {
-    // the bucket holding i: last b with s_start[b] <= i (empty buckets share
-    // their start with the next one, so the search lands on the non-empty one)
-    uint32_t lo = 0, hi = kPbBuckets + 1;  // s_start[lo] <= i < s_start[hi]
+  for (uint32_t it = w; it < total_items; it += kPbThreads / 32) {
+    // the piece of this item: last bucket whose first item is <= it (pieces
+    // without items share their first item with the next piece)
+    uint32_t lo = 0, hi = kPbBuckets + 1;
     while (hi - lo > 1) {
       const uint32_t mid = (lo + hi) >> 1;
-      if (s_start[mid] <= i) lo = mid; else hi = mid;
+      if (s_item[mid] <= it) lo = mid; else hi = mid;
     }
-    const uint64_t dst = static_cast<uint64_t>(s_off[lo]) + (i - s_start[lo]);
-    const K key = x[i];
-    kout[dst] = MAP ? unmap_key(key, a.mode) : key;
-    if constexpr (PAIRS) a.vout[dst] = xv[i];
+    const uint32_t first = (it - s_item[lo]) * kPbChunk;
+    const uint32_t len = s_start[lo + 1] - s_start[lo];
+    const uint32_t stop = first + kPbChunk < len ? first + kPbChunk : len;
+    const uint32_t src = s_start[lo];
+    const uint64_t dst = s_off[lo];
+    for (uint32_t i = first + lane; i < stop; i += 4 * 32) {
+      K key[4];
+      uint32_t val[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const uint32_t j = i + u * 32;
+        if (j < stop) {
+          key[u] = x[src + j];
+          if constexpr (PAIRS) val[u] = xv[src + j];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const uint32_t j = i + u * 32;
+        if (j < stop) {
+          kout[dst + j] = MAP ? unmap_key(key[u], a.mode) : key[u];
+          if constexpr (PAIRS) a.vout[dst + j] = val[u];
+        }
+      }
+    }
   }
 }
 

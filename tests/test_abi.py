@@ -124,6 +124,13 @@ def test_host_side_argument_errors_return_before_launch(lib):
     # partial overlap of output and input
     assert lib.bcf_sort_keys(ctypes.c_void_p(0x10000), ctypes.c_void_p(0x10010), 100, 0, opts,
                              None, 0, None) == EINVAL
+    # host-buffer sorts: null host pointers, short workspace
+    assert lib.bcf_sort_keys_host(None, None, 10, 0, opts, None, 0, None) == EINVAL
+    assert lib.bcf_sort_keys_host(None, None, 0, 0, opts, None, 0, None) == 0
+    assert lib.bcf_sort_keys_host(ctypes.c_void_p(0x1000), ctypes.c_void_p(0x2000), 1 << 20, 0,
+                                  opts, ctypes.c_void_p(0x300000000), 4096, None) == 2
+    assert lib.bcf_sort_pairs_host(ctypes.c_void_p(0x1000), None, ctypes.c_void_p(0x2000), None,
+                                   10, 0, opts, None, 0, None) == EINVAL
     # unknown algorithm
     bad_algo = ctypes.byref(_native.BcfOpts(0, 1, 7))
     assert lib.bcf_sort_keys(ctypes.c_void_p(0x10000), ctypes.c_void_p(0x20000), 10, 0, bad_algo,
