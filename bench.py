@@ -410,6 +410,89 @@ def pb_bench(torch, dev, bcf, log2n=LOG2N):
     return {"n": n, "key": "u32", "results": out}
 
 
+def segmented_bench(torch, dev, bcf):
+    """Row A6 on its workload: 100,000 segments of log-uniform size in [1, 2^18]
+    (about 2.1e9 keys; seed 4000) and the 1 GiB variant ([1, 2^14]), uniform u32
+    keys, keys only and with u32 payloads, one persistent launch replayed from a
+    CUDA graph.  Bytes per key and pass: 2 x (key + payload)."""
+    import numpy as np
+
+    import workloads
+
+    out = {}
+    side = torch.cuda.Stream(dev)
+    for label, hi in (("[1, 2^18]", 1 << 18), ("[1, 2^14] (1 GiB variant)", 1 << 14)):
+        sizes = workloads.segment_sizes(100_000, hi, seed=4000)
+        offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+        n = int(offs[-1])
+        g = torch.Generator(device=dev)
+        g.manual_seed(4001)
+        kd = torch.randint(-2**31, 2**31 - 1, (n,), dtype=torch.int32, device=dev, generator=g)
+        ko = torch.empty_like(kd)
+        od = torch.from_numpy(offs).to(dev)
+        for pairs in (False, True):
+            vd = torch.arange(n, dtype=torch.int32, device=dev) if pairs else None
+            vo = torch.empty_like(vd) if pairs else None
+            ws = torch.empty(bcf.bcf_workspace_bytes(bcf.BCF_OP_SEGMENTED, n, sizes.size,
+                                                     bcf.BCF_U32, pairs),
+                             dtype=torch.uint8, device=dev)
+
+            def call():
+                bcf.bcf_segmented_sort(ko, vo, kd, vd, od, kt=bcf.BCF_U32, ws=ws, stream=side)
+
+            with torch.cuda.stream(side):
+                call()
+            side.synchronize()
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=side):
+                call()
+            ms = timed_ms(torch, torch.cuda.current_stream(dev), graph.replay, warmup=2, reps=5)
+            out[f"{label}{' +u32' if pairs else ''}"] = {
+                "segments": int(sizes.size), "keys": n, "ms": ms, "keys_per_s": n / (ms * 1e-3),
+                "payload": "u32" if pairs else None}
+            del vd, vo, ws, graph
+            torch.cuda.empty_cache()
+        del kd, ko, od
+        torch.cuda.empty_cache()
+    if bcf.bcf_last_device_error() != 0:
+        raise RuntimeError("segmented sort: device error word set")
+    return {"graph_replay": True, "results": out}
+
+
+def merge_runs_bench(torch, dev, bcf, peak):
+    """Row A5 on its workload: k in {2, 16, 256} sorted u32 runs, 2^27 keys in
+    total, lengths log-uniform in [2^10, 2^24] rescaled to the total (seed
+    3000 + k), merged into one output; keys only and with u32 payloads."""
+    import numpy as np
+
+    import workloads
+
+    total = 1 << 27
+    out = {}
+    stream = torch.cuda.current_stream(dev)
+    for k in (2, 16, 256):
+        keys, offs = workloads.sorted_runs(k, total)
+        kd = torch.from_numpy(keys.view(np.int32)).to(dev)
+        ko = torch.empty_like(kd)
+        offl = [int(x) for x in offs]
+        for pairs in (False, True):
+            vd = torch.arange(total, dtype=torch.int32, device=dev) if pairs else None
+            vo = torch.empty_like(vd) if pairs else None
+            ws = torch.empty(bcf.bcf_workspace_bytes(bcf.BCF_OP_MERGE, total, k, bcf.BCF_U32,
+                                                     pairs), dtype=torch.uint8, device=dev)
+            ms = timed_ms(torch, stream, lambda: bcf.bcf_merge_runs(
+                ko, vo, kd, vd, offl, kt=bcf.BCF_U32, ws=ws, stream=stream), warmup=2, reps=5)
+            passes = int(np.ceil(np.log2(k)))
+            gbs = passes * 2 * total * (4 + (4 if pairs else 0)) / (ms * 1e-3) / 1e9
+            out[f"k={k}{' +u32' if pairs else ''}"] = {
+                "ms": ms, "keys_per_s": total / (ms * 1e-3), "merge_passes": passes,
+                "gbs_over_passes": gbs, "frac": gbs / peak}
+            del vd, vo, ws
+            torch.cuda.empty_cache()
+        del kd, ko
+    return {"total_keys": total, "results": out}
+
+
 def profile_case(args):
     """A small case of one path, for ncu captures (inputs larger than L2, a
     few launches): 'cps' = colored prefix sums of 2^26 elements, 16 colors,
@@ -439,7 +522,7 @@ def profile_case(args):
         for _ in range(2):
             bcf.bcf_sort_keys(ko, kd, kt=bcf.BCF_U32, algorithm="pivot_buckets")
     else:
-        keys, offs = workloads.segments(20_000, 1 << 14, "u32", seed=4000)
+        keys, offs = workloads.segments(5_000, 1 << 18, "u32", seed=4000)
         n = keys.size
         kd = torch.from_numpy(keys.view(np.int32)).to(dev)
         ko = torch.empty_like(kd)
@@ -577,7 +660,9 @@ def run_gpu(args, world, rank, local, pg):
     if not args.no_extras:
         extras = {"key_types": key_types_bench(torch, dev, bcf, peak),
                   "colored_prefix_sums": cps_bench(torch, dev, bcf, peak),
-                  "pivot_buckets": pb_bench(torch, dev, bcf)}
+                  "pivot_buckets": pb_bench(torch, dev, bcf),
+                  "merge_runs": merge_runs_bench(torch, dev, bcf, peak),
+                  "segmented": segmented_bench(torch, dev, bcf)}
 
     if rank != 0:
         return 0

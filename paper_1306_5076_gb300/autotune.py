@@ -98,7 +98,7 @@ def tune_sort(torch, kb, pairs, reps, log):
     return rows
 
 
-def tune_segmented(torch, kb, pairs, reps, log, nseg=20000, hi=1 << 16):
+def tune_segmented(torch, kb, pairs, reps, log, nseg=5000, hi=1 << 18):
     import numpy as np
 
     import workloads

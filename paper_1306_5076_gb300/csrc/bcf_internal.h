@@ -78,7 +78,7 @@ bool block_cfg_supported(int key_bytes, bool pairs, int cfg);
 bool merge_cfg_supported(int key_bytes, bool pairs, int cfg);
 
 // Segmented sort (persistent kernel); tile = merge tile = E * NT.
-constexpr TileCfg kSegCfgs[] = {{16, 256}, {16, 128}, {32, 128}};
+constexpr TileCfg kSegCfgs[] = {{16, 256}, {16, 128}, {32, 128}, {32, 256}, {32, 512}};
 constexpr int kNumSegCfgs = sizeof(kSegCfgs) / sizeof(kSegCfgs[0]);
 constexpr uint64_t kMinSegTile = 2048;
 

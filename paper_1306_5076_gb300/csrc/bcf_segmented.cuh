@@ -461,6 +461,12 @@ cudaError_t dispatch_seg(int cfg, const SegArgs& a, cudaStream_t s) {
     case 2:
       if constexpr (!PAIRS && sizeof(K) == 4) return launch_seg<K, PAIRS, 32, 128, MAP>(a, s);
       break;
+    case 3:  // larger tiles: more bytes per work item's latency chain
+      if constexpr (!PAIRS && sizeof(K) == 4) return launch_seg<K, PAIRS, 32, 256, MAP>(a, s);
+      break;
+    case 4:
+      if constexpr (!PAIRS && sizeof(K) == 4) return launch_seg<K, PAIRS, 32, 512, MAP>(a, s);
+      break;
     default: break;
   }
   return cudaErrorInvalidValue;
