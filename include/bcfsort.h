@@ -10,8 +10,8 @@
  * --------------------------------------
  *  - Memory.  Every key / value pointer is DEVICE memory owned by the caller
  *    and must be 16-byte aligned when the element count is non-zero.  Keys are
- *    arrays of the key type (4 bytes for BCF_U32 / BCF_I32 / BCF_F32, 8 for
- *    BCF_U64 / BCF_I64 / BCF_F64);
+ *    arrays of the key type (2 bytes for BCF_U16 / BCF_I16, 4 for BCF_U32 /
+ *    BCF_I32 / BCF_F32, 8 for BCF_U64 / BCF_I64 / BCF_F64);
  *    values are uint32_t arrays of the same length.  Arrays are contiguous.
  *  - Workspace.  The library allocates nothing on the sort path.  Calls that
  *    need scratch take a caller-provided device workspace `ws` of at least
@@ -26,8 +26,8 @@
  *    A launch failure returns BCF_ECUDA.  Device-side bounded waits that run
  *    out set a device error word that bcf_last_device_error() reports.
  *  - Order.  Keys are compared after an order-preserving map to unsigned
- *    integers: u32 / u64 as-is, i32 / i64 in two's-complement order, f32 /
- *    f64 under IEEE 754 totalOrder
+ *    integers: u16 / u32 / u64 as-is, i16 / i32 / i64 in two's-complement
+ *    order, f32 / f64 under IEEE 754 totalOrder
  *    (-NaN < -inf < ... < -0 < +0 < ... < +inf < +NaN).  Keys are returned
  *    bit-for-bit (NaN payloads and the sign of zero survive).  Descending
  *    order reverses the key order; ties ALWAYS keep input order (stable), in
@@ -61,7 +61,9 @@ typedef enum {
     BCF_F32 = 2, /* IEEE 754 binary32, totalOrder */
     BCF_I32 = 3, /* int32_t, two's-complement order */
     BCF_I64 = 4, /* int64_t, two's-complement order */
-    BCF_F64 = 5  /* IEEE 754 binary64, totalOrder */
+    BCF_F64 = 5, /* IEEE 754 binary64, totalOrder */
+    BCF_U16 = 6, /* uint16_t, natural order (sorted as zero-extended 32-bit keys) */
+    BCF_I16 = 7  /* int16_t, two's-complement order (sorted as sign-extended i32) */
 } bcf_dtype;
 
 typedef enum {
@@ -94,7 +96,7 @@ typedef struct {
 
 /* Operation codes for bcf_workspace_bytes. */
 enum { BCF_OP_SORT = 0, BCF_OP_MERGE = 1, BCF_OP_SEGMENTED = 2, BCF_OP_CPS = 3,
-       BCF_OP_SORT_PB = 4, BCF_OP_SORT_HOST = 5, BCF_OP_SORT_HOST_PB = 6 };
+       BCF_OP_SORT_PB = 4, BCF_OP_SORT_HOST = 5, BCF_OP_SORT_HOST_PB = 6, BCF_OP_SORT_WIDE = 7 };
 
 /*
  * Workspace size in bytes for an operation.
@@ -106,7 +108,9 @@ enum { BCF_OP_SORT = 0, BCF_OP_MERGE = 1, BCF_OP_SEGMENTED = 2, BCF_OP_CPS = 3,
  *             BCF_OP_SORT_PB: sort n keys with BCF_ALGO_PIVOT_BUCKETS (pairs if
  *             has_vals; also enough for BCF_ALGO_MERGE);
  *             BCF_OP_SORT_HOST / BCF_OP_SORT_HOST_PB: bcf_sort_*_host with the
- *             merge / pivot-bucket algorithm.
+ *             merge / pivot-bucket algorithm;
+ *             BCF_OP_SORT_WIDE: bcf_sort_pairs_wide (either algorithm; the
+ *             payload width does not matter).
  * Returns 0 for an unknown op or dtype.  The size is about one extra copy of
  * the keys (+ values) -- the merge is not in place, as in the paper (Sec. 4
  * remarks that BCFMergesort needs less extra space than its competitors) --
@@ -213,6 +217,25 @@ bcf_status bcf_profile_collect(bcf_profile* out);
 
 /* Version string of the library. */
 const char* bcf_version(void);
+
+/* ---- payloads wider than 32 bits ------------------------------------------ */
+
+/*
+ * Stable sort by key with a payload row of `val_bytes` bytes per key (a
+ * multiple of 4, up to 4096: u64 row ids, pointers, small structs).  The keys
+ * are sorted with 32-bit row indices as payload (bcf_sort_pairs, either
+ * algorithm), then the rows are gathered in the sorted order; the result is
+ * the stable order, ties in input order.
+ *   keys_out  device, n keys (may equal keys_in); 16-byte aligned
+ *   vals_out  device, n rows; must not overlap vals_in (the gather reads the
+ *             rows in any order); 4-byte aligned (16 for the fastest copies)
+ *   ws        bcf_workspace_bytes(BCF_OP_SORT_WIDE, n, 0, kt, 1) bytes
+ * n must be below 2^32 (BCF_EUNSUPPORTED otherwise).
+ */
+bcf_status bcf_sort_pairs_wide(void* keys_out, void* vals_out, const void* keys_in,
+                               const void* vals_in, uint64_t n, uint32_t val_bytes, bcf_dtype kt,
+                               const bcf_opts* opts, void* ws, size_t ws_bytes,
+                               cudaStream_t stream);
 
 /* ---- sorting host buffers --------------------------------------------------- */
 
@@ -403,7 +426,9 @@ bcf_status bcf_arena_destroy(bcf_arena* a);
  * array) lives in a device array inside the library.
  *
  *   - n <= BCF_STATIC_MAX_KEYS, else BCF_EUNSUPPORTED before any launch; keys
- *     only; otherwise the arguments, results and errors of bcf_sort_keys.
+ *     only; 16-bit keys and opts->algorithm other than BCF_ALGO_MERGE are not
+ *     available here (BCF_EUNSUPPORTED, resp. the merge path is taken);
+ *     otherwise the arguments, results and errors of bcf_sort_keys.
  *   - The array (about 8 MiB) is held by every GPU that loads the library until
  *     the process exits.  The call allocates nothing.
  *   - All calls share the array: calls whose GPU work overlaps in time (other

@@ -9,8 +9,8 @@ The arithmetic lives in ``bcf_oracle.c`` (plain C, built with gcc into
 Each function states the definition it computes:
 
 * :func:`sort` -- "sort N keys" (Sec. 3): stable ascending/descending order,
-  f32/f64 keys under IEEE 754 totalOrder, i32/i64 as signed integers,
-  u32/u64 as unsigned, payloads kept in input order on ties.
+  f32/f64 keys under IEEE 754 totalOrder, i16/i32/i64 as signed integers,
+  u16/u32/u64 as unsigned, payloads kept in input order on ties.
 * :func:`merge_runs` -- "merge sorted sequences" (Sec. 3.2, Algorithm 6): the
   stable sort of the runs concatenated in run order.
 * :func:`segmented_sort` -- :func:`sort` applied to every segment.
@@ -34,7 +34,8 @@ _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
 
 _DTYPE_CODE = {np.dtype(np.uint32): 0, np.dtype(np.uint64): 1, np.dtype(np.float32): 2,
-               np.dtype(np.int32): 3, np.dtype(np.int64): 4, np.dtype(np.float64): 5}
+               np.dtype(np.int32): 3, np.dtype(np.int64): 4, np.dtype(np.float64): 5,
+               np.dtype(np.uint16): 6, np.dtype(np.int16): 7}
 
 _lock = threading.Lock()
 _lib = None

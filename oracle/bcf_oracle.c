@@ -29,8 +29,8 @@
  * The merge step takes the element of the LEFT run unless the right one is
  * strictly smaller, which is what makes it stable.
  *
- * Key order.  u32 and u64: the integers' natural order.  i32 and i64: C's
- * signed comparison of the two's-complement values.  f32 and f64: IEEE 754
+ * Key order.  u16, u32 and u64: the integers' natural order.  i16, i32 and
+ * i64: C's signed comparison of the two's-complement values.  f32 and f64: IEEE 754
  * totalOrder (IEEE 754-2008 Sec. 5.10), written as a case analysis on sign and
  * magnitude bits: every negative-signed value precedes every positive-signed
  * one; among positive-signed values a larger magnitude field (exponent and
@@ -55,7 +55,7 @@
 #include <string.h>
 
 enum { ORACLE_U32 = 0, ORACLE_U64 = 1, ORACLE_F32 = 2, ORACLE_I32 = 3, ORACLE_I64 = 4,
-       ORACLE_F64 = 5 };
+       ORACLE_F64 = 5, ORACLE_U16 = 6, ORACLE_I16 = 7 };
 
 typedef struct {
     const void* keys;
@@ -89,14 +89,18 @@ static int f64_total_less(uint64_t a, uint64_t b)
 
 static size_t key_size(int dtype)
 {
+    if (dtype == ORACLE_U16 || dtype == ORACLE_I16)
+        return 2;
     return (dtype == ORACLE_U64 || dtype == ORACLE_I64 || dtype == ORACLE_F64) ? 8 : 4;
 }
 
 static uint64_t key_bits(const order_ctx* c, uint64_t i)
 {
-    if (key_size(c->dtype) == 8)
-        return ((const uint64_t*)c->keys)[i];
-    return ((const uint32_t*)c->keys)[i];
+    switch (key_size(c->dtype)) {
+    case 8:  return ((const uint64_t*)c->keys)[i];
+    case 2:  return ((const uint16_t*)c->keys)[i];
+    default: return ((const uint32_t*)c->keys)[i];
+    }
 }
 
 /* Strict "a goes before b" under the ascending key order of dtype. */
@@ -107,6 +111,7 @@ static int bits_less(int dtype, uint64_t a, uint64_t b)
     case ORACLE_F64: return f64_total_less(a, b);
     case ORACLE_I32: return (int32_t)(uint32_t)a < (int32_t)(uint32_t)b;
     case ORACLE_I64: return (int64_t)a < (int64_t)b;
+    case ORACLE_I16: return (int16_t)(uint16_t)a < (int16_t)(uint16_t)b;
     default:         return a < b;
     }
 }
@@ -234,7 +239,7 @@ int oracle_key_less(int dtype, uint64_t a, uint64_t b)
 int oracle_sort(void* keys_out, uint32_t* vals_out, const void* keys_in,
                 const uint32_t* vals_in, uint64_t n, int dtype, int descending, int nthreads)
 {
-    if (dtype < ORACLE_U32 || dtype > ORACLE_F64)
+    if (dtype < ORACLE_U32 || dtype > ORACLE_I16)
         return -1;
     if ((vals_out == NULL) != (vals_in == NULL))
         return -1;

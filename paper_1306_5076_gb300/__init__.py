@@ -16,18 +16,19 @@ import ctypes
 
 from . import _native
 from ._native import (BCF_ALGO_MERGE, BCF_ALGO_PIVOT_BUCKETS, BCF_CPS_BANKED, BCF_CPS_ROWS,
-                      BCF_F32, BCF_F64, BCF_I32, BCF_I64, BCF_OP_CPS, BCF_OP_MERGE,
-                      BCF_OP_SEGMENTED, BCF_OP_SORT, BCF_OP_SORT_PB, BCF_U32, BCF_U64)
+                      BCF_F32, BCF_F64, BCF_I16, BCF_I32, BCF_I64, BCF_OP_CPS, BCF_OP_MERGE,
+                      BCF_OP_SEGMENTED, BCF_OP_SORT, BCF_OP_SORT_PB, BCF_U16, BCF_U32, BCF_U64)
 
 __all__ = [
     "BcfError", "bcf_workspace_bytes", "bcf_sort_keys", "bcf_sort_pairs", "bcf_merge_runs",
     "bcf_segmented_sort", "bcf_last_device_error", "bcf_sort_plan", "bcf_profile_enable",
     "bcf_profile_collect", "bcf_version", "bcf_sort_keys_static", "bcf_tuning_set",
     "bcf_tuning_config", "bcf_tuning_supported", "key_dtype_of", "BCF_U32",
-    "BCF_U64", "BCF_F32", "BCF_I32", "BCF_I64", "BCF_F64",
+    "BCF_U64", "BCF_F32", "BCF_I32", "BCF_I64", "BCF_F64", "BCF_U16", "BCF_I16",
     "BCF_OP_SORT", "BCF_OP_MERGE", "BCF_OP_SEGMENTED", "BCF_OP_CPS",
     "bcf_colored_prefix_sums", "BCF_CPS_BANKED", "BCF_CPS_ROWS", "BCF_OP_SORT_PB",
     "BCF_ALGO_MERGE", "BCF_ALGO_PIVOT_BUCKETS", "bcf_sort_keys_host", "bcf_sort_pairs_host",
+    "bcf_sort_pairs_wide",
 ]
 
 
@@ -45,13 +46,14 @@ def _check(status: int, what: str) -> None:
 
 def key_dtype_of(t) -> int:
     """C key-type code of a tensor's dtype: float32 / float64 sort under IEEE
-    totalOrder, int32 / int64 as signed integers, uint32 / uint64 as unsigned.
+    totalOrder, int16 / int32 / int64 as signed integers, uint16 / uint32 /
+    uint64 as unsigned.
     (To sort the bits of a signed tensor as unsigned, pass ``kt`` explicitly.)"""
     import torch
 
     table = {torch.float32: BCF_F32, torch.float64: BCF_F64, torch.int32: BCF_I32,
-             torch.int64: BCF_I64}
-    for name, code in (("uint32", BCF_U32), ("uint64", BCF_U64)):
+             torch.int64: BCF_I64, torch.int16: BCF_I16}
+    for name, code in (("uint32", BCF_U32), ("uint64", BCF_U64), ("uint16", BCF_U16)):
         if hasattr(torch, name):
             table[getattr(torch, name)] = code
     try:
@@ -116,6 +118,25 @@ def bcf_sort_keys(keys_out, keys_in, *, descending=False, ws=None, stream=None, 
     _check(_native.load().bcf_sort_keys(_ptr(keys_out), _ptr(keys_in), n, kt, opts,
                                         _ptr(ws), wsb, _stream(stream)), "bcf_sort_keys")
     return keys_out
+
+
+def bcf_sort_pairs_wide(keys_out, vals_out, keys_in, vals_in, *, descending=False, ws=None,
+                        stream=None, kt=None, algorithm="merge"):
+    """Stable sort by key with payload rows wider than 32 bits: ``vals_in`` is a
+    CUDA tensor whose first dimension is n (any dtype; each row a multiple of 4
+    bytes), e.g. int64 row ids or an [n, 3] float32 array.  ``vals_out`` must
+    be a different tensor of the same shape."""
+    kt = key_dtype_of(keys_in) if kt is None else kt
+    n = keys_in.numel()
+    if vals_in.shape != vals_out.shape or vals_in.shape[0] != n:
+        raise ValueError("bcf_sort_pairs_wide: payloads must be n rows, in and out alike")
+    row_bytes = vals_in.numel() * vals_in.element_size() // max(n, 1)
+    ws, wsb = _workspace(_native.BCF_OP_SORT_WIDE, n, 0, kt, True, ws, keys_in.device)
+    _check(_native.load().bcf_sort_pairs_wide(_ptr(keys_out), _ptr(vals_out), _ptr(keys_in),
+                                              _ptr(vals_in), n, row_bytes, kt,
+                                              _opts(descending, algorithm), _ptr(ws), wsb,
+                                              _stream(stream)), "bcf_sort_pairs_wide")
+    return keys_out, vals_out
 
 
 def _host_ptr(t):

@@ -12,10 +12,10 @@ import threading
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libbcfsort.so")
 
-BCF_U32, BCF_U64, BCF_F32, BCF_I32, BCF_I64, BCF_F64 = 0, 1, 2, 3, 4, 5
+BCF_U32, BCF_U64, BCF_F32, BCF_I32, BCF_I64, BCF_F64, BCF_U16, BCF_I16 = 0, 1, 2, 3, 4, 5, 6, 7
 BCF_CPS_BANKED, BCF_CPS_ROWS = 0, 1
 (BCF_OP_SORT, BCF_OP_MERGE, BCF_OP_SEGMENTED, BCF_OP_CPS, BCF_OP_SORT_PB, BCF_OP_SORT_HOST,
- BCF_OP_SORT_HOST_PB) = 0, 1, 2, 3, 4, 5, 6
+ BCF_OP_SORT_HOST_PB, BCF_OP_SORT_WIDE) = 0, 1, 2, 3, 4, 5, 6, 7
 BCF_ALGO_MERGE, BCF_ALGO_PIVOT_BUCKETS = 0, 1
 STATUS = {0: "BCF_OK", 1: "BCF_EINVAL", 2: "BCF_ENOMEM", 3: "BCF_ECUDA", 4: "BCF_ETIMEOUT",
           5: "BCF_EUNSUPPORTED"}
@@ -93,6 +93,8 @@ SIGNATURES = {
     "bcf_version": (ctypes.c_char_p, []),
     "bcf_sort_keys_static": (_i32, [_vp, _vp, _u64, _i32, ctypes.POINTER(BcfOpts), _vp]),
     "bcf_colored_prefix_sums": (_i32, [_vp, _vp, _vp, _u64, _u32, _i32, _i32, _vp, _sz, _vp]),
+    "bcf_sort_pairs_wide": (_i32, [_vp, _vp, _vp, _vp, _u64, _u32, _i32, ctypes.POINTER(BcfOpts),
+                                   _vp, _sz, _vp]),
     "bcf_sort_keys_host": (_i32, [_vp, _vp, _u64, _i32, ctypes.POINTER(BcfOpts), _vp, _sz, _vp]),
     "bcf_sort_pairs_host": (_i32, [_vp, _vp, _vp, _vp, _u64, _i32, ctypes.POINTER(BcfOpts), _vp,
                                    _sz, _vp]),

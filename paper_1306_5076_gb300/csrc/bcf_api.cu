@@ -31,10 +31,14 @@ namespace {
 constexpr size_t kAlign = 256;
 constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-bool dtype_ok(int kt) { return kt >= BCF_U32 && kt <= BCF_F64; }
+bool dtype_ok(int kt) { return kt >= BCF_U32 && kt <= BCF_I16; }
+bool is16(int kt) { return kt == BCF_U16 || kt == BCF_I16; }
 int key_bytes_of(bcf_dtype kt) {
+  if (is16(kt)) return 2;
   return (kt == BCF_U64 || kt == BCF_I64 || kt == BCF_F64) ? 8 : 4;
 }
+// 16-bit keys go through the 32-bit sort: zero- (u16) or sign-extended (i16).
+bcf_dtype wide_of(bcf_dtype kt) { return kt == BCF_U16 ? BCF_U32 : BCF_I32; }
 
 // The key map of the device code: bit 0 totalOrder (f32 / f64), bit 2
 // two's-complement (i32 / i64), bit 1 descending.
@@ -676,20 +680,146 @@ bcf_status run_sort_pb(void* ko, uint32_t* vo, const void* ki, const uint32_t* v
                        wl.seg_bytes, s, true);
 }
 
+// ---------------------------------------------------------------- dispatch
+
+bcf_status sort_any(void* ko, uint32_t* vo, const void* ki, const uint32_t* vi, uint64_t n,
+                    bcf_dtype kt, const bcf_opts* o, void* ws, size_t ws_bytes, cudaStream_t s,
+                    bool pairs);
+
+// ---------------------------------------------------------------- 16-bit keys
+
+// [header | widened keys in | widened keys out | workspace of the 32-bit call]
+struct Wide16Layout {
+  size_t kin, kout, inner, total;
+};
+Wide16Layout wide16_layout(uint64_t n, size_t inner_bytes) {
+  Wide16Layout w;
+  w.kin = kAlign;
+  w.kout = align_up(w.kin + n * 4, kAlign);
+  w.inner = align_up(w.kout + n * 4, kAlign);
+  w.total = align_up(w.inner + inner_bytes, kAlign);
+  return w;
+}
+
+// Widens the 16-bit keys [0, n) of `ki`, runs `op(kout32, kin32, inner_ws,
+// inner_bytes)` -- the same call on 32-bit keys -- and narrows its output
+// [lo, n) into `ko`.  The widening is order-preserving (zero extension for
+// u16, sign extension for i16), so the 32-bit result is the 16-bit one.
+template <typename Op>
+bcf_status via_wide16(void* ko, const void* ki, uint64_t lo, uint64_t n, bcf_dtype kt, void* ws,
+                      size_t ws_bytes, size_t inner_bytes, cudaStream_t s, Op op) {
+  const Wide16Layout wl = wide16_layout(n, inner_bytes);
+  if (ws_bytes < wl.total || !ws) return BCF_ENOMEM;
+  if (!aligned16(ws)) return BCF_EINVAL;
+  const Span sw{ws, wl.total};
+  if (overlap(sw, {ko, n * 2}) || overlap(sw, {ki, n * 2})) return BCF_EINVAL;
+  char* wsb = static_cast<char*>(ws);
+  uint32_t* kin32 = reinterpret_cast<uint32_t*>(wsb + wl.kin);
+  uint32_t* kout32 = reinterpret_cast<uint32_t*>(wsb + wl.kout);
+  if (launch_widen16(kin32, static_cast<const uint16_t*>(ki), n, kt == BCF_I16, s) !=
+      cudaSuccess)
+    return BCF_ECUDA;
+  const bcf_status st = op(kout32, kin32, wsb + wl.inner, inner_bytes);
+  if (st != BCF_OK) return st;
+  if (launch_narrow16(static_cast<uint16_t*>(ko) + lo, kout32 + lo, n - lo, s) != cudaSuccess)
+    return BCF_ECUDA;
+  return BCF_OK;
+}
+
+// The workspace of a device sort of n keys of type kt.
+size_t sort_ws_bytes(uint64_t n, bcf_dtype kt, bool pairs, bool pb) {
+  if (is16(kt)) return wide16_layout(n, sort_ws_bytes(n, wide_of(kt), pairs, pb)).total;
+  const int kb = key_bytes_of(kt);
+  return pb ? pb_layout(n, kb, pairs).total : ws_layout(n, 0, kb, pairs).total;
+}
+
+// A device sort: merge passes or pivot buckets, any key type.
+bcf_status sort_any(void* ko, uint32_t* vo, const void* ki, const uint32_t* vi, uint64_t n,
+                    bcf_dtype kt, const bcf_opts* o, void* ws, size_t ws_bytes, cudaStream_t s,
+                    bool pairs) {
+  const bool pb = o && o->algorithm == BCF_ALGO_PIVOT_BUCKETS;
+  if (o && o->algorithm != BCF_ALGO_MERGE && !pb) return BCF_EINVAL;
+  if (is16(kt)) {
+    bcf_status st = check_common(ko, vo, ki, vi, n, kt, pairs);
+    if (st != BCF_OK || n == 0) return st;
+    const bcf_dtype wk = wide_of(kt);
+    return via_wide16(ko, ki, 0, n, kt, ws, ws_bytes, sort_ws_bytes(n, wk, pairs, pb), s,
+                      [&](void* k32o, const void* k32i, void* iw, size_t ib) {
+                        return sort_any(k32o, vo, k32i, vi, n, wk, o, iw, ib, s, pairs);
+                      });
+  }
+  if (pb) return run_sort_pb(ko, vo, ki, vi, n, kt, o, ws, ws_bytes, s, pairs);
+  return run_sort(ko, vo, ki, vi, n, kt, o, ws, ws_bytes, s, pairs);
+}
+
+// ---------------------------------------------------------------- wide payloads
+
+// [header | row indices in | row indices out | workspace of the pairs sort]
+struct WideLayout {
+  size_t idx_in, idx_out, inner, inner_bytes, total;
+};
+WideLayout wide_layout(uint64_t n, bcf_dtype kt) {
+  WideLayout w;
+  w.idx_in = kAlign;
+  w.idx_out = align_up(w.idx_in + n * 4, kAlign);
+  w.inner = align_up(w.idx_out + n * 4, kAlign);
+  const size_t merge = sort_ws_bytes(n, kt, true, false), pb = sort_ws_bytes(n, kt, true, true);
+  w.inner_bytes = merge > pb ? merge : pb;  // either algorithm
+  w.total = align_up(w.inner + w.inner_bytes, kAlign);
+  return w;
+}
+
+// Stable sort by key with payload rows of `val_bytes` bytes: the pairs sort of
+// (key, row index), then the rows gathered in the sorted order.
+bcf_status run_sort_wide(void* ko, void* vo, const void* ki, const void* vi, uint64_t n,
+                         uint32_t val_bytes, bcf_dtype kt, const bcf_opts* o, void* ws,
+                         size_t ws_bytes, cudaStream_t s) {
+  if (!dtype_ok(kt) || val_bytes < 4 || val_bytes % 4 != 0 || val_bytes > 4096) return BCF_EINVAL;
+  if (n == 0) return BCF_OK;
+  if (!ko || !ki || !vo || !vi) return BCF_EINVAL;
+  if (!aligned16(ko) || !aligned16(ki) || (reinterpret_cast<uintptr_t>(vo) & 3u) ||
+      (reinterpret_cast<uintptr_t>(vi) & 3u))
+    return BCF_EINVAL;
+  if (n > 0xFFFFFFFFull) return BCF_EUNSUPPORTED;  // 32-bit row indices
+  const size_t kb = key_bytes_of(kt);
+  const Span sko{ko, n * kb}, ski{ki, n * kb}, svo{vo, n * val_bytes}, svi{vi, n * val_bytes};
+  // the payloads cannot be permuted in place: the gather reads rows in any order
+  if (bad_overlap(sko, ski) || overlap(svo, svi) || overlap(sko, svo) || overlap(sko, svi) ||
+      overlap(ski, svo))
+    return BCF_EINVAL;
+  const WideLayout wl = wide_layout(n, kt);
+  if (ws_bytes < wl.total || !ws) return BCF_ENOMEM;
+  if (!aligned16(ws)) return BCF_EINVAL;
+  const Span sw{ws, wl.total};
+  if (overlap(sw, sko) || overlap(sw, ski) || overlap(sw, svo) || overlap(sw, svi))
+    return BCF_EINVAL;
+  char* wsb = static_cast<char*>(ws);
+  uint32_t* idx_in = reinterpret_cast<uint32_t*>(wsb + wl.idx_in);
+  uint32_t* idx_out = reinterpret_cast<uint32_t*>(wsb + wl.idx_out);
+  if (launch_iota(idx_in, n, s) != cudaSuccess) return BCF_ECUDA;
+  const bcf_status st =
+      sort_any(ko, idx_out, ki, idx_in, n, kt, o, wsb + wl.inner, wl.inner_bytes, s, true);
+  if (st != BCF_OK) return st;
+  return from_cuda(launch_gather(vo, vi, idx_out, n, val_bytes, s));
+}
+
 // ---------------------------------------------------------------- host buffers
 
 // [header | device keys in | values in | keys out | values out | sort workspace]
 struct HostLayout {
   size_t kin, vin, kout, vout, sort, sort_bytes, total;
 };
-HostLayout host_layout(uint64_t n, int kb, bool pairs, bool pb) {
+size_t sort_ws_bytes(uint64_t n, bcf_dtype kt, bool pairs, bool pb);
+
+HostLayout host_layout(uint64_t n, bcf_dtype kt, bool pairs, bool pb) {
   HostLayout w;
+  const int kb = key_bytes_of(kt);
   w.kin = kAlign;
   w.vin = align_up(w.kin + n * kb, kAlign);
   w.kout = align_up(w.vin + (pairs ? n * 4 : 0), kAlign);
   w.vout = align_up(w.kout + n * kb, kAlign);
   w.sort = align_up(w.vout + (pairs ? n * 4 : 0), kAlign);
-  w.sort_bytes = pb ? pb_layout(n, kb, pairs).total : ws_layout(n, 0, kb, pairs).total;
+  w.sort_bytes = sort_ws_bytes(n, kt, pairs, pb);
   w.total = align_up(w.sort + w.sort_bytes, kAlign);
   return w;
 }
@@ -765,7 +895,7 @@ bcf_status run_sort_host(void* hko, uint32_t* hvo, const void* hki, const uint32
   const int kb = key_bytes_of(kt);
   const bool pb = o && o->algorithm == BCF_ALGO_PIVOT_BUCKETS;
   if (o && o->algorithm != BCF_ALGO_MERGE && !pb) return BCF_EINVAL;
-  const HostLayout wl = host_layout(n, kb, pairs, pb);
+  const HostLayout wl = host_layout(n, kt, pairs, pb);
   if (ws_bytes < wl.total || !ws) return BCF_ENOMEM;
   if (!aligned16(ws)) return BCF_EINVAL;
   int dev = 0;
@@ -776,11 +906,11 @@ bcf_status run_sort_host(void* hko, uint32_t* hvo, const void* hki, const uint32
   char* dko = wsb + wl.kout;
   uint32_t* dvo = pairs ? reinterpret_cast<uint32_t*>(wsb + wl.vout) : nullptr;
   bcf_status st;
-  if (pb) {  // the distribution needs the whole input first: one copy in
+  if (pb || is16(kt)) {  // the whole input first (one copy in), then the device sort
     if (cudaMemcpyAsync(dki, hki, n * kb, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         (pairs && cudaMemcpyAsync(dvi, hvi, n * 4, cudaMemcpyHostToDevice, s) != cudaSuccess))
       return BCF_ECUDA;
-    st = run_sort_pb(dko, dvo, dki, dvi, n, kt, o, wsb + wl.sort, wl.sort_bytes, s, pairs);
+    st = sort_any(dko, dvo, dki, dvi, n, kt, o, wsb + wl.sort, wl.sort_bytes, s, pairs);
   } else {
     // copy in on the copy stream, in 8 pieces of whole tiles; each piece's
     // block sort starts as soon as it has landed
@@ -864,14 +994,30 @@ extern "C" {
 
 size_t bcf_workspace_bytes(int op, uint64_t n, uint64_t nseg_or_k, bcf_dtype kt, int has_vals) {
   if (!dtype_ok(kt)) return 0;
+  const bool pairs = has_vals != 0;
+  if (is16(kt)) {  // 16-bit keys: widened copies in and out, then the 32-bit call's workspace
+    const bcf_dtype wk = wide_of(kt);
+    switch (op) {
+      case BCF_OP_SORT:
+      case BCF_OP_MERGE:
+      case BCF_OP_SEGMENTED:
+      case BCF_OP_SORT_PB:
+        return wide16_layout(n, bcf_workspace_bytes(op, n, nseg_or_k, wk, has_vals)).total;
+      case BCF_OP_SORT_HOST: return host_layout(n, kt, pairs, false).total;
+      case BCF_OP_SORT_HOST_PB: return host_layout(n, kt, pairs, true).total;
+      case BCF_OP_SORT_WIDE: return wide_layout(n, kt).total;
+      default: return 0;
+    }
+  }
   const int kb = key_bytes_of(kt);
   switch (op) {
-    case BCF_OP_SORT: return ws_layout(n, 0, kb, has_vals != 0).total;
-    case BCF_OP_MERGE: return ws_layout(n, nseg_or_k, kb, has_vals != 0).total;
-    case BCF_OP_SEGMENTED: return seg_layout(n, nseg_or_k, kb, has_vals != 0).total;
-    case BCF_OP_SORT_PB: return pb_layout(n, kb, has_vals != 0).total;
-    case BCF_OP_SORT_HOST: return host_layout(n, kb, has_vals != 0, false).total;
-    case BCF_OP_SORT_HOST_PB: return host_layout(n, kb, has_vals != 0, true).total;
+    case BCF_OP_SORT: return ws_layout(n, 0, kb, pairs).total;
+    case BCF_OP_MERGE: return ws_layout(n, nseg_or_k, kb, pairs).total;
+    case BCF_OP_SEGMENTED: return seg_layout(n, nseg_or_k, kb, pairs).total;
+    case BCF_OP_SORT_PB: return pb_layout(n, kb, pairs).total;
+    case BCF_OP_SORT_HOST: return host_layout(n, kt, pairs, false).total;
+    case BCF_OP_SORT_HOST_PB: return host_layout(n, kt, pairs, true).total;
+    case BCF_OP_SORT_WIDE: return wide_layout(n, kt).total;
     case BCF_OP_CPS:
       if (kt != BCF_U32 || has_vals || nseg_or_k < 1 || nseg_or_k > kCpsMaxColors) return 0;
       return cps_layout(n, static_cast<uint32_t>(nseg_or_k)).total;
@@ -881,21 +1027,13 @@ size_t bcf_workspace_bytes(int op, uint64_t n, uint64_t nseg_or_k, bcf_dtype kt,
 
 bcf_status bcf_sort_keys(void* keys_out, const void* keys_in, uint64_t n, bcf_dtype kt,
                          const bcf_opts* opts, void* ws, size_t ws_bytes, cudaStream_t stream) {
-  if (opts && opts->algorithm == BCF_ALGO_PIVOT_BUCKETS)
-    return run_sort_pb(keys_out, nullptr, keys_in, nullptr, n, kt, opts, ws, ws_bytes, stream,
-                       false);
-  if (opts && opts->algorithm != BCF_ALGO_MERGE) return BCF_EINVAL;
-  return run_sort(keys_out, nullptr, keys_in, nullptr, n, kt, opts, ws, ws_bytes, stream, false);
+  return sort_any(keys_out, nullptr, keys_in, nullptr, n, kt, opts, ws, ws_bytes, stream, false);
 }
 
 bcf_status bcf_sort_pairs(void* keys_out, uint32_t* vals_out, const void* keys_in,
                           const uint32_t* vals_in, uint64_t n, bcf_dtype kt,
                           const bcf_opts* opts, void* ws, size_t ws_bytes, cudaStream_t stream) {
-  if (opts && opts->algorithm == BCF_ALGO_PIVOT_BUCKETS)
-    return run_sort_pb(keys_out, vals_out, keys_in, vals_in, n, kt, opts, ws, ws_bytes, stream,
-                       true);
-  if (opts && opts->algorithm != BCF_ALGO_MERGE) return BCF_EINVAL;
-  return run_sort(keys_out, vals_out, keys_in, vals_in, n, kt, opts, ws, ws_bytes, stream, true);
+  return sort_any(keys_out, vals_out, keys_in, vals_in, n, kt, opts, ws, ws_bytes, stream, true);
 }
 
 bcf_status bcf_merge_runs(void* keys_out, uint32_t* vals_out, const void* keys_in,
@@ -903,6 +1041,22 @@ bcf_status bcf_merge_runs(void* keys_out, uint32_t* vals_out, const void* keys_i
                           bcf_dtype kt, const bcf_opts* opts, void* ws, size_t ws_bytes,
                           cudaStream_t stream) {
   if ((vals_out == nullptr) != (vals_in == nullptr)) return BCF_EINVAL;
+  if (is16(kt)) {
+    if (!run_offsets_host || k == 0) return BCF_EINVAL;
+    for (uint32_t r = 0; r < k; ++r)
+      if (run_offsets_host[r + 1] < run_offsets_host[r]) return BCF_EINVAL;
+    const uint64_t n = run_offsets_host[k], lo = run_offsets_host[0];
+    const bool pairs = vals_out != nullptr;
+    bcf_status st = check_common(keys_out, vals_out, keys_in, vals_in, n, kt, pairs);
+    if (st != BCF_OK || n == lo) return st;
+    const bcf_dtype wk = wide_of(kt);
+    return via_wide16(keys_out, keys_in, lo, n, kt, ws, ws_bytes,
+                      ws_layout(n, k, 4, pairs).total, stream,
+                      [&](void* k32o, const void* k32i, void* iw, size_t ib) {
+                        return run_merge(k32o, vals_out, k32i, vals_in, run_offsets_host, k, wk,
+                                         opts, iw, ib, stream);
+                      });
+  }
   return run_merge(keys_out, vals_out, keys_in, vals_in, run_offsets_host, k, kt, opts, ws,
                    ws_bytes, stream);
 }
@@ -913,8 +1067,28 @@ bcf_status bcf_segmented_sort(void* keys_out, uint32_t* vals_out, const void* ke
                               const bcf_opts* opts, void* ws, size_t ws_bytes,
                               cudaStream_t stream) {
   if ((vals_out == nullptr) != (vals_in == nullptr)) return BCF_EINVAL;
+  if (is16(kt)) {
+    const bool pairs = vals_out != nullptr;
+    bcf_status st = check_common(keys_out, vals_out, keys_in, vals_in, n_total, kt, pairs);
+    if (st != BCF_OK || n_total == 0 || nseg == 0) return st;
+    const bcf_dtype wk = wide_of(kt);
+    return via_wide16(keys_out, keys_in, 0, n_total, kt, ws, ws_bytes,
+                      seg_layout(n_total, nseg, 4, pairs).total, stream,
+                      [&](void* k32o, const void* k32i, void* iw, size_t ib) {
+                        return run_segmented(k32o, vals_out, k32i, vals_in, seg_offsets_dev, nseg,
+                                             n_total, wk, opts, iw, ib, stream);
+                      });
+  }
   return run_segmented(keys_out, vals_out, keys_in, vals_in, seg_offsets_dev, nseg, n_total, kt,
                        opts, ws, ws_bytes, stream);
+}
+
+bcf_status bcf_sort_pairs_wide(void* keys_out, void* vals_out, const void* keys_in,
+                               const void* vals_in, uint64_t n, uint32_t val_bytes, bcf_dtype kt,
+                               const bcf_opts* opts, void* ws, size_t ws_bytes,
+                               cudaStream_t stream) {
+  return run_sort_wide(keys_out, vals_out, keys_in, vals_in, n, val_bytes, kt, opts, ws, ws_bytes,
+                       stream);
 }
 
 bcf_status bcf_sort_keys_host(void* keys_out_host, const void* keys_in_host, uint64_t n,
@@ -965,6 +1139,7 @@ bcf_status bcf_last_device_error(cudaStream_t stream) {
 
 bcf_status bcf_sort_plan(uint64_t n, bcf_dtype kt, int has_vals, bcf_plan* out) {
   if (!out || !dtype_ok(kt)) return BCF_EINVAL;
+  if (is16(kt)) kt = wide_of(kt);  // the passes run on the widened keys
   const int kb = key_bytes_of(kt);
   const Plan p = make_plan(n, kb, has_vals != 0);
   out->block_tile = p.T;

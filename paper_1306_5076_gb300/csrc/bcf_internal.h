@@ -168,4 +168,13 @@ struct PbArgs {
 };
 cudaError_t launch_pb(int step, int key_bytes, bool pairs, const PbArgs& a, cudaStream_t s);
 
+// Conversions (bcf_convert.cu): 16-bit keys through the 32-bit sort, and wide
+// payloads gathered by sorted row index.
+cudaError_t launch_widen16(uint32_t* out, const uint16_t* in, uint64_t n, bool sign,
+                           cudaStream_t s);
+cudaError_t launch_narrow16(uint16_t* out, const uint32_t* in, uint64_t n, cudaStream_t s);
+cudaError_t launch_iota(uint32_t* v, uint64_t n, cudaStream_t s);
+cudaError_t launch_gather(void* out, const void* in, const uint32_t* idx, uint64_t n,
+                          uint32_t row_bytes, cudaStream_t s);
+
 }  // namespace bcf

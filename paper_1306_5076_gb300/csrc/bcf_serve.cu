@@ -110,6 +110,11 @@ __global__ void batch_copy_kernel(const CopyDesc* d, void* batch_k, uint32_t* ba
     const uint32_t* src = GATHER ? static_cast<const uint32_t*>(c.kin) : bk;
     uint32_t* dst = GATHER ? bk : static_cast<uint32_t*>(c.kout);
     for (uint64_t i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+  } else if (kb == 2) {
+    uint16_t* bk = static_cast<uint16_t*>(batch_k) + c.off;
+    const uint16_t* src = GATHER ? static_cast<const uint16_t*>(c.kin) : bk;
+    uint16_t* dst = GATHER ? bk : static_cast<uint16_t*>(c.kout);
+    for (uint64_t i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
   } else {
     uint64_t* bk = static_cast<uint64_t*>(batch_k) + c.off;
     const uint64_t* src = GATHER ? static_cast<const uint64_t*>(c.kin) : bk;
@@ -170,6 +175,7 @@ namespace {
 bcf_status cuda_ok(cudaError_t e) { return e == cudaSuccess ? BCF_OK : BCF_ECUDA; }
 
 int key_bytes(bcf_dtype kt) {
+  if (kt == BCF_U16 || kt == BCF_I16) return 2;
   return (kt == BCF_U64 || kt == BCF_I64 || kt == BCF_F64) ? 8 : 4;
 }
 
@@ -434,7 +440,7 @@ double bcf_server_now(const bcf_server* s) { return s ? now_s(s->t0) : 0.0; }
 bcf_status bcf_server_submit(bcf_server* s, const bcf_request* r) {
   if (!s || !r) return BCF_EINVAL;
   if (r->op != BCF_OP_SORT && r->op != BCF_OP_MERGE) return BCF_EINVAL;
-  if (r->kt < BCF_U32 || r->kt > BCF_F64) return BCF_EINVAL;
+  if (r->kt < BCF_U32 || r->kt > BCF_I16) return BCF_EINVAL;
   if ((r->vals_in == nullptr) != (r->vals_out == nullptr)) return BCF_EINVAL;
   Req q;
   q.r = *r;

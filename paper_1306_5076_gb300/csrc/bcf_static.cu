@@ -63,6 +63,8 @@ extern "C" bcf_status bcf_sort_keys_static(void* keys_out, const void* keys_in, 
                                            bcf_dtype kt, const bcf_opts* opts,
                                            cudaStream_t stream) {
   if (n > kMaxKeys) return BCF_EUNSUPPORTED;
+  // 16-bit keys need widened copies the static array has no room for
+  if (kt == BCF_U16 || kt == BCF_I16) return BCF_EUNSUPPORTED;
   // the static array is sized for the merge path: the algorithm choice is ignored
   bcf_opts o{};
   if (opts) o = *opts;

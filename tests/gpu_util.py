@@ -3,15 +3,14 @@ from __future__ import annotations
 
 import numpy as np
 
-KT = {"u32": 0, "u64": 1, "f32": 2, "i32": 3, "i64": 4, "f64": 5}
+KT = {"u32": 0, "u64": 1, "f32": 2, "i32": 3, "i64": 4, "f64": 5, "u16": 6, "i16": 7}
 
 
 def to_dev(a: np.ndarray, dev="cuda:0"):
     import torch
 
-    if a.dtype.itemsize == 8:
-        return torch.from_numpy(np.ascontiguousarray(a).view(np.int64)).to(dev)
-    return torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).to(dev)
+    view = {2: np.int16, 4: np.int32, 8: np.int64}[a.dtype.itemsize]
+    return torch.from_numpy(np.ascontiguousarray(a).view(view)).to(dev)
 
 
 def from_dev(t, like: np.dtype) -> np.ndarray:
@@ -21,9 +20,10 @@ def from_dev(t, like: np.dtype) -> np.ndarray:
 
 def kt_of(a: np.ndarray) -> int:
     return {np.dtype(np.uint32): 0, np.dtype(np.uint64): 1, np.dtype(np.float32): 2,
-            np.dtype(np.int32): 3, np.dtype(np.int64): 4, np.dtype(np.float64): 5}[a.dtype]
+            np.dtype(np.int32): 3, np.dtype(np.int64): 4, np.dtype(np.float64): 5,
+            np.dtype(np.uint16): 6, np.dtype(np.int16): 7}[a.dtype]
 
 
 def bits(a: np.ndarray) -> np.ndarray:
     """Bit patterns as unsigned integers of the key width (exact comparison)."""
-    return a.view(np.uint32 if a.dtype.itemsize == 4 else np.uint64)
+    return a.view({2: np.uint16, 4: np.uint32, 8: np.uint64}[a.dtype.itemsize])

@@ -77,7 +77,7 @@ def as_bits(keys: np.ndarray) -> list[int]:
 
 def raw_bits(keys: np.ndarray) -> np.ndarray:
     """The keys' bit patterns as an unsigned array of the same width."""
-    return keys.view(np.uint32 if keys.dtype.itemsize == 4 else np.uint64)
+    return keys.view({2: np.uint16, 4: np.uint32, 8: np.uint64}[keys.dtype.itemsize])
 
 
 def stable_selection_sort(items, lt):

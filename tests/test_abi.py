@@ -67,7 +67,12 @@ def test_workspace_bytes_scale_with_input(lib):
     # the signed and double key types take the space of their width
     for kt, same in ((BCF_I32, keys), (BCF_I64, wide), (BCF_F64, wide)):
         assert lib.bcf_workspace_bytes(BCF_OP_SORT, n, 0, kt, 0) == same
-    assert lib.bcf_workspace_bytes(BCF_OP_SORT, n, 0, 6, 0) == 0
+    assert lib.bcf_workspace_bytes(BCF_OP_SORT, n, 0, 8, 0) == 0
+    # 16-bit keys: widened copies in and out (4 bytes each) on top of the 32-bit sort's
+    for kt16 in (6, 7):
+        w16 = lib.bcf_workspace_bytes(BCF_OP_SORT, n, 0, kt16, 0)
+        assert w16 >= keys + 8 * n
+        assert lib.bcf_workspace_bytes(BCF_OP_SORT, n, 0, kt16, 1) >= pairs + 8 * n
     # colored prefix sums: one look-back word per (tile, color); u32 values only
     from paper_1306_5076_gb300 import BCF_OP_CPS
     cps = lib.bcf_workspace_bytes(BCF_OP_CPS, n, 16, BCF_U32, 0)
@@ -84,7 +89,7 @@ def test_workspace_bytes_scale_with_input(lib):
         assert pb >= lib.bcf_workspace_bytes(BCF_OP_SORT, 10, 0, kt, hv)
     assert lib.bcf_workspace_bytes(BCF_OP_MERGE, n, 256, BCF_U32, 0) >= keys
     assert lib.bcf_workspace_bytes(9, n, 0, BCF_U32, 0) == 0
-    assert lib.bcf_workspace_bytes(BCF_OP_SORT, n, 0, 7, 0) == 0
+    assert lib.bcf_workspace_bytes(BCF_OP_SORT, n, 0, 9, 0) == 0
 
 
 @pytest.mark.parametrize("n", [0, 1, 4095, 4096, 8192, 8193, 1 << 20, (1 << 28) + 1])
@@ -92,7 +97,7 @@ def test_plan_pass_count_is_lemma_2(lib, n):
     """Lemma 2: one base-case pass plus ceil(log2(n / T)) merge passes."""
     from paper_1306_5076_gb300 import _native
 
-    for kt in range(6):
+    for kt in range(8):
         for has_vals in (0, 1):
             p = _native.BcfPlan()
             assert lib.bcf_sort_plan(n, kt, has_vals, ctypes.byref(p)) == 0
@@ -112,7 +117,7 @@ def test_host_side_argument_errors_return_before_launch(lib):
     EINVAL = 1
     # bad dtype (one past the last key type, and a negative code)
     assert lib.bcf_sort_keys(None, None, 0, 9, opts, None, 0, None) == EINVAL
-    assert lib.bcf_sort_keys(None, None, 0, 6, opts, None, 0, None) == EINVAL
+    assert lib.bcf_sort_keys(None, None, 0, 8, opts, None, 0, None) == EINVAL
     assert lib.bcf_sort_keys(None, None, 0, -1, opts, None, 0, None) == EINVAL
     # n == 0 is a no-op
     assert lib.bcf_sort_keys(None, None, 0, 0, opts, None, 0, None) == 0
@@ -124,6 +129,11 @@ def test_host_side_argument_errors_return_before_launch(lib):
     # partial overlap of output and input
     assert lib.bcf_sort_keys(ctypes.c_void_p(0x10000), ctypes.c_void_p(0x10010), 100, 0, opts,
                              None, 0, None) == EINVAL
+    # wide payloads: rows must be a positive multiple of 4 bytes; null pointers
+    assert lib.bcf_sort_pairs_wide(None, None, None, None, 10, 6, 0, opts, None, 0, None) == EINVAL
+    assert lib.bcf_sort_pairs_wide(None, None, None, None, 10, 8, 0, opts, None, 0, None) == EINVAL
+    assert lib.bcf_sort_pairs_wide(None, None, None, None, 0, 8, 0, opts, None, 0, None) == 0
+    assert lib.bcf_workspace_bytes(7, 1 << 20, 0, 0, 1) >= 8 * (1 << 20)
     # host-buffer sorts: null host pointers, short workspace
     assert lib.bcf_sort_keys_host(None, None, 10, 0, opts, None, 0, None) == EINVAL
     assert lib.bcf_sort_keys_host(None, None, 0, 0, opts, None, 0, None) == 0

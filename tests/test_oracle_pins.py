@@ -107,7 +107,7 @@ def test_order_rank_helper_matches_ieee(width):
     assert np.all(r[1:] > r[:-1])
 
 
-@pytest.mark.parametrize("dtype,width", [(np.int32, 32), (np.int64, 64)])
+@pytest.mark.parametrize("dtype,width", [(np.int16, 16), (np.int32, 32), (np.int64, 64)])
 def test_oracle_signed_order_matches_python_integers(oracle_lib, dtype, width):
     """Two's-complement order: the oracle's comparison of raw bit patterns
     agrees with Python's ``<`` on the values the patterns encode."""
@@ -146,6 +146,8 @@ ALPHABETS = {
     # a positive value, -1 and the most negative value: unsigned order differs
     "i32": [5, -1, -(2**31)],
     "i64": [5, -1, -(2**63)],
+    "u16": [7, 3, 0xFFFF],
+    "i16": [5, -1, -(2**15)],
     "f64": [0x8000000000000000, 0x0000000000000000, 0x7FF8000000000000],
 }
 
@@ -164,7 +166,7 @@ def check_ternary_sequences(lib, dtype, descending, max_n=7):
             assert [int(v) for v in vo] == [v for _, v in exp]
 
 
-@pytest.mark.parametrize("dtype", ["u32", "u64", "f32", "i32", "i64", "f64"])
+@pytest.mark.parametrize("dtype", list(workloads.DTYPES))
 @pytest.mark.parametrize("descending", [False, True])
 def test_all_ternary_sequences_stable(oracle_lib, dtype, descending):
     check_ternary_sequences(oracle_lib, dtype, descending, max_n=7 if dtype == "u32" else 6)
@@ -177,7 +179,7 @@ def random_bits(r, dtype, n, alphabet):
     return workloads.keys("uniform", dtype, n, seed=int(r.integers(1 << 30)))
 
 
-@pytest.mark.parametrize("dtype", ["u32", "u64", "f32", "i32", "i64", "f64"])
+@pytest.mark.parametrize("dtype", list(workloads.DTYPES))
 def test_insertion_sort_random(oracle_lib, dtype):
     r = workloads.rng(13)
     for case in range(6):
@@ -194,7 +196,7 @@ def test_insertion_sort_random(oracle_lib, dtype):
 
 # ---------------------------------------------------------------- library special cases
 
-@pytest.mark.parametrize("dtype", ["u32", "u64", "i32", "i64"])
+@pytest.mark.parametrize("dtype", ["u32", "u64", "i32", "i64", "u16", "i16"])
 def test_matches_numpy_stable_argsort_integers(oracle_lib, dtype):
     r = workloads.rng(14)
     for n, alpha in [(100_000, None), (50_000, 97)]:
@@ -369,6 +371,10 @@ MUTANTS = {
     "i32_unsigned": (r"return \(int32_t\)\(uint32_t\)a < \(int32_t\)\(uint32_t\)b;",
                      "return (uint32_t)a < (uint32_t)b;"),
     "i64_unsigned": (r"return \(int64_t\)a < \(int64_t\)b;", "return a < b;"),
+    "i16_unsigned": (r"return \(int16_t\)\(uint16_t\)a < \(int16_t\)\(uint16_t\)b;",
+                     "return (uint16_t)a < (uint16_t)b;"),
+    # 16-bit keys read as 32-bit ones
+    "u16_as_32bit": (r"    case 2:  return \(\(const uint16_t\*\)c->keys\)\[i\];\n", ""),
     # 64-bit floats read through the 32-bit key path
     "f64_as_32bit": (r"dtype == ORACLE_I64 \|\| dtype == ORACLE_F64\) \? 8 : 4",
                      "dtype == ORACLE_I64) ? 8 : 4"),
@@ -385,6 +391,8 @@ def _pins_fail(lib, mutant):
         lambda: check_all_permutations(lib, 6),
         lambda: check_ternary_sequences(lib, "i32", False, 3),
         lambda: check_ternary_sequences(lib, "i64", False, 3),
+        lambda: check_ternary_sequences(lib, "i16", False, 3),
+        lambda: check_ternary_sequences(lib, "u16", False, 3),
         lambda: check_ternary_sequences(lib, "u32", False, 5),
         lambda: check_ternary_sequences(lib, "f32", True, 4),
         lambda: check_merge_runs(lib, "u32", False),

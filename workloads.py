@@ -20,7 +20,7 @@ import math
 import numpy as np
 
 DTYPES = {"u32": np.uint32, "u64": np.uint64, "f32": np.float32, "i32": np.int32,
-          "i64": np.int64, "f64": np.float64}
+          "i64": np.int64, "f64": np.float64, "u16": np.uint16, "i16": np.int16}
 DISTRIBUTIONS = ("uniform", "gaussian", "sorted", "reverse", "distinct16", "zipf")
 PAPER_SETS = ("random1e6", "distinct", "zero_one", "dup2", "dup16", "dup2250")
 
@@ -42,6 +42,9 @@ def large_sort_seed(dist: str, dtype: str, n: int) -> int:
 
 def _uniform_bits(g, n, dtype):
     """Uniform random bit patterns of the key width, viewed as ``dtype``."""
+    if DTYPES[dtype]().itemsize == 2:
+        u = g.integers(0, 2**16, size=n, dtype=np.uint64).astype(np.uint16)
+        return u.view(DTYPES[dtype])
     if DTYPES[dtype]().itemsize == 8:
         u = g.integers(0, 2**64, size=n, dtype=np.uint64, endpoint=False)
         return u.view(DTYPES[dtype])
@@ -52,9 +55,12 @@ def _uniform_bits(g, n, dtype):
 def _from_u32(u: np.ndarray, dtype: str) -> np.ndarray:
     """u32 workload values carried to ``dtype`` by a monotone map: u64 widens,
     f32 rounds to float32, i32 / i64 / f64 subtract 2^31 (so half the values are
-    negative)."""
+    negative), u16 keeps the top 16 bits and i16 those minus 2^15."""
     if dtype == "u32":
         return u
+    if dtype in ("u16", "i16"):
+        h = (u >> np.uint32(16)).astype(np.uint16)
+        return h if dtype == "u16" else (h ^ np.uint16(0x8000)).view(np.int16)
     if dtype == "u64":
         return u.astype(np.uint64)
     if dtype == "f32":
@@ -118,11 +124,14 @@ def keys(dist: str, dtype: str, n: int, seed: int | None = None) -> np.ndarray:
                 widened; f32 = float32 of the same values (many ties); i32 /
                 i64 / f64 = the same values minus 2^31.
     sorted    : non-decreasing by construction (exponential spacings).
+    (u16 / i16 carry the u32 values over by their top 16 bits, the gaussian
+    and sorted laws included.)
     reverse   : ``sorted`` read backwards.
     distinct16: 16 values drawn from the uniform law, each element picks one.
     zipf      : rank r ~ Zipf(1.1) over 2^20 symbols, key = (r-1)*golden mod
                 2^64 (u64; its bits for i64) or mod 2^32 (u32; f32 = float32
-                of it; i32 = its bits; f64 = its value minus 2^31).
+                of it; i32 = its bits; f64 = its value minus 2^31; u16 / i16 =
+                its low 16 bits).
     """
     if seed is None:
         seed = large_sort_seed(dist, dtype, n)
@@ -143,6 +152,8 @@ def keys(dist: str, dtype: str, n: int, seed: int | None = None) -> np.ndarray:
         if dtype in ("u64", "i64"):
             return (r * np.uint64(_GOLDEN64)).view(DTYPES[dtype])  # wraps mod 2^64
         u = ((r * np.uint64(_GOLDEN32)) & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+        if dtype in ("u16", "i16"):  # the low 16 bits: the symbol's identity mod 2^16
+            return (u & np.uint32(0xFFFF)).astype(np.uint16).view(DTYPES[dtype])
         return u.view(np.int32) if dtype == "i32" else _from_u32(u, dtype)
     raise ValueError(f"unknown distribution {dist!r}")
 
