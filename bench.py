@@ -301,14 +301,14 @@ def key_types_bench(torch, dev, bcf, peak, log2n=LOG2N):
     stream = torch.cuda.current_stream(dev)
     out = {}
     codes = {"u32": bcf.BCF_U32, "i32": bcf.BCF_I32, "f32": bcf.BCF_F32, "u64": bcf.BCF_U64,
-             "i64": bcf.BCF_I64, "f64": bcf.BCF_F64}
+             "i64": bcf.BCF_I64, "f64": bcf.BCF_F64, "u16": bcf.BCF_U16, "i16": bcf.BCF_I16}
     for name, kt in codes.items():
         for pairs in (False, True):
             if pairs and name not in ("u32", "u64"):
                 continue
             keys = workloads.keys("uniform", name, n)
             kb = keys.dtype.itemsize
-            kd = torch.from_numpy(keys.view(np.int32 if kb == 4 else np.int64)).to(dev)
+            kd = torch.from_numpy(keys.view({2: np.int16, 4: np.int32, 8: np.int64}[kb])).to(dev)
             ko = torch.empty_like(kd)
             vd = torch.arange(n, dtype=torch.int32, device=dev) if pairs else None
             vo = torch.empty_like(vd) if pairs else None
@@ -337,6 +337,20 @@ def key_types_bench(torch, dev, bcf, peak, log2n=LOG2N):
                 "merge_passes": plan["merge_passes"]}
             del kd, ko, vd, vo, ws
             torch.cuda.empty_cache()
+    # u32 keys with 64-bit payloads (bcf_sort_pairs_wide: pairs sort + row gather)
+    keys = workloads.keys("uniform", "u32", n)
+    kd = torch.from_numpy(keys.view(np.int32)).to(dev)
+    ko = torch.empty_like(kd)
+    vd = torch.arange(n, dtype=torch.int64, device=dev)
+    vo = torch.empty_like(vd)
+    ws = torch.empty(bcf.bcf_workspace_bytes(bcf._native.BCF_OP_SORT_WIDE, n, 0, bcf.BCF_U32, 1),
+                     dtype=torch.uint8, device=dev)
+    ms = timed_ms(torch, stream, lambda: bcf.bcf_sort_pairs_wide(
+        ko, vo, kd, vd, kt=bcf.BCF_U32, ws=ws, stream=stream), warmup=2, reps=5)
+    out["u32+u64"] = {"ms": ms, "keys_per_s": n / (ms * 1e-3),
+                      "how": "pairs sort with u32 row indices, then a gather of the 8-byte rows"}
+    del kd, ko, vd, vo, ws
+    torch.cuda.empty_cache()
     return {"n": n, "distribution": "uniform", "results": out}
 
 
