@@ -50,29 +50,36 @@ __global__ void pb_sample_kernel(const PbArgs a) {
 
 // One CTA of kPbThreads threads: candidate j < P - 1 is the sorted sample at
 // rank (j + 1) * ns / P; a candidate equal to the previous one is dropped.
+// The candidates are taken kPbThreads at a time, compacted in order.
 template <typename K>
 __global__ void __launch_bounds__(kPbThreads) pb_splitter_kernel(const PbArgs a) {
   __shared__ uint32_t warp_sums[kPbThreads / 32];
-  const uint32_t j = threadIdx.x, lane = j & 31u, w = j >> 5;
+  const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
   const K* S = static_cast<const K*>(a.sorted_samples);
-  bool keep = false;
-  K cand = 0;
-  if (j < kPbSplitters) {
-    cand = S[((j + 1) * a.ns) / kPbP];
-    keep = j == 0 || cand != S[(j * a.ns) / kPbP];
+  uint32_t carry = 0;
+  for (uint32_t j0 = 0; j0 < kPbSplitters; j0 += kPbThreads) {
+    const uint32_t j = j0 + threadIdx.x;
+    bool keep = false;
+    K cand = 0;
+    if (j < kPbSplitters) {
+      cand = S[((j + 1) * a.ns) / kPbP];
+      keep = j == 0 || cand != S[(j * a.ns) / kPbP];
+    }
+    // exclusive block scan of the keep flags
+    const uint32_t ballot = __ballot_sync(0xFFFFFFFFu, keep);
+    const uint32_t before = __popc(ballot & ((1u << lane) - 1u));
+    if (lane == 0) warp_sums[w] = __popc(ballot);
+    __syncthreads();
+    uint32_t base = carry, total = 0;
+    for (uint32_t q = 0; q < kPbThreads / 32; ++q) {
+      if (q < w) base += warp_sums[q];
+      total += warp_sums[q];
+    }
+    if (keep) static_cast<K*>(a.splitters)[base + before] = cand;
+    carry += total;
+    __syncthreads();  // warp_sums is reused by the next chunk
   }
-  // exclusive block scan of the keep flags
-  const uint32_t ballot = __ballot_sync(0xFFFFFFFFu, keep);
-  const uint32_t before = __popc(ballot & ((1u << lane) - 1u));
-  if (lane == 0) warp_sums[w] = __popc(ballot);
-  __syncthreads();
-  uint32_t base = 0, total = 0;
-  for (uint32_t q = 0; q < kPbThreads / 32; ++q) {
-    if (q < w) base += warp_sums[q];
-    total += warp_sums[q];
-  }
-  if (keep) static_cast<K*>(a.splitters)[base + before] = cand;
-  if (j == 0) *a.nsplit = total;
+  if (threadIdx.x == 0) *a.nsplit = carry;
 }
 
 template <typename K>

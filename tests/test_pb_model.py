@@ -18,7 +18,7 @@ import pytest
 import workloads
 
 STRIDE = 256       # sample stride
-P = 256            # P - 1 splitters
+P = 256            # P - 1 splitters (the library default)
 B = 2 * (P - 1) + 1  # open, equal, open, ..., open
 
 
