@@ -237,31 +237,43 @@ def serving_bench(torch, dev, seconds, rate=2000.0, seed=5000):
     kout = torch.empty(out_keys, dtype=torch.int32, device=dev)
     vout = torch.empty(out_keys, dtype=torch.int32, device=dev)
     arena = torch.empty(40 << 30, dtype=torch.uint8, device=dev)
-    res = {}
-    for name, mode in (("served", serve.BCF_SERVE_BATCHED), ("plain", serve.BCF_SERVE_PLAIN)):
-        torch.cuda.synchronize()
+    # untimed warm-up trace: every size band, with and without payloads, so
+    # that no kernel is loaded or launched for the first time inside the trace
+    w_sizes = np.array([1 << b for b in range(8, 25, 2)] * 2)
+    w_pairs = np.repeat([False, True], w_sizes.size // 2)
+    w_t = np.arange(w_sizes.size) * 2e-3
+
+    def replay(mode, ts, szs, prs):
         srv = serve.Server(arena, mode=mode, streams=4, small_max=1 << 16)
         outs = serve.Arena(out_keys * 4)
         held = {}
 
         def make(i):
-            n = int(sizes[i])
+            n = int(szs[i])
             off = outs.alloc(n * 4)
             if off is None:
                 return None  # output pool full: the request waits (its latency counts)
             held[i] = off
             src = ((i * 2654435761) % (pool - n)) & ~3
             kw = dict(kt=0, n=n, keys_in=kin[src:].data_ptr(), keys_out=kout.data_ptr() + off)
-            if pairs[i]:
+            if prs[i]:
                 kw.update(vals_in=vin[src:].data_ptr(), vals_out=vout.data_ptr() + off)
             return kw
 
         def release(i):
-            outs.free(held.pop(i), int(sizes[i]) * 4)
+            outs.free(held.pop(i), int(szs[i]) * 4)
 
-        r = serve.replay(srv, list(t), make, release)
+        r = serve.replay(srv, list(ts), make, release)
         srv.close()
         outs.close()
+        return r
+
+    res = {}
+    for name, mode in (("served", serve.BCF_SERVE_BATCHED), ("plain", serve.BCF_SERVE_PLAIN)):
+        torch.cuda.synchronize()
+        replay(mode, w_t, w_sizes, w_pairs)
+        torch.cuda.synchronize()
+        r = replay(mode, t, sizes, pairs)
         keys = float(sizes.sum())
         res[name] = {"p50_ms": r["p50_s"] * 1e3, "p99_ms": r["p99_s"] * 1e3,
                      "mean_ms": r["mean_s"] * 1e3, "keys_per_s": keys / r["span_s"],
@@ -511,7 +523,8 @@ def profile_case(args):
     """A small case of one path, for ncu captures (inputs larger than L2, a
     few launches): 'cps' = colored prefix sums of 2^26 elements, 16 colors,
     both layouts, two launches each; 'pb' = pivot-bucket sort of 2^26
-    16-distinct u32 keys, twice."""
+    16-distinct u32 keys, twice; 'seg' = segmented sort of 5,000 segments
+    with sizes log-uniform over [1, 2^18] (about 1.05e8 u32 keys), twice."""
     import numpy as np
     import torch
 

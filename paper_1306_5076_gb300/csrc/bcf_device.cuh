@@ -213,6 +213,7 @@ struct Frag {
   K k[E];
   uint32_t ix[PAIRS ? E : 1];
   uint32_t v[PAIRS ? E : 1];
+  uint32_t one;  // the multiplier of the FMA-pipe maximum (see ce()); set by kernels that use it
 
   __device__ __forceinline__ void put(uint32_t* sm, uint32_t plane, int e, uint32_t a) const {
     sm[a] = static_cast<uint32_t>(k[e]);
@@ -246,10 +247,28 @@ __device__ __forceinline__ bool after(K kx, uint32_t ix, K ky, uint32_t iy) {
   }
 }
 
+// A 1 that the compiler cannot fold away (it could be written from the host),
+// read once per thread into Frag::one.
+static __device__ uint32_t g_unit_multiplier = 1;
+
 // Compare-exchange registers a < b: ascending puts the smaller element in a.
+// fma_max (32-bit keys without payloads only): the maximum is computed as
+// x * one + y - min(x, y) with two integer multiply-adds, which run on the FMA
+// pipe, instead of a second min/max on the ALU pipe.  Exact in modular
+// arithmetic.  The block sort's networks keep the ALU pipe saturated, so moving
+// part of the work over shortens them (measured: the BLK-layout stages).
 template <typename K, bool PAIRS, int E>
-__device__ __forceinline__ void ce(Frag<K, PAIRS, E>& f, int a, int b, bool desc) {
-  if constexpr (!PAIRS) {
+__device__ __forceinline__ void ce(Frag<K, PAIRS, E>& f, int a, int b, bool desc,
+                                   bool fma_max = false) {
+  if (!PAIRS && sizeof(K) == 4 && fma_max) {
+    const uint32_t x = static_cast<uint32_t>(f.k[a]), y = static_cast<uint32_t>(f.k[b]);
+    const uint32_t lo = x < y ? x : y;
+    uint32_t hi;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(hi) : "r"(x), "r"(f.one), "r"(y));
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(hi) : "r"(lo), "r"(0u - f.one), "r"(hi));
+    f.k[a] = static_cast<K>(desc ? hi : lo);
+    f.k[b] = static_cast<K>(desc ? lo : hi);
+  } else if constexpr (!PAIRS) {
     const K x = f.k[a], y = f.k[b];
     const K lo = x < y ? x : y, hi = x < y ? y : x;
     f.k[a] = desc ? hi : lo;
@@ -392,8 +411,8 @@ __device__ __forceinline__ void relayout(Frag<K, PAIRS, E>& f, uint32_t* sm) {
 }
 
 // Ascending half-cleaner stages on k bits HI down to LO, all inside layout
-// L's register window.
-template <int L, int HI, int LO, int NT, typename K, bool PAIRS, int E>
+// L's register window (FMA: the compare-exchanges take the FMA-pipe maximum).
+template <int L, int HI, int LO, int NT, bool FMA = false, typename K, bool PAIRS, int E>
 __device__ __forceinline__ void stages(Frag<K, PAIRS, E>& f) {
   using G = Geo<E, NT>;
 #pragma unroll
@@ -401,7 +420,7 @@ __device__ __forceinline__ void stages(Frag<K, PAIRS, E>& f) {
     const int q = b - G::template win<L>();
 #pragma unroll
     for (int e = 0; e < E; ++e)
-      if (!(e & (1 << q))) ce(f, e, e | (1 << q), false);
+      if (!(e & (1 << q))) ce(f, e, e | (1 << q), false, FMA);
   }
 }
 
@@ -409,7 +428,8 @@ __device__ __forceinline__ void stages(Frag<K, PAIRS, E>& f) {
 // ascending result in BLK layout.  Stages on bits t-1 .. 0 in STR, MID, BLK.
 // Both layout changes reuse one buffer (a second buffer would save two
 // barriers but halves the CTAs per SM, which was measured slower).
-template <int NT, typename K, bool PAIRS, int E>
+// FMA_BLK: the BLK stages take the FMA-pipe maximum (Frag::one must be set).
+template <int NT, bool FMA_BLK = false, typename K, bool PAIRS, int E>
 __device__ __forceinline__ void bitonic_merge_str(Frag<K, PAIRS, E>& f, uint32_t* sm) {
   using G = Geo<E, NT>;
   constexpr int r = G::r, t = G::t;
@@ -421,13 +441,13 @@ __device__ __forceinline__ void bitonic_merge_str(Frag<K, PAIRS, E>& f, uint32_t
   } else {
     relayout<kSTR, kBLK, 0, NT>(f, sm);
   }
-  stages<kBLK, r - 1, 0, NT>(f);
+  stages<kBLK, r - 1, 0, NT, FMA_BLK>(f);
 }
 
 // One level J of the bitonic sort (r < J <= t): the tile's blocks of 2^(J-1)
 // are ascending; merge pairs of them into ascending blocks of 2^J.  Enters and
 // leaves in BLK layout.
-template <int J, int NT, typename K, bool PAIRS, int E>
+template <int J, int NT, bool FMA_BLK, typename K, bool PAIRS, int E>
 __device__ __forceinline__ void sort_level(Frag<K, PAIRS, E>& f, uint32_t* sm) {
   using G = Geo<E, NT>;
   constexpr int r = G::r, t = G::t, top = J - 1;
@@ -446,27 +466,29 @@ __device__ __forceinline__ void sort_level(Frag<K, PAIRS, E>& f, uint32_t* sm) {
     stages<kMID, top, r, NT>(f);
     relayout<kMID, kBLK, 0, NT>(f, sm);
   }
-  stages<kBLK, r - 1, 0, NT>(f);
+  stages<kBLK, r - 1, 0, NT, FMA_BLK>(f);
 }
 
-template <int J, int NT, typename K, bool PAIRS, int E, bool DONE = (J > ilog2(E * NT))>
+template <int J, int NT, bool FMA_BLK, typename K, bool PAIRS, int E,
+          bool DONE = (J > ilog2(E * NT))>
 struct SortLevels {
   __device__ static __forceinline__ void run(Frag<K, PAIRS, E>& f, uint32_t* sm) {
-    sort_level<J, NT>(f, sm);
-    SortLevels<J + 1, NT, K, PAIRS, E>::run(f, sm);
+    sort_level<J, NT, FMA_BLK>(f, sm);
+    SortLevels<J + 1, NT, FMA_BLK, K, PAIRS, E>::run(f, sm);
   }
 };
-template <int J, int NT, typename K, bool PAIRS, int E>
-struct SortLevels<J, NT, K, PAIRS, E, true> {
+template <int J, int NT, bool FMA_BLK, typename K, bool PAIRS, int E>
+struct SortLevels<J, NT, FMA_BLK, K, PAIRS, E, true> {
   __device__ static __forceinline__ void run(Frag<K, PAIRS, E>&, uint32_t*) {}
 };
 
 // Sort of the whole CTA tile: each thread's registers with Batcher's network
 // (levels 1..r), then levels r+1..t; ascending result in BLK layout.
-template <int NT, typename K, bool PAIRS, int E>
+// FMA_BLK: the BLK stages take the FMA-pipe maximum (Frag::one must be set).
+template <int NT, bool FMA_BLK = false, typename K, bool PAIRS, int E>
 __device__ __forceinline__ void block_sort_tile(Frag<K, PAIRS, E>& f, uint32_t* sm) {
   thread_sort(f, false);
-  SortLevels<ilog2(E) + 1, NT, K, PAIRS, E>::run(f, sm);
+  SortLevels<ilog2(E) + 1, NT, FMA_BLK, K, PAIRS, E>::run(f, sm);
 }
 
 }  // namespace bcf

@@ -323,7 +323,8 @@ __global__ void __launch_bounds__(NT) merge_kernel(const MergeArgs a,
     }
   }
 
-  bitonic_merge_str<NT>(f, reinterpret_cast<uint32_t*>(body));
+  f.one = g_unit_multiplier;  // FMA-pipe maxima in the BLK stages (keys-only 32-bit)
+  bitonic_merge_str<NT, true>(f, reinterpret_cast<uint32_t*>(body));
   if constexpr (!IRREG && !MAP) {
     // samples of the output run for the next pass's merge-path search
     if (a.samples_out && ((p.out0 + tid * E) % kSampleStride) == 0 && tid * E < p.d1 - p.d0)
