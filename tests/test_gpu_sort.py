@@ -250,3 +250,64 @@ def test_outputs_16_but_not_32_byte_aligned(bcf, dtype, n):
     # nothing written outside the output slices
     assert not kout[:per16].any() and not kout[per16 + n:].any()
     assert not vout[:4].any() and not vout[4 + n:].any()
+
+
+def test_more_than_2p32_keys_closed_form(bcf):
+    """Maximum sizes: n = 2^32 + 2^20 + 37 keys, past every 32-bit index
+    (tiles, merge items, samples, run offsets).  Key i is (i * C) mod 2^32 for
+    an odd C, a bijection on the first 2^32 positions, so the multiset is every
+    u32 value once plus the values D of positions 2^32 .. n-1 (those of
+    i - 2^32) once more.  The sorted output is then known in closed form: value
+    v fills positions [v + #(D < v), v + #(D <= v)], checked at every position.
+    Payload i mod 2^32 must come out as (key * C^-1) mod 2^32 (both copies of a
+    value carry the same payload)."""
+    need = 100 << 30
+    if torch.cuda.get_device_properties(0).total_memory < need + (8 << 30):
+        pytest.skip("needs about 100 GB of device memory")
+    C = 0x9E3779B1
+    Cinv = pow(C, -1, 1 << 32)
+    n = (1 << 32) + (1 << 20) + 37
+    r = n - (1 << 32)
+    chunk = 1 << 27
+
+    def u32_as_i32(x):
+        return torch.where(x >= (1 << 31), x - (1 << 32), x).to(torch.int32)
+
+    kd = torch.empty(n, dtype=torch.int32, device="cuda")
+    for c0 in range(0, n, chunk):
+        i = torch.arange(c0, min(n, c0 + chunk), dtype=torch.int64, device="cuda")
+        kd[c0:c0 + i.numel()] = u32_as_i32((i * C) & 0xFFFFFFFF)
+    D = torch.sort((torch.arange(r, dtype=torch.int64, device="cuda") * C) & 0xFFFFFFFF).values
+
+    def check_keys(ko):
+        for c0 in range(0, n, chunk):
+            c1 = min(n, c0 + chunk)
+            v = ko[c0:c1].to(torch.int64) & 0xFFFFFFFF
+            p = torch.arange(c0, c1, dtype=torch.int64, device="cuda")
+            lt = torch.searchsorted(D, v, right=False)
+            le = torch.searchsorted(D, v, right=True)
+            bad = ~((v + lt <= p) & (p <= v + le))
+            if bool(bad.any()):
+                j = int(torch.nonzero(bad)[0, 0]) + c0
+                raise AssertionError(f"position {j} holds {int(ko[j]) & 0xFFFFFFFF}")
+
+    ko = torch.empty_like(kd)
+    bcf.bcf_sort_keys(ko, kd, kt=0)
+    torch.cuda.synchronize()
+    check_keys(ko)
+
+    vd = torch.empty_like(kd)
+    for c0 in range(0, n, chunk):
+        i = torch.arange(c0, min(n, c0 + chunk), dtype=torch.int64, device="cuda")
+        vd[c0:c0 + i.numel()] = u32_as_i32(i & 0xFFFFFFFF)
+    vo = torch.empty_like(vd)
+    ko.zero_()
+    bcf.bcf_sort_pairs(ko, vo, kd, vd, kt=0)
+    torch.cuda.synchronize()
+    check_keys(ko)
+    for c0 in range(0, n, chunk):
+        c1 = min(n, c0 + chunk)
+        k = ko[c0:c1].to(torch.int64) & 0xFFFFFFFF
+        v = vo[c0:c1].to(torch.int64) & 0xFFFFFFFF
+        assert torch.equal(v, (k * Cinv) & 0xFFFFFFFF), c0
+    assert bcf.bcf_last_device_error() == 0
