@@ -179,7 +179,7 @@ WsLayout ws_layout(uint64_t n, uint64_t runs_or_segs, int kb, bool pairs) {
 // sizes: a segment touches at most size/T + 2 tiles, and each of its passes
 // has one item per tile.
 struct SegLayout {
-  size_t ctl, items, tiny, queue, keys, vals, total;
+  size_t ctl, items, tiny, tbase, splits, queue, keys, vals, total;
   uint64_t capacity;
 };
 
@@ -192,7 +192,9 @@ SegLayout seg_layout(uint64_t n, uint64_t nseg, int kb, bool pairs) {
   w.ctl = kAlign;
   w.items = align_up(w.ctl + seg_ctl_bytes(), kAlign);
   w.tiny = align_up(w.items + nseg * 4, kAlign);
-  w.queue = align_up(w.tiny + nseg * 4, kAlign);
+  w.tbase = align_up(w.tiny + nseg * 4, kAlign);
+  w.splits = align_up(w.tbase + nseg * 8, kAlign);
+  w.queue = align_up(w.splits + tiles * 8, kAlign);
   w.keys = align_up(w.queue + w.capacity * seg_work_bytes(), kAlign);
   w.vals = align_up(w.keys + n * kb, kAlign);
   w.total = align_up(w.vals + (pairs ? n * 4 : 0), kAlign);
@@ -551,6 +553,8 @@ bcf_status run_segmented(void* ko, uint32_t* vo, const void* ki, const uint32_t*
   L.capacity = wl.capacity;
   L.items_left = reinterpret_cast<uint32_t*>(wsb + wl.items);
   L.tiny_list = reinterpret_cast<uint32_t*>(wsb + wl.tiny);
+  L.tile_base = reinterpret_cast<uint64_t*>(wsb + wl.tbase);
+  L.piece_split = reinterpret_cast<uint64_t*>(wsb + wl.splits);
   L.ctl = wsb + wl.ctl;
   L.err = err;
   // unpublished queue slots must read "not ready"

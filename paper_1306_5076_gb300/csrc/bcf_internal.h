@@ -97,6 +97,8 @@ struct SegLaunch {
   uint64_t capacity;
   uint32_t* items_left;  // nseg
   uint32_t* tiny_list;   // nseg
+  uint64_t* tile_base;   // nseg: index of the segment's first tile among all segments' tiles
+  uint64_t* piece_split; // one per tile of all segments: merge-path split of its next piece
   void* ctl;             // queue counters
   uint32_t* err;
 };

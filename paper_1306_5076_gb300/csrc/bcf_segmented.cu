@@ -20,11 +20,12 @@
 // Waiting for a slot to be published is bounded (global timer); on expiry the
 // device error word is set and the CTA exits.
 //
-// Merge pieces compute their own exact splitters (merge path, two warps in
-// parallel, 32-ary search) and read their windows straight from global memory
-// (.cg loads: data written by other SMs earlier in the same launch must not be
-// served from a stale L1 line), then run the same conflict-free bitonic merge
-// as the merge pass kernel.
+// The CTA that publishes a segment's merge pass first finds the exact
+// splitters of all its pieces (merge path, one warp per piece, 32-ary
+// search), so a piece starts with its two splits in hand.  Pieces read their
+// windows straight from global memory (.cg loads: data written by other SMs
+// earlier in the same launch must not be served from a stale L1 line), then
+// run the same conflict-free bitonic merge as the merge pass kernel.
 #include <cuda_runtime.h>
 
 #include "bcf_segmented.cuh"
@@ -82,6 +83,7 @@ __global__ void __launch_bounds__(1024) plan_kernel(const SegArgs a, uint32_t T,
     const unsigned long long sum_tot = sum;
     if (s < a.nseg) {
       a.items_left[s] = g.tiles;
+      a.tile_base[s] = carry_tiles + t_excl;
       if (g.tiny) a.tiny_list[carry_tiny + y_incl - 1] = static_cast<uint32_t>(s);
       const unsigned long long base = carry_tiles + t_excl;
       for (uint32_t q = 0; q < g.tiles; ++q) {
@@ -150,6 +152,8 @@ cudaError_t launch_segmented(int key_bytes, bool pairs, int cfg, const SegLaunch
   a.capacity = L.capacity;
   a.items_left = L.items_left;
   a.tiny_list = L.tiny_list;
+  a.tile_base = L.tile_base;
+  a.piece_split = L.piece_split;
   a.ctl = static_cast<SegCtl*>(L.ctl);
   a.err = L.err;
   return key_bytes == 4 ? launch_segmented_typed<uint32_t>(pairs, cfg, a, s)

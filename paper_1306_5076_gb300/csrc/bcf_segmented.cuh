@@ -78,6 +78,8 @@ struct SegArgs {
   uint64_t capacity;
   uint32_t* items_left;
   uint32_t* tiny_list;
+  uint64_t* tile_base;    // per segment: its first tile's index among all segments' tiles
+  uint64_t* piece_split;  // per tile: merge-path split (A-keys before the piece) of its piece
   SegCtl* ctl;
   uint32_t* err;
 };
@@ -276,41 +278,80 @@ __device__ __forceinline__ uint64_t warp_merge_path(const K* A, uint64_t na, con
   return lo;
 }
 
-template <typename K, bool PAIRS, int E, int NT, bool MAP>
-__device__ __forceinline__ void merge_piece_item(const SegArgs& a, const SegGeo& g,
-                                                 uint32_t pass, uint64_t rel, uint32_t* sm,
-                                                 uint64_t* s_split) {
-  constexpr uint64_t T = E * NT;  // merge tile == sort tile here
-  const uint32_t tid = threadIdx.x;
+// Geometry of merge piece `rel` of pass `pass` of a segment: the pair of
+// input runs A = [A0, A0 + na), B = [A0 + na, A0 + na + nb) it draws from and
+// the diagonals [d0, d1) of their merged order that land in its T-aligned
+// output tile gt.
+struct PieceGeo {
+  uint64_t gt, A0, na, nb, ps, pe, d0, d1;
+};
+__device__ __forceinline__ PieceGeo piece_geo(const SegGeo& g, uint32_t pass, uint64_t rel,
+                                              uint64_t T) {
+  PieceGeo p;
   const uint64_t G0 = g.lo / T;
-  const uint64_t gt = G0 + rel;                 // absolute output tile
+  p.gt = G0 + rel;                              // absolute output tile
   const uint64_t q = rel >> pass;               // pair index within the segment
   const uint64_t half = 1ull << (pass - 1);     // tiles per input run
   const uint64_t a0 = (G0 + (q << pass)) * T;
-  const uint64_t A0 = a0 > g.lo ? a0 : g.lo;
+  p.A0 = a0 > g.lo ? a0 : g.lo;
   const uint64_t a1 = (G0 + (q << pass) + half) * T;
   const uint64_t A1 = a1 < g.hi ? a1 : g.hi;
   const uint64_t b1 = (G0 + ((q + 1) << pass)) * T;
   const uint64_t B1 = b1 < g.hi ? b1 : g.hi;
-  const uint64_t na = A1 - A0, nb = B1 > A1 ? B1 - A1 : 0;
-  const uint64_t ps = gt * T > A0 ? gt * T : A0;
-  const uint64_t pe = (gt + 1) * T < A0 + na + nb ? (gt + 1) * T : A0 + na + nb;
-  const uint64_t d0 = ps - A0, d1 = pe - A0;
-  // pass p reads the buffer pass p-1 wrote
-  const bool src_out = ((g.passes - (pass - 1)) % 2) == 0;
+  p.na = A1 - p.A0;
+  p.nb = B1 > A1 ? B1 - A1 : 0;
+  p.ps = p.gt * T > p.A0 ? p.gt * T : p.A0;
+  p.pe = (p.gt + 1) * T < p.A0 + p.na + p.nb ? (p.gt + 1) * T : p.A0 + p.na + p.nb;
+  p.d0 = p.ps - p.A0;
+  p.d1 = p.pe - p.A0;
+  return p;
+}
+
+// The merge passes alternate between the output and the workspace copy so
+// that the last pass writes the output: pass p reads what pass p-1 wrote.
+__device__ __forceinline__ bool pass_reads_out(const SegGeo& g, uint32_t pass) {
+  return ((g.passes - (pass - 1)) % 2) == 0;
+}
+
+// Run by the whole CTA that completed a segment's pass `pass - 1`, before it
+// publishes pass `pass`: the split (A-keys before the piece's first output)
+// of every piece of the pass, one warp per piece, stored per tile.  Each piece
+// then reads its start split and the next piece's (or |A| at its pair's end)
+// instead of searching for them itself.
+template <typename K, int NT>
+__device__ __forceinline__ void publish_splits(const SegArgs& a, const SegGeo& g, uint64_t seg,
+                                               uint32_t pass, uint64_t T) {
+  const uint32_t warp = threadIdx.x >> 5;
+  const K* src = static_cast<const K*>(pass_reads_out(g, pass) ? a.kout : a.kbuf);
+  const uint64_t tb = __ldcg(a.tile_base + seg);
+  for (uint64_t rel = warp; rel < g.pieces; rel += NT / 32) {
+    const PieceGeo p = piece_geo(g, pass, rel, T);
+    const K* A = src + p.A0;
+    const uint64_t i0 = warp_merge_path(A, p.na, A + p.na, p.nb, p.d0);
+    if ((threadIdx.x & 31u) == 0) a.piece_split[tb + rel] = i0;
+  }
+  __threadfence();  // every split is visible before the pass is published
+}
+
+template <typename K, bool PAIRS, int E, int NT, bool MAP>
+__device__ __forceinline__ void merge_piece_item(const SegArgs& a, const SegGeo& g,
+                                                 uint64_t seg, uint32_t pass, uint64_t rel,
+                                                 uint32_t* sm) {
+  constexpr uint64_t T = E * NT;  // merge tile == sort tile here
+  const uint32_t tid = threadIdx.x;
+  const PieceGeo pg = piece_geo(g, pass, rel, T);
+  const uint64_t gt = pg.gt, A0 = pg.A0, na = pg.na, nb = pg.nb;
+  const uint64_t ps = pg.ps, pe = pg.pe, d0 = pg.d0, d1 = pg.d1;
+  const uint64_t A1 = A0 + na;
+  const bool src_out = pass_reads_out(g, pass);
   const bool dst_out = ((g.passes - pass) % 2) == 0;
   const K* src = static_cast<const K*>(src_out ? a.kout : a.kbuf);
   const uint32_t* vsrc = PAIRS ? (src_out ? a.vout : a.vbuf) : nullptr;
-  const K* A = src + A0;
-  const K* B = src + A1;
-  const uint32_t w = tid >> 5;
-  if (w < 2) {
-    const uint64_t d = w == 0 ? d0 : d1;
-    const uint64_t i = (w == 1 && d1 == na + nb) ? na : warp_merge_path(A, na, B, nb, d);
-    if ((tid & 31u) == 0) s_split[w] = i;
-  }
-  __syncthreads();
-  const uint64_t i0 = s_split[0], i1 = s_split[1];
+  // splits published with the pass (publish_splits); the next piece of the
+  // same pair starts where this one ends
+  const uint64_t tb = __ldcg(a.tile_base + seg);
+  const uint64_t i0 = __ldcg(a.piece_split + tb + rel);
+  const uint64_t i1 = d1 == na + nb ? na : __ldcg(a.piece_split + tb + rel + 1);
   const uint32_t wa = static_cast<uint32_t>(i1 - i0);
   const uint32_t wb = static_cast<uint32_t>((d1 - i1) - (d0 - i0));
   const uint32_t front = static_cast<uint32_t>(ps - gt * T);
@@ -367,7 +408,7 @@ __global__ void __launch_bounds__(NT) seg_worker(const SegArgs a) {
   extern __shared__ __align__(16) uint32_t sm[];
   __shared__ SegWork s_w;
   __shared__ int s_go;
-  __shared__ uint64_t s_split[2];
+  __shared__ int s_publish;
   const uint32_t tid = threadIdx.x;
   for (;;) {
     if (tid == 0) {
@@ -404,13 +445,20 @@ __global__ void __launch_bounds__(NT) seg_worker(const SegArgs a) {
     if (type == kWTile)
       sort_tile_item<K, PAIRS, E, NT, MAP>(a, g, w.arg, sm);
     else
-      merge_piece_item<K, PAIRS, E, NT, MAP>(a, g, pass, w.arg, sm, s_split);
+      merge_piece_item<K, PAIRS, E, NT, MAP>(a, g, w.seg, pass, w.arg, sm);
     __syncthreads();  // every store of this item is issued
     if (tid == 0) {
       __threadfence();  // ... and visible before the completion is counted
       const uint32_t left = atomicSub(a.items_left + w.seg, 1u);
-      if (left == 1 && pass < g.passes) {
-        // last item of this pass: publish the segment's next pass
+      s_publish = left == 1 && pass < g.passes;
+    }
+    __syncthreads();
+    if (s_publish) {
+      // last item of this pass: the CTA finds the next pass's splits, then
+      // publishes the segment's next pass
+      publish_splits<K, NT>(a, g, w.seg, pass + 1, T);
+      __syncthreads();
+      if (tid == 0) {
         const uint32_t m = g.pieces;
         a.items_left[w.seg] = m;
         const unsigned long long base = atomicAdd(&a.ctl->reserve, static_cast<unsigned long long>(m));

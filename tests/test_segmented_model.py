@@ -3,8 +3,9 @@
 Restates, as plain index arithmetic, what csrc/bcf_segmented.cuh computes for
 every work item -- the segment classes, the T-aligned tiles clipped to a
 segment, the merge pieces of every pass (pair index, A/B windows, output range,
-diagonals) and the buffer each pass reads and writes -- and executes the
-schedule on numpy data with an exact merge per piece.  Checks that every read
+diagonals), the splits the publishing CTA finds for every piece of a pass and
+the buffer each pass reads and writes -- and executes the schedule on numpy
+data, each piece merging only the windows its published splits give.  Checks that every read
 and write stays inside its segment, that each pass's pieces tile the segment
 exactly once, that the simulated result is the sorted segment, and that the
 work count the plan publishes equals the items executed.
@@ -55,6 +56,20 @@ def piece_item(lo, hi, T, p, rel):
     return A0, A1, na, nb, ps, pe, ps - A0, pe - A0, gt
 
 
+def merge_path(src, A0, A1, na, nb, d):
+    """Smallest i with A[i] > B[d-1-i] (the number of A-keys among the first d
+    outputs of the stable merge, A first on ties), or min(d, na)."""
+    A, B = src[A0:A1], src[A1:A1 + nb]
+    lo, hi = max(0, d - nb), min(d, na)
+    while lo < hi:
+        mid = (lo + hi) // 2
+        if A[mid] > B[d - 1 - mid]:
+            hi = mid
+        else:
+            lo = mid + 1
+    return lo
+
+
 def simulate(offs, keys, T, per_group=8):
     out = keys.copy()
     buf = np.zeros_like(keys)
@@ -82,13 +97,29 @@ def simulate(offs, keys, T, per_group=8):
             src = out if (passes - (p - 1)) % 2 == 0 else buf
             dst = out if (passes - p) % 2 == 0 else buf
             assert src is not dst
+            # publication: the CTA that completed pass p-1 finds every piece's
+            # start split (A-keys before the piece's first output)
+            split = []
+            for rel in range(pieces):
+                A0, A1, na, nb, _ps, _pe, d0, _d1, _gt = piece_item(lo, hi, T, p, rel)
+                split.append(merge_path(src, A0, A1, na, nb, d0))
             covered = np.zeros(hi - lo, np.int32)
             for rel in range(pieces):
                 A0, A1, na, nb, ps, pe, d0, d1, gt = piece_item(lo, hi, T, p, rel)
                 A, B = src[A0:A1], src[A1:A1 + nb]
                 assert np.all(np.diff(A) >= 0) and np.all(np.diff(B) >= 0), "runs not sorted"
+                # the piece's windows from the published splits: its own start
+                # split and the next piece's, or |A| at the end of its pair
+                i0 = split[rel]
+                i1 = na if d1 == na + nb else split[rel + 1]
+                if d1 < na + nb:
+                    assert (rel + 1) >> p == rel >> p, "next piece is in another pair"
+                wa, wb = A[i0:i1], B[d0 - i0:d1 - i1]
+                assert wa.size + wb.size == pe - ps
+                window = np.sort(np.concatenate([wa, wb]), kind="stable")
                 merged = np.sort(np.concatenate([A, B]), kind="stable")
-                dst[ps:pe] = merged[d0:d1]
+                assert np.array_equal(window, merged[d0:d1])
+                dst[ps:pe] = window
                 assert gt * T <= ps and pe <= (gt + 1) * T
                 covered[ps - lo:pe - lo] += 1
                 executed += 1
