@@ -684,6 +684,27 @@ def run_gpu(args, world, rank, local, pg):
         e2e_ms = float(t.item())
     # every stream's last result equals the device-timed sort's output
     ok_e2e = all(bool(torch.equal(h, ko.cpu())) for h in houts)
+
+    # the host link of this machine, for reading the end-to-end number: plain
+    # copies of the same pinned buffers, each way alone and both at once
+    def copy_gbs(pairs_):
+        sts = [torch.cuda.Stream(dev) for _ in pairs_]
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(2):
+            torch.cuda.synchronize()
+            c0.record(stream)
+            for st, (dst, src) in zip(sts, pairs_):
+                st.wait_event(c0)
+                with torch.cuda.stream(st):
+                    dst.copy_(src, non_blocking=True)
+            for st in sts:
+                stream.wait_stream(st)
+            c1.record(stream)
+            torch.cuda.synchronize()
+        return sum(d.numel() * d.element_size() for d, _ in pairs_) / (c0.elapsed_time(c1) * 1e6)
+
+    link = {"h2d_gbs": copy_gbs([(kd, host_in)]), "d2h_gbs": copy_gbs([(houts[0], ko)]),
+            "both_gbs": copy_gbs([(kd, host_in), (houts[0], ko)])}
     del wss
     torch.cuda.empty_cache()
 
@@ -751,7 +772,7 @@ def run_gpu(args, world, rank, local, pg):
         "e2e": {"value": world * N / (e2e_ms * 1e-3), "unit": "keys/s",
                 "h2d_bytes_per_step": N * KEY_BYTES, "d2h_bytes_per_step": N * KEY_BYTES,
                 "api": "bcf_sort_keys_host, pinned host buffers", "streams": E2E_STREAMS,
-                "steps": e2e_steps},
+                "steps": e2e_steps, "host_link": link},
         "clocks": clk,
         "checks": {"sorted": ok_sorted, "multiset": ok_multiset, "e2e_roundtrip": ok_e2e},
     }

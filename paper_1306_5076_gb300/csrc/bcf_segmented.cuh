@@ -402,8 +402,9 @@ __device__ __forceinline__ bool wait_ready(const SegWork* slot, uint32_t* err) {
   return true;
 }
 
+// The worker loop; the kernels below differ only in their register budget.
 template <typename K, bool PAIRS, int E, int NT, bool MAP>
-__global__ void __launch_bounds__(NT) seg_worker(const SegArgs a) {
+__device__ __forceinline__ void seg_worker_body(const SegArgs& a) {
   constexpr uint32_t T = E * NT;
   extern __shared__ __align__(16) uint32_t sm[];
   __shared__ SegWork s_w;
@@ -480,11 +481,32 @@ __global__ void __launch_bounds__(NT) seg_worker(const SegArgs a) {
   }
 }
 
+// 32-bit keys without payloads: held to 1024 / NT CTAs per SM (64 registers
+// a thread, which they need at most), so the 128- and 256-thread
+// configurations run 8 and 4 CTAs per SM; left to the compiler they took 128
+// registers and half the CTAs, and the sort of 100,000 segments ran 52 ms
+// instead of 37 ms.  Payloads and 64-bit keys need more registers than that.
+template <typename K, bool PAIRS, int E, int NT, bool MAP>
+__global__ void __launch_bounds__(NT, 1024 / NT) seg_worker_capped(const SegArgs a) {
+  seg_worker_body<K, PAIRS, E, NT, MAP>(a);
+}
+template <typename K, bool PAIRS, int E, int NT, bool MAP>
+__global__ void __launch_bounds__(NT) seg_worker(const SegArgs a) {
+  seg_worker_body<K, PAIRS, E, NT, MAP>(a);
+}
+template <typename K, bool PAIRS, int E, int NT, bool MAP>
+constexpr auto seg_kernel() {
+  if constexpr (!PAIRS && sizeof(K) == 4)
+    return &seg_worker_capped<K, PAIRS, E, NT, MAP>;
+  else
+    return &seg_worker<K, PAIRS, E, NT, MAP>;
+}
+
 template <typename K, bool PAIRS, int E, int NT, bool MAP>
 cudaError_t launch_seg(const SegArgs& a, cudaStream_t s) {
   constexpr int W = Frag<K, PAIRS, E>::W;
   const size_t smem = static_cast<size_t>(W) * Geo<E, NT>::kPlane * sizeof(uint32_t);
-  auto kern = seg_worker<K, PAIRS, E, NT, MAP>;
+  auto kern = seg_kernel<K, PAIRS, E, NT, MAP>();
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
   if (err != cudaSuccess) return err;
