@@ -160,6 +160,22 @@ def dist_setup(args):
     return world, rank, local, pg
 
 
+def max_over_ranks(torch, pg, x, dev):
+    """The largest of every rank's x (the job's time is its slowest rank's);
+    x itself when there is no process group."""
+    if pg is None:
+        return x
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_keys_per_s(world, n_per_rank, ms):
+    """Whole-job throughput: every rank sorts its own n_per_rank keys (weak
+    scaling, replicas), the job takes the slowest rank's ms."""
+    return world * n_per_rank / (ms * 1e-3)
+
+
 def cpu_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -628,11 +644,7 @@ def run_gpu(args, world, rank, local, pg):
     clk = clocks.stop(m0, m1)
     bcf.bcf_profile_enable(False)
     prof = bcf.bcf_profile_collect()
-    ms = e0.elapsed_time(e1) / args.steps
-    if pg is not None:
-        t = torch.tensor([ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(torch, pg, e0.elapsed_time(e1) / args.steps, dev)
 
     # correctness of the timed output (bit-exact order check on the device:
     # sorted and same multiset fingerprint as the input)
@@ -677,11 +689,7 @@ def run_gpu(args, world, rank, local, pg):
         stream.wait_stream(st)
     h1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = h0.elapsed_time(h1) / e2e_steps
-    if pg is not None:
-        t = torch.tensor([e2e_ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(torch, pg, h0.elapsed_time(h1) / e2e_steps, dev)
     # every stream's last result equals the device-timed sort's output
     ok_e2e = all(bool(torch.equal(h, ko.cpu())) for h in houts)
 
@@ -742,7 +750,7 @@ def run_gpu(args, world, rank, local, pg):
                          f"(C, {cores} threads), {t[0]:.2f} s"}
     line = {
         "metric": METRIC,
-        "value": world * N / (ms * 1e-3),
+        "value": job_keys_per_s(world, N, ms),
         "unit": "keys/s",
         "n_gpus": world,
         "steps": args.steps,
@@ -769,7 +777,7 @@ def run_gpu(args, world, rank, local, pg):
                           "partition": part["total_ms"] / max(part["launches"], 1),
                           "merge": merge_ms},
         "gpu_launches": launches,
-        "e2e": {"value": world * N / (e2e_ms * 1e-3), "unit": "keys/s",
+        "e2e": {"value": job_keys_per_s(world, N, e2e_ms), "unit": "keys/s",
                 "h2d_bytes_per_step": N * KEY_BYTES, "d2h_bytes_per_step": N * KEY_BYTES,
                 "api": "bcf_sort_keys_host, pinned host buffers", "streams": E2E_STREAMS,
                 "steps": e2e_steps, "host_link": link},
