@@ -535,13 +535,24 @@ def merge_runs_bench(torch, dev, bcf, peak):
             vo = torch.empty_like(vd) if pairs else None
             ws = torch.empty(bcf.bcf_workspace_bytes(bcf.BCF_OP_MERGE, total, k, bcf.BCF_U32,
                                                      pairs), dtype=torch.uint8, device=dev)
-            ms = timed_ms(torch, stream, lambda: bcf.bcf_merge_runs(
-                ko, vo, kd, vd, offl, kt=bcf.BCF_U32, ws=ws, stream=stream), warmup=2, reps=5)
+            def call():
+                bcf.bcf_merge_runs(ko, vo, kd, vd, offl, kt=bcf.BCF_U32, ws=ws, stream=stream)
+
+            ms = timed_ms(torch, stream, call, warmup=2, reps=5)
+            # where one call's device time goes (library events on the stream)
+            torch.cuda.synchronize()
+            bcf.bcf_profile_collect()
+            bcf.bcf_profile_enable(True)
+            call()
+            torch.cuda.synchronize()
+            bcf.bcf_profile_enable(False)
+            prof = bcf.bcf_profile_collect()
             passes = int(np.ceil(np.log2(k)))
             gbs = passes * 2 * total * (4 + (4 if pairs else 0)) / (ms * 1e-3) / 1e9
             out[f"k={k}{' +u32' if pairs else ''}"] = {
                 "ms": ms, "keys_per_s": total / (ms * 1e-3), "merge_passes": passes,
-                "gbs_over_passes": gbs, "frac": gbs / peak}
+                "gbs_over_passes": gbs, "frac": gbs / peak,
+                "partition_ms": prof["partition"]["total_ms"], "merge_ms": prof["merge"]["total_ms"]}
             del vd, vo, ws
             torch.cuda.empty_cache()
         del kd, ko

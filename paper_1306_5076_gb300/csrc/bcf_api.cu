@@ -467,6 +467,13 @@ bcf_status run_merge(void* ko, uint32_t* vo, const void* ki, const uint32_t* vi,
     src_v = wv;
   }
   uint64_t* splits = reinterpret_cast<uint64_t*>(wsb + wl.splits);
+  // Samples (the keys at array positions that are multiples of
+  // kSampleStride, in mapped order) narrow every merge-path search to a
+  // window: pass i reads samp[i & 1], its merge kernel writes the next pass's
+  // into samp[(i + 1) & 1], and pass 1's are taken from the input first.
+  void* samp[2] = {wsb + wl.samples0, wsb + wl.samples1};
+  if (launch_sample_span(kb, src_k, samp[1], src_mode, lo, offs[k], s) != cudaSuccess)
+    return BCF_ECUDA;
   for (int i = 1; i <= m; ++i) {
     const bool to_out = ((m - i) % 2) == 0;
     void* dst_k = to_out ? ko : wk;
@@ -503,6 +510,8 @@ bcf_status run_merge(void* ko, uint32_t* vo, const void* ki, const uint32_t* vi,
       ma.mode_out = i == m ? mode : 0;
       ma.err = err;
       ma.nitems = end_piece - pl.p[0].piece0;
+      ma.samples_in = samp[i & 1];
+      ma.samples_out = i == m ? nullptr : samp[(i + 1) & 1];
       cudaError_t e =
           timed(1, s, [&] { return launch_partition(kb, plan.tune.merge_cfg, ma, &pl, s); });
       if (e != cudaSuccess) return BCF_ECUDA;

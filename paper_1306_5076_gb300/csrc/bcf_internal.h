@@ -54,8 +54,8 @@ struct MergeArgs {
   int mode_out;
   uint32_t* err;        // device error word
   uint64_t nitems;      // work items (tile pieces) of this launch
-  const void* samples_in;  // regular mode: sample array of kin, or nullptr
-  void* samples_out;       // regular mode: sample array of kout, or nullptr
+  const void* samples_in;  // sample array of kin (key g / S at every g = 0 mod S), or nullptr
+  void* samples_out;       // sample array of kout, or nullptr
 };
 
 // Tuning configuration: elements per thread and threads per CTA.
@@ -112,6 +112,10 @@ cudaError_t launch_block_sort(int key_bytes, bool pairs, int cfg, const BlockSor
                               cudaStream_t s);
 cudaError_t launch_partition(int key_bytes, int cfg, const MergeArgs& a, const PairList* pl,
                              cudaStream_t s);
+// Samples of keys [lo, hi): samples[g / kSampleStride] = (mapped) keys[g] for
+// every g in [lo, hi) that is a multiple of kSampleStride.
+cudaError_t launch_sample_span(int key_bytes, const void* keys, void* samples, int mode,
+                               uint64_t lo, uint64_t hi, cudaStream_t s);
 cudaError_t launch_merge(int key_bytes, bool pairs, int cfg, const MergeArgs& a,
                          const PairList* pl, cudaStream_t s);
 

@@ -167,6 +167,41 @@ __global__ void __launch_bounds__(256) partition_kernel(const MergeArgs a, int T
         return;
       }
     }
+  } else if constexpr (IRREG) {
+    if (a.samples_in) {
+      // Runs at any offsets: the samples are the keys at the array positions
+      // that are multiples of S, so A's are A[cA + kS] and B's B[cB + kS]
+      // with cA, cB < S.  Merge path on them at diagonal
+      // D = floor((d - cA - cB) / S) + 1 puts the true split within S of
+      // cA + S * (A-samples taken) (checked exhaustively on small runs by the
+      // host model of this search); the result is then checked against the
+      // split's defining inequalities, with the full search as the fallback.
+      constexpr uint64_t S = kSampleStride;
+      const uint64_t offA = p.src, offB = p.src + p.na_tot;
+      const uint64_t gA = (offA + S - 1) / S, gB = (offB + S - 1) / S;
+      const uint64_t cA = gA * S - offA, cB = gB * S - offB;
+      const uint64_t nas = p.na_tot > cA ? (p.na_tot - cA + S - 1) / S : 0;
+      const uint64_t nbs = p.nb_tot > cB ? (p.nb_tot - cB + S - 1) / S : 0;
+      const K* As = static_cast<const K*>(a.samples_in) + gA;
+      const K* Bs = static_cast<const K*>(a.samples_in) + gB;
+      uint64_t D = d >= cA + cB ? (d - cA - cB) / S + 1 : 0;
+      D = D < nas + nbs ? D : nas + nbs;
+      const uint64_t sa = merge_path_bs<K, false>(As, Bs, D, D > nbs ? D - nbs : 0,
+                                                  D < nas ? D : nas, 0);
+      const uint64_t c = cA + sa * S;
+      const uint64_t wlo0 = c > lo + S ? c - S : lo;
+      const uint64_t whi = c + S < hi ? c + S : hi;
+      const uint64_t wlo = wlo0 < whi ? wlo0 : whi;
+      const int m = MAP ? a.mode_in : 0;
+      const uint64_t i = merge_path_bs<K, MAP>(A, B, d, wlo, whi, m);
+      const auto key = [m](const K* q) { return MAP ? map_key(__ldg(q), m) : __ldg(q); };
+      const bool left_ok = i == 0 || d - i >= p.nb_tot || !(key(A + i - 1) > key(B + (d - i)));
+      const bool right_ok = i >= p.na_tot || d == i || key(A + i) > key(B + (d - i - 1));
+      if (left_ok && right_ok && i >= lo && i <= hi) {
+        a.splits[item] = i;
+        return;
+      }
+    }
   }
   a.splits[item] = merge_path_bs<K, MAP>(A, B, d, lo, hi, a.mode_in);
 }
@@ -234,7 +269,11 @@ __device__ __forceinline__ T read_seq(const T* sa, const T* sb, uint32_t k, uint
   return lds_pred(sb + (Tm1 - k), isB, v);
 }
 
-template <typename K, bool PAIRS, int E, int NT, bool IRREG, bool MAP>
+// SMP (irregular passes): the launch writes samples of its output (a pass
+// with a successor); without it the kernel carries no sample code at all.
+// Regular passes check for a sample array at run time, as the measured
+// sort's passes always have.
+template <typename K, bool PAIRS, int E, int NT, bool IRREG, bool MAP, bool SMP>
 __global__ void __launch_bounds__(NT) merge_kernel(const MergeArgs a,
                                                    const __grid_constant__ PairParam<IRREG> pl) {
   using S = MergeSmem<K, PAIRS, E, NT>;
@@ -325,9 +364,15 @@ __global__ void __launch_bounds__(NT) merge_kernel(const MergeArgs a,
 
   f.one = g_unit_multiplier;  // FMA-pipe maxima in the BLK stages (keys-only 32-bit)
   bitonic_merge_str<NT, true>(f, reinterpret_cast<uint32_t*>(body));
-  if constexpr (!IRREG && !MAP) {
-    // samples of the output run for the next pass's merge-path search
+  // samples of the output for the next pass's merge-path search: the keys at
+  // array positions that are multiples of S, still in mapped order (a pass
+  // with a successor writes no unmapped keys)
+  if constexpr (!IRREG) {
     if (a.samples_out && ((p.out0 + tid * E) % kSampleStride) == 0 && tid * E < p.d1 - p.d0)
+      static_cast<K*>(a.samples_out)[(p.out0 + tid * E) / kSampleStride] = f.k[0];
+  } else if constexpr (SMP) {
+    if (((p.out0 + tid * E) % kSampleStride) == 0 && tid * E >= front &&
+        tid * E < front + (p.d1 - p.d0))
       static_cast<K*>(a.samples_out)[(p.out0 + tid * E) / kSampleStride] = f.k[0];
   }
 
@@ -357,6 +402,42 @@ __global__ void __launch_bounds__(NT) merge_kernel(const MergeArgs a,
   }
 }
 
+// Samples of the keys of a merge's given runs (its first pass; later passes
+// get theirs from the merge kernel).
+template <typename K, bool MAP>
+__global__ void __launch_bounds__(256) sample_span_kernel(const K* keys, K* samples, int mode,
+                                                          uint64_t g0, uint64_t count) {
+  const uint64_t t = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  const uint64_t g = g0 + t;
+  const K k = keys[g * kSampleStride];
+  samples[g] = MAP ? map_key(k, mode) : k;
+}
+
+template <typename K>
+static cudaError_t launch_ss(const void* keys, void* samples, int mode, uint64_t lo, uint64_t hi,
+                             cudaStream_t s) {
+  constexpr uint64_t S = kSampleStride;
+  const uint64_t g0 = (lo + S - 1) / S, g1 = (hi + S - 1) / S;
+  if (g1 <= g0) return cudaSuccess;
+  const uint64_t count = g1 - g0;
+  const unsigned grid = static_cast<unsigned>((count + 255) / 256);
+  if (mode)
+    sample_span_kernel<K, true><<<grid, 256, 0, s>>>(static_cast<const K*>(keys),
+                                                     static_cast<K*>(samples), mode, g0, count);
+  else
+    sample_span_kernel<K, false><<<grid, 256, 0, s>>>(static_cast<const K*>(keys),
+                                                      static_cast<K*>(samples), mode, g0, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sample_span(int key_bytes, const void* keys, void* samples, int mode,
+                               uint64_t lo, uint64_t hi, cudaStream_t s) {
+  if (key_bytes == 4) return launch_ss<uint32_t>(keys, samples, mode, lo, hi, s);
+  if (key_bytes == 8) return launch_ss<uint64_t>(keys, samples, mode, lo, hi, s);
+  return cudaErrorInvalidValue;
+}
+
 // ---------------------------------------------------------------- dispatch
 
 // Pairs and 64-bit keys are built with E = 16 only (register budget).
@@ -367,15 +448,21 @@ bool merge_cfg_supported(int key_bytes, bool pairs, int cfg) {
   return true;
 }
 
-template <typename K, bool PAIRS, int E, int NT, bool IRREG, bool MAP>
-static cudaError_t launch_m2(const MergeArgs& a, const PairParam<IRREG>& pl, cudaStream_t s) {
+template <typename K, bool PAIRS, int E, int NT, bool IRREG, bool MAP, bool SMP>
+static cudaError_t launch_m3(const MergeArgs& a, const PairParam<IRREG>& pl, cudaStream_t s) {
   using S = MergeSmem<K, PAIRS, E, NT>;
-  auto kern = merge_kernel<K, PAIRS, E, NT, IRREG, MAP>;
+  auto kern = merge_kernel<K, PAIRS, E, NT, IRREG, MAP, SMP>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          S::kTotal);
   if (err != cudaSuccess) return err;
   kern<<<static_cast<unsigned>(a.nitems), NT, S::kTotal, s>>>(a, pl);
   return cudaGetLastError();
+}
+
+template <typename K, bool PAIRS, int E, int NT, bool IRREG, bool MAP>
+static cudaError_t launch_m2(const MergeArgs& a, const PairParam<IRREG>& pl, cudaStream_t s) {
+  if (IRREG && !a.samples_out) return launch_m3<K, PAIRS, E, NT, IRREG, MAP, false>(a, pl, s);
+  return launch_m3<K, PAIRS, E, NT, IRREG, MAP, true>(a, pl, s);
 }
 
 template <typename K, bool PAIRS, int E, int NT>
