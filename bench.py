@@ -709,7 +709,8 @@ def run_gpu(args, world, rank, local, pg):
     def copy_gbs(pairs_):
         sts = [torch.cuda.Stream(dev) for _ in pairs_]
         c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        for _ in range(2):
+        best = None
+        for _ in range(3):  # the fastest of three
             torch.cuda.synchronize()
             c0.record(stream)
             for st, (dst, src) in zip(sts, pairs_):
@@ -720,7 +721,9 @@ def run_gpu(args, world, rank, local, pg):
                 stream.wait_stream(st)
             c1.record(stream)
             torch.cuda.synchronize()
-        return sum(d.numel() * d.element_size() for d, _ in pairs_) / (c0.elapsed_time(c1) * 1e6)
+            t = c0.elapsed_time(c1)
+            best = t if best is None else min(best, t)
+        return sum(d.numel() * d.element_size() for d, _ in pairs_) / (best * 1e6)
 
     link = {"h2d_gbs": copy_gbs([(kd, host_in)]), "d2h_gbs": copy_gbs([(houts[0], ko)]),
             "both_gbs": copy_gbs([(kd, host_in), (houts[0], ko)])}
