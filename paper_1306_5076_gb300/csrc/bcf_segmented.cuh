@@ -313,6 +313,28 @@ __device__ __forceinline__ bool pass_reads_out(const SegGeo& g, uint32_t pass) {
   return ((g.passes - (pass - 1)) % 2) == 0;
 }
 
+// The two splits of one piece of a long segment, searched by warps 0 and 1
+// (out of line: the common path, published splits, keeps its registers).
+template <typename K>
+__device__ __noinline__ void search_piece_splits(const K* A, uint64_t na, uint64_t nb,
+                                                 uint64_t d0, uint64_t d1, uint64_t* s_split) {
+  const uint32_t w = threadIdx.x >> 5;
+  if (w < 2) {
+    const uint64_t d = w == 0 ? d0 : d1;
+    const uint64_t i = (w == 1 && d1 == na + nb) ? na : warp_merge_path(A, na, A + na, nb, d);
+    if ((threadIdx.x & 31u) == 0) s_split[w] = i;
+  }
+}
+
+// Whether the CTA that publishes a pass of this segment also finds the
+// pass's splits: up to 16 rounds of its warps (a few tens of microseconds).
+// A longer segment's pieces search their own, in parallel, so that a single
+// huge segment is not held up by one CTA.
+template <int NT>
+__device__ __forceinline__ bool splits_published(const SegGeo& g) {
+  return g.pieces <= 16u * (NT / 32);
+}
+
 // Run by the whole CTA that completed a segment's pass `pass - 1`, before it
 // publishes pass `pass`: the split (A-keys before the piece's first output)
 // of every piece of the pass, one warp per piece, stored per tile.  Each piece
@@ -336,7 +358,7 @@ __device__ __forceinline__ void publish_splits(const SegArgs& a, const SegGeo& g
 template <typename K, bool PAIRS, int E, int NT, bool MAP>
 __device__ __forceinline__ void merge_piece_item(const SegArgs& a, const SegGeo& g,
                                                  uint64_t seg, uint32_t pass, uint64_t rel,
-                                                 uint32_t* sm) {
+                                                 uint32_t* sm, uint64_t* s_split) {
   constexpr uint64_t T = E * NT;  // merge tile == sort tile here
   const uint32_t tid = threadIdx.x;
   const PieceGeo pg = piece_geo(g, pass, rel, T);
@@ -347,11 +369,20 @@ __device__ __forceinline__ void merge_piece_item(const SegArgs& a, const SegGeo&
   const bool dst_out = ((g.passes - pass) % 2) == 0;
   const K* src = static_cast<const K*>(src_out ? a.kout : a.kbuf);
   const uint32_t* vsrc = PAIRS ? (src_out ? a.vout : a.vbuf) : nullptr;
-  // splits published with the pass (publish_splits); the next piece of the
-  // same pair starts where this one ends
-  const uint64_t tb = __ldcg(a.tile_base + seg);
-  const uint64_t i0 = __ldcg(a.piece_split + tb + rel);
-  const uint64_t i1 = d1 == na + nb ? na : __ldcg(a.piece_split + tb + rel + 1);
+  uint64_t i0, i1;
+  if (splits_published<NT>(g)) {
+    // splits published with the pass (publish_splits); the next piece of the
+    // same pair starts where this one ends
+    const uint64_t tb = __ldcg(a.tile_base + seg);
+    i0 = __ldcg(a.piece_split + tb + rel);
+    i1 = d1 == na + nb ? na : __ldcg(a.piece_split + tb + rel + 1);
+  } else {
+    // a long segment: two warps search this piece's two splits
+    search_piece_splits(src + A0, na, nb, d0, d1, s_split);
+    __syncthreads();
+    i0 = s_split[0];
+    i1 = s_split[1];
+  }
   const uint32_t wa = static_cast<uint32_t>(i1 - i0);
   const uint32_t wb = static_cast<uint32_t>((d1 - i1) - (d0 - i0));
   const uint32_t front = static_cast<uint32_t>(ps - gt * T);
@@ -410,6 +441,7 @@ __device__ __forceinline__ void seg_worker_body(const SegArgs& a) {
   __shared__ SegWork s_w;
   __shared__ int s_go;
   __shared__ int s_publish;
+  __shared__ uint64_t s_split[2];
   const uint32_t tid = threadIdx.x;
   for (;;) {
     if (tid == 0) {
@@ -446,7 +478,7 @@ __device__ __forceinline__ void seg_worker_body(const SegArgs& a) {
     if (type == kWTile)
       sort_tile_item<K, PAIRS, E, NT, MAP>(a, g, w.arg, sm);
     else
-      merge_piece_item<K, PAIRS, E, NT, MAP>(a, g, w.seg, pass, w.arg, sm);
+      merge_piece_item<K, PAIRS, E, NT, MAP>(a, g, w.seg, pass, w.arg, sm, s_split);
     __syncthreads();  // every store of this item is issued
     if (tid == 0) {
       __threadfence();  // ... and visible before the completion is counted
@@ -457,7 +489,7 @@ __device__ __forceinline__ void seg_worker_body(const SegArgs& a) {
     if (s_publish) {
       // last item of this pass: the CTA finds the next pass's splits, then
       // publishes the segment's next pass
-      publish_splits<K, NT>(a, g, w.seg, pass + 1, T);
+      if (splits_published<NT>(g)) publish_splits<K, NT>(a, g, w.seg, pass + 1, T);
       __syncthreads();
       if (tid == 0) {
         const uint32_t m = g.pieces;
@@ -481,13 +513,14 @@ __device__ __forceinline__ void seg_worker_body(const SegArgs& a) {
   }
 }
 
-// 32-bit keys without payloads: held to 1024 / NT CTAs per SM (64 registers
-// a thread, which they need at most), so the 128- and 256-thread
-// configurations run 8 and 4 CTAs per SM; left to the compiler they took 128
-// registers and half the CTAs, and the sort of 100,000 segments ran 52 ms
-// instead of 37 ms.  Payloads and 64-bit keys need more registers than that.
+// 32-bit keys without payloads: at least 1152 / NT CTAs per SM (at most 56
+// registers a thread for 128 threads, 64 for 256 and 512), so the 128-thread
+// configuration runs 9 or more CTAs per SM and the 256-thread one 4.  Left to
+// the compiler they took 128 registers and half the CTAs, and the sort of
+// 100,000 segments ran 52 ms instead of 37 ms.  Payloads and 64-bit keys need
+// more registers than that.
 template <typename K, bool PAIRS, int E, int NT, bool MAP>
-__global__ void __launch_bounds__(NT, 1024 / NT) seg_worker_capped(const SegArgs a) {
+__global__ void __launch_bounds__(NT, 1152 / NT) seg_worker_capped(const SegArgs a) {
   seg_worker_body<K, PAIRS, E, NT, MAP>(a);
 }
 template <typename K, bool PAIRS, int E, int NT, bool MAP>

@@ -140,3 +140,61 @@ def test_cuda_graph_replay(bcf):
         assert np.array_equal(from_dev(ko, np.uint32), ek)
         assert np.array_equal(from_dev(vo, np.uint32), ev)
     assert bcf.bcf_last_device_error() == 0
+
+
+@pytest.mark.parametrize("pairs", [False, True])
+def test_segments_past_2p32_keys(bcf, pairs):
+    """Maximum sizes: 2^32 + 2^20 + 37 keys in segments of every class, one of
+    them 2^31 keys long and one crossing position 2^32, so tile indices,
+    merge-piece offsets and the queue go past 32 bits.  Key i is
+    (i * C) mod 2^32 (odd C) and payload i mod 2^32, so every output element
+    must satisfy key == payload * C mod 2^32; each segment must come out
+    sorted with the multiset of its input (sum and sum of squares mod a prime,
+    per segment)."""
+    need = (100 if pairs else 60) << 30
+    if torch.cuda.get_device_properties(0).total_memory < need + (8 << 30):
+        pytest.skip("needs a large device memory")
+    C = 0x9E3779B1
+    n = (1 << 32) + (1 << 20) + 37
+    offs = np.array([0, 0, 1, 300, 5000, 70000, (1 << 31) + 70000, (1 << 32) - 999,
+                     (1 << 32) + 4096 + 17, n], dtype=np.int64)
+    chunk = 1 << 27
+
+    def u32_as_i32(x):
+        return torch.where(x >= (1 << 31), x - (1 << 32), x).to(torch.int32)
+
+    kd = torch.empty(n, dtype=torch.int32, device="cuda")
+    vd = torch.empty(n, dtype=torch.int32, device="cuda") if pairs else None
+    for c0 in range(0, n, chunk):
+        i = torch.arange(c0, min(n, c0 + chunk), dtype=torch.int64, device="cuda")
+        kd[c0:c0 + i.numel()] = u32_as_i32((i * C) & 0xFFFFFFFF)
+        if pairs:
+            vd[c0:c0 + i.numel()] = u32_as_i32(i & 0xFFFFFFFF)
+    P = 1000000007
+
+    def fingerprint(x):
+        s1 = s2 = 0
+        for c0 in range(0, x.numel(), chunk):
+            v = x[c0:c0 + chunk].to(torch.int64) & 0xFFFFFFFF
+            s1 += int(v.sum())
+            s2 += int(((v * v) % P).sum())
+        return s1, s2 % P
+
+    before = [fingerprint(kd[a:b]) for a, b in zip(offs[:-1], offs[1:])]
+    ko = torch.empty_like(kd)
+    vo = torch.empty_like(vd) if pairs else None
+    od = torch.from_numpy(offs).to("cuda")
+    bcf.bcf_segmented_sort(ko, vo, kd, vd, od, kt=0)
+    torch.cuda.synchronize()
+    assert bcf.bcf_last_device_error() == 0
+    del kd, vd
+    for s, (a, b) in enumerate(zip(offs[:-1], offs[1:])):
+        a, b = int(a), int(b)
+        for c0 in range(a, b, chunk):
+            c1 = min(b, c0 + chunk + 1)  # one element of overlap joins the chunks
+            v = ko[c0:c1].to(torch.int64) & 0xFFFFFFFF
+            assert bool((v[1:] >= v[:-1]).all()), (s, c0)
+            if pairs:
+                p = vo[c0:c1].to(torch.int64) & 0xFFFFFFFF
+                assert torch.equal(v, (p * C) & 0xFFFFFFFF), (s, c0)
+        assert fingerprint(ko[a:b]) == before[s], s
