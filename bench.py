@@ -160,6 +160,27 @@ def dist_setup(args):
     return world, rank, local, pg
 
 
+def per_pass_ms(launch_list):
+    """Each pass of the sort on its own, averaged over the timed steps: the
+    launches of one step are a block sort, then a partition and a merge per
+    merge pass (launch order, as the library records them)."""
+    steps, cur = [], None
+    for kind, ms in launch_list:
+        if kind == "block_sort":
+            cur = {"block_sort": ms, "partition": [], "merge": []}
+            steps.append(cur)
+        elif cur is not None and kind in ("partition", "merge"):
+            cur[kind].append(ms)
+    if not steps:
+        return None
+    n = min(len(s["merge"]) for s in steps)
+    mean = lambda xs: sum(xs) / len(xs)  # noqa: E731
+    return {"block_sort": mean([s["block_sort"] for s in steps]),
+            "partition": [mean([s["partition"][i] for s in steps]) for i in range(n)],
+            "merge": [mean([s["merge"][i] for s in steps]) for i in range(n)],
+            "steps": len(steps)}
+
+
 def max_over_ranks(torch, pg, x, dev):
     """The largest of every rank's x (the job's time is its slowest rank's);
     x itself when there is no process group."""
@@ -654,8 +675,9 @@ def run_gpu(args, world, rank, local, pg):
     barrier()
     clk = clocks.stop(m0, m1)
     bcf.bcf_profile_enable(False)
-    prof = bcf.bcf_profile_collect()
+    prof, launch_list = bcf.bcf_profile_collect_launches(64 * (args.steps + 1) + 64)
     ms = max_over_ranks(torch, pg, e0.elapsed_time(e1) / args.steps, dev)
+    passes = per_pass_ms(launch_list)
 
     # correctness of the timed output (bit-exact order check on the device:
     # sorted and same multiset fingerprint as the input)
@@ -790,6 +812,7 @@ def run_gpu(args, world, rank, local, pg):
         "per_kernel_ms": {"block_sort": bs["total_ms"] / max(bs["launches"], 1),
                           "partition": part["total_ms"] / max(part["launches"], 1),
                           "merge": merge_ms},
+        "per_pass_ms": passes,
         "gpu_launches": launches,
         "e2e": {"value": job_keys_per_s(world, N, e2e_ms), "unit": "keys/s",
                 "h2d_bytes_per_step": N * KEY_BYTES, "d2h_bytes_per_step": N * KEY_BYTES,

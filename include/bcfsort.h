@@ -214,6 +214,14 @@ typedef struct {
 bcf_status bcf_profile_enable(int on);
 /* Synchronise the recorded events, accumulate their times into *out, clear. */
 bcf_status bcf_profile_collect(bcf_profile* out);
+/*
+ * The same, and also each launch on its own, in launch order: kinds[i] and
+ * ms[i] for the first min(count of launches, max) of them (host arrays of max
+ * entries, owned by the caller; either may be NULL when max is 0).  *count
+ * gets the number of launches recorded.  BCF_EINVAL for a NULL out or count.
+ */
+bcf_status bcf_profile_collect_launches(bcf_profile* out, int* kinds, float* ms, uint32_t max,
+                                        uint32_t* count);
 
 /* Version string of the library. */
 const char* bcf_version(void);

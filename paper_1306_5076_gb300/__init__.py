@@ -22,7 +22,8 @@ from ._native import (BCF_ALGO_MERGE, BCF_ALGO_PIVOT_BUCKETS, BCF_CPS_BANKED, BC
 __all__ = [
     "BcfError", "bcf_workspace_bytes", "bcf_sort_keys", "bcf_sort_pairs", "bcf_merge_runs",
     "bcf_segmented_sort", "bcf_last_device_error", "bcf_sort_plan", "bcf_profile_enable",
-    "bcf_profile_collect", "bcf_version", "bcf_sort_keys_static", "bcf_tuning_set",
+    "bcf_profile_collect", "bcf_profile_collect_launches", "bcf_version",
+    "bcf_sort_keys_static", "bcf_tuning_set",
     "bcf_tuning_config", "bcf_tuning_supported", "key_dtype_of", "BCF_U32",
     "BCF_U64", "BCF_F32", "BCF_I32", "BCF_I64", "BCF_F64", "BCF_U16", "BCF_I16",
     "BCF_OP_SORT", "BCF_OP_MERGE", "BCF_OP_SEGMENTED", "BCF_OP_CPS",
@@ -267,13 +268,32 @@ def bcf_profile_enable(on: bool = True) -> None:
     _check(_native.load().bcf_profile_enable(int(bool(on))), "bcf_profile_enable")
 
 
+PROFILE_KINDS = ("block_sort", "partition", "merge", "segmented", "colored_prefix_sums",
+                 "pivot_buckets")
+
+
 def bcf_profile_collect() -> dict:
     p = _native.BcfProfile()
     _check(_native.load().bcf_profile_collect(ctypes.byref(p)), "bcf_profile_collect")
-    kinds = ("block_sort", "partition", "merge", "segmented", "colored_prefix_sums",
-             "pivot_buckets")
     return {k: {"launches": int(p.launches[i]), "total_ms": float(p.total_ms[i])}
-            for i, k in enumerate(kinds)}
+            for i, k in enumerate(PROFILE_KINDS)}
+
+
+def bcf_profile_collect_launches(max_launches: int = 4096):
+    """Like bcf_profile_collect, plus every recorded launch in order as
+    (kind name, ms) -- e.g. each merge pass of a sort on its own."""
+    p = _native.BcfProfile()
+    kinds = (ctypes.c_int * max_launches)()
+    ms = (ctypes.c_float * max_launches)()
+    count = ctypes.c_uint32(0)
+    _check(_native.load().bcf_profile_collect_launches(ctypes.byref(p), kinds, ms, max_launches,
+                                                       ctypes.byref(count)),
+           "bcf_profile_collect_launches")
+    totals = {k: {"launches": int(p.launches[i]), "total_ms": float(p.total_ms[i])}
+              for i, k in enumerate(PROFILE_KINDS)}
+    n = min(int(count.value), max_launches)
+    return totals, [(PROFILE_KINDS[kinds[i]] if 0 <= kinds[i] < len(PROFILE_KINDS) else str(kinds[i]),
+                     float(ms[i])) for i in range(n)]
 
 
 def bcf_sort_keys_static(keys_out, keys_in, *, descending=False, stream=None, kt=None):

@@ -90,6 +90,9 @@ SIGNATURES = {
     "bcf_sort_plan": (_i32, [_u64, _i32, _i32, ctypes.POINTER(BcfPlan)]),
     "bcf_profile_enable": (_i32, [_i32]),
     "bcf_profile_collect": (_i32, [ctypes.POINTER(BcfProfile)]),
+    "bcf_profile_collect_launches": (_i32, [ctypes.POINTER(BcfProfile), ctypes.POINTER(ctypes.c_int),
+                                            ctypes.POINTER(ctypes.c_float), _u32,
+                                            ctypes.POINTER(ctypes.c_uint32)]),
     "bcf_version": (ctypes.c_char_p, []),
     "bcf_sort_keys_static": (_i32, [_vp, _vp, _u64, _i32, ctypes.POINTER(BcfOpts), _vp]),
     "bcf_colored_prefix_sums": (_i32, [_vp, _vp, _vp, _u64, _u32, _i32, _i32, _vp, _sz, _vp]),

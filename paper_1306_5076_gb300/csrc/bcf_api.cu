@@ -1170,11 +1170,13 @@ bcf_status bcf_profile_enable(int on) {
   return BCF_OK;
 }
 
-bcf_status bcf_profile_collect(bcf_profile* out) {
-  if (!out) return BCF_EINVAL;
+bcf_status bcf_profile_collect_launches(bcf_profile* out, int* kinds, float* ms_out,
+                                        uint32_t max, uint32_t* count) {
+  if (!out || !count || (max > 0 && (!kinds || !ms_out))) return BCF_EINVAL;
   Profiler& P = prof();
   std::lock_guard<std::mutex> lk(P.mu);
   bcf_status st = BCF_OK;
+  uint32_t i = 0;
   for (auto& r : P.pending) {
     float ms = 0.f;
     if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess)
@@ -1183,11 +1185,22 @@ bcf_status bcf_profile_collect(bcf_profile* out) {
       out->launches[r.kind] += 1;
       out->total_ms[r.kind] += ms;
     }
+    if (i < max) {
+      kinds[i] = r.kind;
+      ms_out[i] = ms;
+    }
+    ++i;
     P.pool.push_back(r.a);
     P.pool.push_back(r.b);
   }
+  *count = i;
   P.pending.clear();
   return st;
+}
+
+bcf_status bcf_profile_collect(bcf_profile* out) {
+  uint32_t count = 0;
+  return bcf_profile_collect_launches(out, nullptr, nullptr, 0, &count);
 }
 
 const char* bcf_version(void) { return "bcfsort 0.1 (sm_103a)"; }

@@ -193,3 +193,20 @@ def test_committed_tuning_table_rows_are_valid(lib):
     with pytest.raises(bcf.BcfError):
         bcf.bcf_tuning_set([dict(op=0, key_bytes=8, has_vals=1, n_min=0, n_max=10, block_cfg=1,
                                  merge_cfg=0, seg_cfg=0)])  # no E = 32 for 64-bit pairs
+
+
+def test_profile_collect_launches_without_records(lib):
+    """Host-side only: nothing recorded gives zero launches; missing output
+    pointers are BCF_EINVAL."""
+    from paper_1306_5076_gb300 import _native
+
+    p = _native.BcfProfile()
+    count = ctypes.c_uint32(7)
+    kinds = (ctypes.c_int * 4)()
+    ms = (ctypes.c_float * 4)()
+    assert lib.bcf_profile_collect_launches(ctypes.byref(p), kinds, ms, 4, ctypes.byref(count)) == 0
+    assert count.value == 0 and sum(p.launches) == 0
+    assert lib.bcf_profile_collect_launches(ctypes.byref(p), None, None, 0, ctypes.byref(count)) == 0
+    assert lib.bcf_profile_collect_launches(None, kinds, ms, 4, ctypes.byref(count)) == 1
+    assert lib.bcf_profile_collect_launches(ctypes.byref(p), kinds, ms, 4, None) == 1
+    assert lib.bcf_profile_collect_launches(ctypes.byref(p), None, ms, 4, ctypes.byref(count)) == 1

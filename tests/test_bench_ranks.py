@@ -85,3 +85,16 @@ def test_reference_arm_under_torchrun_two_ranks(tmp_path):
     assert line["impl"] == "reference" and line["n_gpus"] == 2
     assert line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle"
     assert line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_per_pass_times_from_the_launch_list():
+    """Each merge pass's time, averaged over steps, from the library's launch list."""
+    one = [("block_sort", 2.0)] + [x for i in range(3)
+                                   for x in (("partition", 0.04), ("merge", 0.3 + 0.01 * i))]
+    two = [("block_sort", 4.0)] + [x for i in range(3)
+                                   for x in (("partition", 0.06), ("merge", 0.5 + 0.01 * i))]
+    got = bench.per_pass_ms(one + two)
+    assert got["steps"] == 2 and got["block_sort"] == pytest.approx(3.0)
+    assert got["partition"] == pytest.approx([0.05] * 3)
+    assert got["merge"] == pytest.approx([0.4, 0.41, 0.42])
+    assert bench.per_pass_ms([]) is None
