@@ -22,7 +22,9 @@
 //
 // The CTA that publishes a segment's merge pass first finds the exact
 // splitters of all its pieces (merge path, one warp per piece, 32-ary
-// search), so a piece starts with its two splits in hand.  Pieces read their
+// search), so a piece starts with its two splits in hand -- for passes of up
+// to 16 pieces per warp; a longer segment's pieces search their own, so that
+// one huge segment does not wait on a single CTA.  Pieces read their
 // windows straight from global memory (.cg loads: data written by other SMs
 // earlier in the same launch must not be served from a stale L1 line), then
 // run the same conflict-free bitonic merge as the merge pass kernel.
