@@ -251,16 +251,21 @@ __device__ __forceinline__ bool after(K kx, uint32_t ix, K ky, uint32_t iy) {
 // read once per thread into Frag::one.
 static __device__ uint32_t g_unit_multiplier = 1;
 
+// Work moved from the ALU pipe, which the sorting networks keep saturated, to
+// the FMA pipe (integer multiply-adds with a multiplier of Frag::one), in the
+// compare-exchanges of the stages that ask for it (measured: the BLK-layout
+// stages).  Both forms are exact in modular arithmetic.
+//   kFmaKeys  (32-bit keys, no payloads): the maximum is x * 1 + y - min(x, y)
+//             instead of a second min/max;
+//   kFmaPairs (32-bit keys with payloads): each of the three words is swapped
+//             as x + s * (y - x), y' = x + y - x' with s = 0 or 1, instead of
+//             two selects.
+enum : int { kFmaKeys = 1, kFmaPairs = 2 };
+
 // Compare-exchange registers a < b: ascending puts the smaller element in a.
-// fma_max (32-bit keys without payloads only): the maximum is computed as
-// x * one + y - min(x, y) with two integer multiply-adds, which run on the FMA
-// pipe, instead of a second min/max on the ALU pipe.  Exact in modular
-// arithmetic.  The block sort's networks keep the ALU pipe saturated, so moving
-// part of the work over shortens them (measured: the BLK-layout stages).
 template <typename K, bool PAIRS, int E>
-__device__ __forceinline__ void ce(Frag<K, PAIRS, E>& f, int a, int b, bool desc,
-                                   bool fma_max = false) {
-  if (!PAIRS && sizeof(K) == 4 && fma_max) {
+__device__ __forceinline__ void ce(Frag<K, PAIRS, E>& f, int a, int b, bool desc, int fma = 0) {
+  if (!PAIRS && sizeof(K) == 4 && (fma & kFmaKeys)) {
     const uint32_t x = static_cast<uint32_t>(f.k[a]), y = static_cast<uint32_t>(f.k[b]);
     const uint32_t lo = x < y ? x : y;
     uint32_t hi;
@@ -273,6 +278,25 @@ __device__ __forceinline__ void ce(Frag<K, PAIRS, E>& f, int a, int b, bool desc
     const K lo = x < y ? x : y, hi = x < y ? y : x;
     f.k[a] = desc ? hi : lo;
     f.k[b] = desc ? lo : hi;
+  } else if (sizeof(K) == 4 && (fma & kFmaPairs)) {
+    const bool sw = after(f.k[a], f.ix[a], f.k[b], f.ix[b]) != desc;
+    const uint32_t s = sw ? f.one : 0u, one = f.one, neg = 0u - f.one;
+    const auto swap_word = [&](uint32_t& xr, uint32_t& yr) {
+      const uint32_t x = xr, y = yr;
+      uint32_t d, nx, t, ny;
+      asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(x), "r"(neg), "r"(y));    // y - x
+      asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(nx) : "r"(s), "r"(d), "r"(x));     // x + s(y - x)
+      asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(t) : "r"(x), "r"(one), "r"(y));    // x + y
+      asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(ny) : "r"(nx), "r"(neg), "r"(t));  // x + y - x'
+      xr = nx;
+      yr = ny;
+    };
+    uint32_t ka = static_cast<uint32_t>(f.k[a]), kb = static_cast<uint32_t>(f.k[b]);
+    swap_word(ka, kb);
+    f.k[a] = static_cast<K>(ka);
+    f.k[b] = static_cast<K>(kb);
+    swap_word(f.ix[a], f.ix[b]);
+    swap_word(f.v[a], f.v[b]);
   } else {
     const bool sw = after(f.k[a], f.ix[a], f.k[b], f.ix[b]) != desc;
     const K ka = f.k[a], kb = f.k[b];
@@ -411,8 +435,8 @@ __device__ __forceinline__ void relayout(Frag<K, PAIRS, E>& f, uint32_t* sm) {
 }
 
 // Ascending half-cleaner stages on k bits HI down to LO, all inside layout
-// L's register window (FMA: the compare-exchanges take the FMA-pipe maximum).
-template <int L, int HI, int LO, int NT, bool FMA = false, typename K, bool PAIRS, int E>
+// L's register window (FMA: the kFma* forms the compare-exchanges use).
+template <int L, int HI, int LO, int NT, int FMA = 0, typename K, bool PAIRS, int E>
 __device__ __forceinline__ void stages(Frag<K, PAIRS, E>& f) {
   using G = Geo<E, NT>;
 #pragma unroll
@@ -428,8 +452,8 @@ __device__ __forceinline__ void stages(Frag<K, PAIRS, E>& f) {
 // ascending result in BLK layout.  Stages on bits t-1 .. 0 in STR, MID, BLK.
 // Both layout changes reuse one buffer (a second buffer would save two
 // barriers but halves the CTAs per SM, which was measured slower).
-// FMA_BLK: the BLK stages take the FMA-pipe maximum (Frag::one must be set).
-template <int NT, bool FMA_BLK = false, typename K, bool PAIRS, int E>
+// FMA_BLK: the kFma* forms of the BLK stages (Frag::one must be set).
+template <int NT, int FMA_BLK = 0, typename K, bool PAIRS, int E>
 __device__ __forceinline__ void bitonic_merge_str(Frag<K, PAIRS, E>& f, uint32_t* sm) {
   using G = Geo<E, NT>;
   constexpr int r = G::r, t = G::t;
@@ -447,7 +471,7 @@ __device__ __forceinline__ void bitonic_merge_str(Frag<K, PAIRS, E>& f, uint32_t
 // One level J of the bitonic sort (r < J <= t): the tile's blocks of 2^(J-1)
 // are ascending; merge pairs of them into ascending blocks of 2^J.  Enters and
 // leaves in BLK layout.
-template <int J, int NT, bool FMA_BLK, typename K, bool PAIRS, int E>
+template <int J, int NT, int FMA_BLK, typename K, bool PAIRS, int E>
 __device__ __forceinline__ void sort_level(Frag<K, PAIRS, E>& f, uint32_t* sm) {
   using G = Geo<E, NT>;
   constexpr int r = G::r, t = G::t, top = J - 1;
@@ -469,7 +493,7 @@ __device__ __forceinline__ void sort_level(Frag<K, PAIRS, E>& f, uint32_t* sm) {
   stages<kBLK, r - 1, 0, NT, FMA_BLK>(f);
 }
 
-template <int J, int NT, bool FMA_BLK, typename K, bool PAIRS, int E,
+template <int J, int NT, int FMA_BLK, typename K, bool PAIRS, int E,
           bool DONE = (J > ilog2(E * NT))>
 struct SortLevels {
   __device__ static __forceinline__ void run(Frag<K, PAIRS, E>& f, uint32_t* sm) {
@@ -477,15 +501,15 @@ struct SortLevels {
     SortLevels<J + 1, NT, FMA_BLK, K, PAIRS, E>::run(f, sm);
   }
 };
-template <int J, int NT, bool FMA_BLK, typename K, bool PAIRS, int E>
+template <int J, int NT, int FMA_BLK, typename K, bool PAIRS, int E>
 struct SortLevels<J, NT, FMA_BLK, K, PAIRS, E, true> {
   __device__ static __forceinline__ void run(Frag<K, PAIRS, E>&, uint32_t*) {}
 };
 
 // Sort of the whole CTA tile: each thread's registers with Batcher's network
 // (levels 1..r), then levels r+1..t; ascending result in BLK layout.
-// FMA_BLK: the BLK stages take the FMA-pipe maximum (Frag::one must be set).
-template <int NT, bool FMA_BLK = false, typename K, bool PAIRS, int E>
+// FMA_BLK: the kFma* forms of the BLK stages (Frag::one must be set).
+template <int NT, int FMA_BLK = 0, typename K, bool PAIRS, int E>
 __device__ __forceinline__ void block_sort_tile(Frag<K, PAIRS, E>& f, uint32_t* sm) {
   thread_sort(f, false);
   SortLevels<ilog2(E) + 1, NT, FMA_BLK, K, PAIRS, E>::run(f, sm);

@@ -362,8 +362,8 @@ __global__ void __launch_bounds__(NT) merge_kernel(const MergeArgs a,
     }
   }
 
-  f.one = g_unit_multiplier;  // FMA-pipe maxima in the BLK stages (keys-only 32-bit)
-  bitonic_merge_str<NT, true>(f, reinterpret_cast<uint32_t*>(body));
+  f.one = g_unit_multiplier;  // FMA-pipe forms in the BLK stages (32-bit keys)
+  bitonic_merge_str<NT, kFmaKeys | kFmaPairs>(f, reinterpret_cast<uint32_t*>(body));
   // samples of the output for the next pass's merge-path search: the keys at
   // array positions that are multiples of S, still in mapped order (a pass
   // with a successor writes no unmapped keys)
