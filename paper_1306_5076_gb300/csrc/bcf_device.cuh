@@ -259,8 +259,10 @@ static __device__ uint32_t g_unit_multiplier = 1;
 //             instead of a second min/max;
 //   kFmaPairs (32-bit keys with payloads): each of the three words is swapped
 //             as x + s * (y - x), y' = x + y - x' with s = 0 or 1, instead of
-//             two selects.
-enum : int { kFmaKeys = 1, kFmaPairs = 2 };
+//             two selects;
+//   kFmaKeys64 (64-bit keys, no payloads): the same swap of the two halves
+//             after one 64-bit comparison, instead of four selects.
+enum : int { kFmaKeys = 1, kFmaPairs = 2, kFmaKeys64 = 4 };
 
 // Compare-exchange registers a < b: ascending puts the smaller element in a.
 template <typename K, bool PAIRS, int E>
@@ -273,6 +275,24 @@ __device__ __forceinline__ void ce(Frag<K, PAIRS, E>& f, int a, int b, bool desc
     asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(hi) : "r"(lo), "r"(0u - f.one), "r"(hi));
     f.k[a] = static_cast<K>(desc ? hi : lo);
     f.k[b] = static_cast<K>(desc ? lo : hi);
+  } else if (!PAIRS && sizeof(K) == 8 && (fma & kFmaKeys64)) {
+    const uint64_t x = static_cast<uint64_t>(f.k[a]), y = static_cast<uint64_t>(f.k[b]);
+    const bool sw = (x > y) != desc;
+    const uint32_t s = sw ? f.one : 0u, one = f.one, neg = 0u - f.one;
+    uint32_t xw[2] = {static_cast<uint32_t>(x), static_cast<uint32_t>(x >> 32)};
+    uint32_t yw[2] = {static_cast<uint32_t>(y), static_cast<uint32_t>(y >> 32)};
+#pragma unroll
+    for (int w = 0; w < 2; ++w) {
+      uint32_t d, nx, t, ny;
+      asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(xw[w]), "r"(neg), "r"(yw[w]));
+      asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(nx) : "r"(s), "r"(d), "r"(xw[w]));
+      asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(t) : "r"(xw[w]), "r"(one), "r"(yw[w]));
+      asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(ny) : "r"(nx), "r"(neg), "r"(t));
+      xw[w] = nx;
+      yw[w] = ny;
+    }
+    f.k[a] = static_cast<K>(xw[0] | (static_cast<uint64_t>(xw[1]) << 32));
+    f.k[b] = static_cast<K>(yw[0] | (static_cast<uint64_t>(yw[1]) << 32));
   } else if constexpr (!PAIRS) {
     const K x = f.k[a], y = f.k[b];
     const K lo = x < y ? x : y, hi = x < y ? y : x;
