@@ -656,7 +656,10 @@ def run_gpu(args, world, rank, local, pg):
         step()
     torch.cuda.synchronize()
 
-    # ---- device-resident timed region
+    # ---- device-resident timed region (Python's garbage collector paused: the
+    # host loop enqueues every step, and a collection pause would idle the GPU)
+    gc.collect()
+    gc.disable()
     clocks = ClockSampler(local)
     bcf.bcf_profile_collect()  # drop anything pending
     bcf.bcf_profile_enable(True)
@@ -676,6 +679,7 @@ def run_gpu(args, world, rank, local, pg):
     clk = clocks.stop(m0, m1)
     bcf.bcf_profile_enable(False)
     prof, launch_list = bcf.bcf_profile_collect_launches(64 * (args.steps + 1) + 64)
+    gc.enable()
     ms = max_over_ranks(torch, pg, e0.elapsed_time(e1) / args.steps, dev)
     passes = per_pass_ms(launch_list)
 
@@ -715,6 +719,8 @@ def run_gpu(args, world, rank, local, pg):
     # host-side stall in one region -- the host loop issues every step -- does
     # not decide the number), and all three are listed
     regions = []
+    gc.collect()
+    gc.disable()
     for _ in range(3):
         h0 = torch.cuda.Event(enable_timing=True)
         h1 = torch.cuda.Event(enable_timing=True)
@@ -728,6 +734,7 @@ def run_gpu(args, world, rank, local, pg):
         h1.record(stream)
         torch.cuda.synchronize()
         regions.append(h0.elapsed_time(h1) / e2e_steps)
+    gc.enable()
     e2e_ms = max_over_ranks(torch, pg, statistics.median(regions), dev)
     # every stream's last result equals the device-timed sort's output
     ok_e2e = all(bool(torch.equal(h, ko.cpu())) for h in houts)
