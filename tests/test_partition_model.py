@@ -76,3 +76,40 @@ def test_runs_at_any_offsets_window(S):
             sa = merge_path(As, Bs, min(D, len(As) + len(Bs)))
             c = cA + sa * S
             assert c - S <= i <= c + S, (trial, d, i, c)
+
+
+def test_irregular_merge_writes_every_sample_once():
+    """The merge kernel's sample writes for a pass of given runs
+    (csrc/bcf_merge.cu, merge_kernel with IRREG): pieces are the Tm-aligned
+    output tiles clipped to each pair's range; thread tid of a piece writes the
+    sample of array position out0 + tid*E when that position is a multiple of
+    S and lies in the piece's slots [front, front + count).  Every multiple
+    of S in the merged span must be written exactly once."""
+    S, E, NT = 256, 16, 128
+    Tm = E * NT
+    r = np.random.default_rng(3)
+    for trial in range(60):
+        k = int(r.integers(1, 9))
+        lens = r.integers(0, 3 * Tm, size=k)
+        lo = int(r.integers(0, 5000))
+        offs = np.concatenate([[lo], lo + np.cumsum(lens)])
+        runs = [(int(offs[i]), int(lens[i])) for i in range(k)]
+        # one pass: pair adjacent runs (an odd last run pairs with an empty one)
+        written = []
+        for q in range(0, len(runs), 2):
+            off = runs[q][0]
+            length = runs[q][1] + (runs[q + 1][1] if q + 1 < len(runs) else 0)
+            if length == 0:
+                continue
+            end = off + length
+            for g in range(off // Tm, (end - 1) // Tm + 1):
+                out0 = g * Tm
+                start, stop = max(off, out0), min(end, out0 + Tm)
+                front, count = start - out0, stop - start
+                for tid in range(NT):
+                    s0 = tid * E
+                    if (out0 + s0) % S == 0 and front <= s0 < front + count:
+                        written.append(out0 + s0)
+        hi = int(offs[-1])
+        expect = list(range((lo + S - 1) // S * S, hi, S))
+        assert sorted(written) == expect, trial
