@@ -164,7 +164,11 @@ bcf_status bcf_merge_runs(void* keys_out, uint32_t* vals_out, const void* keys_i
  * memory, nseg+1 non-decreasing uint64 entries with seg_offsets_dev[nseg] ==
  * n_total.  vals may be NULL (both or neither).  Offsets are read on the
  * device; a decreasing offset is not detected on the host and yields an
- * unspecified (but memory-safe) result.
+ * unspecified (but memory-safe) result.  n_total may exceed 2^32 (and one
+ * segment may be that long); nseg must be below 2^32 (BCF_EUNSUPPORTED
+ * otherwise).  The call makes two launches (a plan and one persistent wave)
+ * and can be captured in a CUDA graph; ws is sized by
+ * bcf_workspace_bytes(BCF_OP_SEGMENTED, n_total, nseg, kt, has_vals).
  */
 bcf_status bcf_segmented_sort(void* keys_out, uint32_t* vals_out, const void* keys_in,
                               const uint32_t* vals_in, const uint64_t* seg_offsets_dev,
