@@ -188,6 +188,16 @@ const char* bcf_status_string(bcf_status status);
  */
 bcf_status bcf_last_device_error(cudaStream_t stream);
 
+/*
+ * Self-test of the failure path: one thread waits, bounded by limit_us
+ * microseconds of the GPU's global timer, for a device flag that nothing ever
+ * sets -- the same bounded wait the library's kernels use -- then records a
+ * wait that ran out in the device error word and exits.  The caller then sees
+ * BCF_ETIMEOUT from bcf_last_device_error(stream), and the context stays
+ * usable.  BCF_EINVAL for limit_us == 0 or above 2,000,000.
+ */
+bcf_status bcf_selftest_bounded_wait(uint32_t limit_us, cudaStream_t stream);
+
 /* ---- plan introspection and building blocks ------------------------------ */
 
 typedef struct {

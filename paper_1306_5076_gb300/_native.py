@@ -90,6 +90,7 @@ SIGNATURES = {
     "bcf_sort_plan": (_i32, [_u64, _i32, _i32, ctypes.POINTER(BcfPlan)]),
     "bcf_profile_enable": (_i32, [_i32]),
     "bcf_profile_collect": (_i32, [ctypes.POINTER(BcfProfile)]),
+    "bcf_selftest_bounded_wait": (_i32, [_u32, _vp]),
     "bcf_profile_collect_launches": (_i32, [ctypes.POINTER(BcfProfile), ctypes.POINTER(ctypes.c_int),
                                             ctypes.POINTER(ctypes.c_float), _u32,
                                             ctypes.POINTER(ctypes.c_uint32)]),

@@ -1150,6 +1150,35 @@ bcf_status bcf_last_device_error(cudaStream_t stream) {
   return BCF_OK;
 }
 
+__device__ uint32_t g_never_set;  // a flag no code writes: the self-test's wait runs out
+
+static __device__ __forceinline__ uint64_t now_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+static __global__ void bounded_wait_selftest_kernel(uint64_t limit_ns, uint32_t* err) {
+  if (threadIdx.x != 0) return;
+  const volatile uint32_t* flag = &g_never_set;
+  const uint64_t t0 = now_ns();
+  while (*flag == 0) {
+    if (now_ns() - t0 > limit_ns) {
+      atomicOr(err, kErrSelftestTimeout);
+      return;
+    }
+    __nanosleep(1000);
+  }
+}
+
+bcf_status bcf_selftest_bounded_wait(uint32_t limit_us, cudaStream_t stream) {
+  if (limit_us == 0 || limit_us > 2000000u) return BCF_EINVAL;
+  uint32_t* err = error_word_ptr();
+  if (!err) return BCF_ECUDA;
+  bounded_wait_selftest_kernel<<<1, 32, 0, stream>>>(static_cast<uint64_t>(limit_us) * 1000u, err);
+  return cudaGetLastError() == cudaSuccess ? BCF_OK : BCF_ECUDA;
+}
+
 bcf_status bcf_sort_plan(uint64_t n, bcf_dtype kt, int has_vals, bcf_plan* out) {
   if (!out || !dtype_ok(kt)) return BCF_EINVAL;
   if (is16(kt)) kt = wide_of(kt);  // the passes run on the widened keys

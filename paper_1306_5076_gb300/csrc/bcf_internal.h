@@ -129,6 +129,7 @@ constexpr int kCpsTile = kCpsThreads * kCpsPerThread * kCpsSteps;
 constexpr uint32_t kCpsMaxColors = 64;
 constexpr uint32_t kErrBadColor = 8u;          // device error bit: a color >= d
 constexpr uint32_t kErrLookbackTimeout = 16u;  // device error bit: look-back wait ran out
+constexpr uint32_t kErrSelftestTimeout = 32u;  // device error bit: the self-test's wait ran out
 struct CpsArgs {
   uint32_t* out;
   const uint32_t* values;

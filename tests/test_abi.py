@@ -210,3 +210,8 @@ def test_profile_collect_launches_without_records(lib):
     assert lib.bcf_profile_collect_launches(None, kinds, ms, 4, ctypes.byref(count)) == 1
     assert lib.bcf_profile_collect_launches(ctypes.byref(p), kinds, ms, 4, None) == 1
     assert lib.bcf_profile_collect_launches(ctypes.byref(p), None, ms, 4, ctypes.byref(count)) == 1
+
+
+def test_selftest_wait_rejects_bad_limits_before_any_launch(lib):
+    assert lib.bcf_selftest_bounded_wait(0, None) == 1
+    assert lib.bcf_selftest_bounded_wait(2000001, None) == 1
