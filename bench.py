@@ -1,7 +1,8 @@
 """Benchmark: GB300 bank-conflict-free merge sort, one JSON line on rank 0.
 
 Workload (one "step" = one full sort through the C ABI): 2^28 uint32 keys,
-uniform over [0, 2^32), seed 10 (the large-sort workload family's seed rule),
+uniform over [0, 2^32), seed 28 (the large-sort workload family's seed rule,
+1000 * distribution + 10 * key type + log2 n),
 ascending, keys only -- the configuration the >= 60 %-of-HBM-roofline-per-merge-
 pass target is stated on.  Inputs are resident in HBM before the timed region;
 1 GiB of keys is far larger than the 129 MB L2, so no flush is needed between
@@ -240,8 +241,9 @@ def run_reference(args, world, rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_t * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic",
-        "config": {"workload": "sort of uniform u32 keys, keys only, ascending", "n": N,
-                   "key": "u32", "parallelism": "host threads"},
+        "config": {"workload": f"sort of 2^{SAMPLE_LOG2N} uniform u32 keys (a bounded sample "
+                               f"of the 2^{LOG2N}-key workload), keys only, ascending",
+                   "n": n, "key": "u32", "parallelism": "host threads"},
         "cpu_baseline": {"value": value, "unit": "keys/s", "cores": cores, "kind": "oracle",
                          "sample": f"2^{SAMPLE_LOG2N} keys of the same workload per step "
                                    f"(stable merge sort, C, {cores} threads)"},
@@ -585,7 +587,9 @@ def profile_case(args):
     few launches): 'cps' = colored prefix sums of 2^26 elements, 16 colors,
     both layouts, two launches each; 'pb' = pivot-bucket sort of 2^26
     16-distinct u32 keys, twice; 'seg' = segmented sort of 5,000 segments
-    with sizes log-uniform over [1, 2^18] (about 1.05e8 u32 keys), twice."""
+    with sizes log-uniform over [1, 2^18] (about 1.05e8 u32 keys), twice;
+    'pairs' / 'u64' / 'u64p' = sort of 2^26 uniform keys, twice: u32 keys
+    with u32 payloads, u64 keys, u64 keys with u32 payloads."""
     import numpy as np
     import torch
 
@@ -594,8 +598,23 @@ def profile_case(args):
 
     dev = torch.device("cuda", 0)
     bcf._native.load()
+    bcf.bcf_profile_set_smem_floor(args.smem_floor)
     n = 1 << 26
-    if args.profile_case == "cps":
+    if args.profile_case in ("pairs", "u64", "u64p"):
+        kname = "u32" if args.profile_case == "pairs" else "u64"
+        keys = workloads.keys("uniform", kname, n)
+        kd = torch.from_numpy(keys.view(np.int32 if kname == "u32" else np.int64)).to(dev)
+        ko = torch.empty_like(kd)
+        kt = bcf.BCF_U32 if kname == "u32" else bcf.BCF_U64
+        with_vals = args.profile_case != "u64"
+        vd = torch.arange(n, dtype=torch.int32, device=dev) if with_vals else None
+        vo = torch.empty_like(vd) if with_vals else None
+        for _ in range(2):
+            if with_vals:
+                bcf.bcf_sort_pairs(ko, vo, kd, vd, kt=kt)
+            else:
+                bcf.bcf_sort_keys(ko, kd, kt=kt)
+    elif args.profile_case == "cps":
         vals, cols = workloads.colored_elements(n, 16, seed=26)
         vd = torch.from_numpy(vals.view(np.int32)).to(dev)
         cd = torch.from_numpy(cols).to(dev)
@@ -634,6 +653,7 @@ def run_gpu(args, world, rank, local, pg):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     bcf._native.load()
+    bcf.bcf_profile_set_smem_floor(args.smem_floor)
     seed = workloads.large_sort_seed("uniform", "u32", N) + 7919 * rank
     keys_np = workloads.keys("uniform", "u32", N, seed=seed)
     host_in = torch.from_numpy(keys_np.view(np.int32)).pin_memory()
@@ -852,13 +872,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile-case", choices=["cps", "pb", "seg"],
+    ap.add_argument("--profile-case", choices=["cps", "pb", "seg", "pairs", "u64", "u64p"],
                     help="run only a small case of one path (for ncu captures) and exit")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the other key types, the colored prefix sums and the "
                          "pivot-bucket comparison")
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="length of the served-vs-plain request trace (0: skip)")
+    ap.add_argument("--smem-floor", type=int, default=0,
+                    help="profiling only: minimum dynamic shared memory (bytes) of the block "
+                         "sort and merge launches, e.g. 200000 for one CTA per SM")
     ap.add_argument("--log2n", type=int, default=LOG2N,
                     help="keys = 2^log2n (default 28, the benchmark workload; smaller values "
                          "are for ncu captures)")

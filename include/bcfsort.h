@@ -181,6 +181,11 @@ const char* bcf_status_string(bcf_status status);
 
 /*
  * Synchronise `stream`, then read and clear the current device's error word.
+ * After BCF_ETIMEOUT the outputs of the calls that ran since the last check are
+ * undefined.  When the wait that ran out was a merge pass's wait for its bulk
+ * copies, copies still in flight when the CTA gave up may land in shared
+ * memory that a later CTA on that SM already uses, so the results of OTHER
+ * launches that ran on the device at the same time are undefined as well.
  * Returns BCF_ETIMEOUT if a kernel's bounded wait ran out since the last call,
  * BCF_EINVAL if the only error seen was a color >= d in
  * bcf_colored_prefix_sums, BCF_ECUDA if the synchronisation failed, else
@@ -197,6 +202,33 @@ bcf_status bcf_last_device_error(cudaStream_t stream);
  * usable.  BCF_EINVAL for limit_us == 0 or above 2,000,000.
  */
 bcf_status bcf_selftest_bounded_wait(uint32_t limit_us, cudaStream_t stream);
+
+/*
+ * Limit of every device-side bounded wait the library's kernels make (the
+ * merge pass's wait for its bulk copies, the segmented sort's wait for a work
+ * item to be published, the colored prefix sums' look-back), in microseconds
+ * of the GPU's global timer.  0 restores the default of 2,000,000 (2 s);
+ * BCF_EINVAL above 60,000,000.  Process-wide; a launch uses the value set when
+ * it is enqueued.  No wait of a correct run comes near the default: the limit
+ * only bounds how long a kernel can hang before it reports BCF_ETIMEOUT.
+ * bcf_wait_limit_us() returns the current value.
+ */
+bcf_status bcf_set_wait_limit_us(uint32_t limit_us);
+uint32_t bcf_wait_limit_us(void);
+
+/*
+ * Self-test of the segmented sort's own bounded wait.  One CTA of the real
+ * segmented-sort worker (32-bit keys) runs on a work queue that announces one
+ * item whose slot the host set-up leaves unpublished, so the worker's wait for
+ * it runs out after the current wait limit (bcf_set_wait_limit_us).  The
+ * worker then records the timeout in the device error word and exits without
+ * reading or writing any keys; bcf_last_device_error(stream) returns
+ * BCF_ETIMEOUT and the context stays usable.
+ *   ws  device scratch of at least 512 bytes, 256-byte aligned (BCF_ENOMEM if
+ *       smaller or NULL, BCF_EINVAL if misaligned); its contents are
+ *       overwritten.
+ */
+bcf_status bcf_selftest_segmented_wait(void* ws, size_t ws_bytes, cudaStream_t stream);
 
 /* ---- plan introspection and building blocks ------------------------------ */
 
@@ -236,6 +268,16 @@ bcf_status bcf_profile_collect(bcf_profile* out);
  */
 bcf_status bcf_profile_collect_launches(bcf_profile* out, int* kinds, float* ms, uint32_t max,
                                         uint32_t* count);
+
+/*
+ * Profiling control: launch the block sort and the merge pass with at least
+ * `bytes` of dynamic shared memory (0, the default, launches them as built).
+ * A floor above half an SM's shared memory leaves one CTA per SM, which
+ * isolates each CTA's own shared-memory traffic from its neighbours' in
+ * hardware counters.  Results never change; only speed does.  BCF_EINVAL
+ * above 232,448 bytes (227 KB, the per-CTA maximum).  Process-wide.
+ */
+bcf_status bcf_profile_set_smem_floor(uint32_t bytes);
 
 /* Version string of the library. */
 const char* bcf_version(void);
@@ -424,8 +466,10 @@ bcf_status bcf_server_destroy(bcf_server* s);
 
 /* The server's arena allocator on its own: first fit over [0, bytes) with a
  * coalescing free list, 256-byte granules.  Host bookkeeping only (no device
- * memory), exported for testing; bcf_arena_free takes back exactly a range
- * that bcf_arena_alloc returned. */
+ * memory), exported for testing.  bcf_arena_free takes back exactly a live
+ * range that bcf_arena_alloc returned (offset and the requested size); any
+ * other range -- a double free, a wrong offset or size -- is BCF_EINVAL and
+ * changes nothing. */
 typedef struct bcf_arena bcf_arena;
 bcf_status bcf_arena_create(uint64_t bytes, bcf_arena** out);
 bcf_status bcf_arena_alloc(bcf_arena* a, uint64_t bytes, uint64_t* offset);
@@ -441,16 +485,17 @@ bcf_status bcf_arena_destroy(bcf_arena* a);
  *
  * Some callers cannot call cudaMalloc: a framework or plugin host that owns
  * every device allocation and hands a plugin only its input and output
- * buffers, code running while another thread captures a CUDA graph in global
- * capture mode (cudaMalloc is an error there), or a latency-critical loop that
- * must not take cudaMalloc's implicit device synchronisation.  They pass only
- * keys_in / keys_out; the merge passes' scratch (ping-pong copy and split
- * array) lives in a device array inside the library.
+ * buffers, a process whose device memory is carved up by an external pool it
+ * must not go around, or a latency-critical loop that must not take
+ * cudaMalloc's implicit device synchronisation.  They pass only keys_in /
+ * keys_out; the merge passes' scratch (ping-pong copy and split array) lives
+ * in a device array inside the library.
  *
  *   - n <= BCF_STATIC_MAX_KEYS, else BCF_EUNSUPPORTED before any launch; keys
- *     only; 16-bit keys and opts->algorithm other than BCF_ALGO_MERGE are not
- *     available here (BCF_EUNSUPPORTED, resp. the merge path is taken);
- *     otherwise the arguments, results and errors of bcf_sort_keys.
+ *     only; 16-bit keys are not available here (BCF_EUNSUPPORTED);
+ *     BCF_ALGO_PIVOT_BUCKETS takes the merge path (same result); otherwise
+ *     the arguments, results and errors of bcf_sort_keys (an unknown
+ *     opts->algorithm is BCF_EINVAL).
  *   - The array (about 8 MiB) is held by every GPU that loads the library until
  *     the process exits.  The call allocates nothing.
  *   - All calls share the array: calls whose GPU work overlaps in time (other

@@ -6,8 +6,10 @@ options) and turn non-OK status codes into :class:`BcfError`.  Every step of
 the sort runs in the CUDA kernels of ``libbcfsort.so``; there is no CPU or
 library fallback.  PyTorch supplies device memory and streams only.
 
-Keys: torch.uint32 / torch.int32 (bits read as u32), torch.uint64 /
-torch.int64 (bits read as u64), torch.float32 (IEEE 754 totalOrder).
+Keys (the code ``key_dtype_of`` picks from the tensor's dtype; pass ``kt`` to
+read a tensor's bits as another type): torch.uint16 / uint32 / uint64 in
+natural order, torch.int16 / int32 / int64 in two's-complement order,
+torch.float32 / float64 under IEEE 754 totalOrder.
 Values: 32-bit tensors (torch.int32 / torch.uint32).
 """
 from __future__ import annotations
@@ -29,7 +31,8 @@ __all__ = [
     "BCF_OP_SORT", "BCF_OP_MERGE", "BCF_OP_SEGMENTED", "BCF_OP_CPS",
     "bcf_colored_prefix_sums", "BCF_CPS_BANKED", "BCF_CPS_ROWS", "BCF_OP_SORT_PB",
     "BCF_ALGO_MERGE", "BCF_ALGO_PIVOT_BUCKETS", "bcf_sort_keys_host", "bcf_sort_pairs_host",
-    "bcf_sort_pairs_wide",
+    "bcf_sort_pairs_wide", "bcf_set_wait_limit_us", "bcf_wait_limit_us",
+    "bcf_profile_set_smem_floor",
 ]
 
 
@@ -262,6 +265,21 @@ def bcf_sort_plan(n: int, kt: int, has_vals: bool) -> dict:
     _check(_native.load().bcf_sort_plan(n, kt, int(bool(has_vals)), ctypes.byref(p)),
            "bcf_sort_plan")
     return {f: getattr(p, f) for f, _ in p._fields_}
+
+
+def bcf_set_wait_limit_us(limit_us: int) -> None:
+    """Limit of every device-side bounded wait, in microseconds (0: 2 s)."""
+    _check(_native.load().bcf_set_wait_limit_us(int(limit_us)), "bcf_set_wait_limit_us")
+
+
+def bcf_wait_limit_us() -> int:
+    return int(_native.load().bcf_wait_limit_us())
+
+
+def bcf_profile_set_smem_floor(nbytes: int) -> None:
+    """Profiling control: minimum dynamic shared memory of the block sort and
+    merge-pass launches (0: as built); limits the CTAs sharing an SM."""
+    _check(_native.load().bcf_profile_set_smem_floor(int(nbytes)), "bcf_profile_set_smem_floor")
 
 
 def bcf_profile_enable(on: bool = True) -> None:

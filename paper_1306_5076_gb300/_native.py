@@ -91,6 +91,10 @@ SIGNATURES = {
     "bcf_profile_enable": (_i32, [_i32]),
     "bcf_profile_collect": (_i32, [ctypes.POINTER(BcfProfile)]),
     "bcf_selftest_bounded_wait": (_i32, [_u32, _vp]),
+    "bcf_set_wait_limit_us": (_i32, [_u32]),
+    "bcf_wait_limit_us": (_u32, []),
+    "bcf_selftest_segmented_wait": (_i32, [_vp, _sz, _vp]),
+    "bcf_profile_set_smem_floor": (_i32, [_u32]),
     "bcf_profile_collect_launches": (_i32, [ctypes.POINTER(BcfProfile), ctypes.POINTER(ctypes.c_int),
                                             ctypes.POINTER(ctypes.c_float), _u32,
                                             ctypes.POINTER(ctypes.c_uint32)]),

@@ -12,6 +12,7 @@
 #include <dlfcn.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -26,10 +27,14 @@ namespace bcf {
 
 __device__ uint32_t g_error_word;  // set by bounded waits that ran out
 
+// Run-time settings read by the launch wrappers (bcf_internal.h).
+static std::atomic<uint64_t> g_wait_limit_ns{kDefaultWaitLimitNs};
+static std::atomic<uint32_t> g_smem_floor{0};
+uint64_t wait_limit_ns() { return g_wait_limit_ns.load(std::memory_order_relaxed); }
+uint32_t smem_floor_bytes() { return g_smem_floor.load(std::memory_order_relaxed); }
+
 namespace {
 
-constexpr size_t kAlign = 256;
-constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 bool dtype_ok(int kt) { return kt >= BCF_U32 && kt <= BCF_I16; }
 bool is16(int kt) { return kt == BCF_U16 || kt == BCF_I16; }
@@ -150,28 +155,6 @@ Plan make_plan(uint64_t n, int kb, bool pairs, int op = BCF_OP_SORT) {
     ++p.passes;
   }
   return p;
-}
-
-// smallest merge tile over all configurations: bounds the split arrays
-constexpr uint64_t kMinMergeTile = 2048;
-
-struct WsLayout {
-  size_t splits, samples0, samples1, keys, vals, total;
-};
-
-// [header | splits | samples of the output buffer | samples of the workspace
-// copy | keys copy | values copy]
-WsLayout ws_layout(uint64_t n, uint64_t runs_or_segs, int kb, bool pairs) {
-  WsLayout w;
-  const uint64_t items = (n + kMinMergeTile - 1) / kMinMergeTile + runs_or_segs + 2;
-  const uint64_t nsamp = n / kSampleStride + 2;
-  w.splits = kAlign;
-  w.samples0 = align_up(w.splits + items * sizeof(uint64_t), kAlign);
-  w.samples1 = align_up(w.samples0 + nsamp * kb, kAlign);
-  w.keys = align_up(w.samples1 + nsamp * kb, kAlign);
-  w.vals = align_up(w.keys + n * kb, kAlign);
-  w.total = align_up(w.vals + (pairs ? n * 4 : 0), kAlign);
-  return w;
 }
 
 // Segmented sort workspace: counters, per-segment state, the work queue and
@@ -1177,6 +1160,31 @@ bcf_status bcf_selftest_bounded_wait(uint32_t limit_us, cudaStream_t stream) {
   if (!err) return BCF_ECUDA;
   bounded_wait_selftest_kernel<<<1, 32, 0, stream>>>(static_cast<uint64_t>(limit_us) * 1000u, err);
   return cudaGetLastError() == cudaSuccess ? BCF_OK : BCF_ECUDA;
+}
+
+bcf_status bcf_set_wait_limit_us(uint32_t limit_us) {
+  if (limit_us > kMaxWaitLimitUs) return BCF_EINVAL;
+  g_wait_limit_ns.store(limit_us == 0 ? kDefaultWaitLimitNs : uint64_t(limit_us) * 1000u,
+                        std::memory_order_relaxed);
+  return BCF_OK;
+}
+
+uint32_t bcf_wait_limit_us(void) {
+  return static_cast<uint32_t>(g_wait_limit_ns.load(std::memory_order_relaxed) / 1000u);
+}
+
+bcf_status bcf_selftest_segmented_wait(void* ws, size_t ws_bytes, cudaStream_t stream) {
+  if (ws_bytes < kSegSelftestBytes || !ws) return BCF_ENOMEM;
+  if ((reinterpret_cast<uintptr_t>(ws) & 255u) != 0) return BCF_EINVAL;
+  uint32_t* err = error_word_ptr();
+  if (!err) return BCF_ECUDA;
+  return from_cuda(launch_segmented_wait_selftest(ws, wait_limit_ns(), err, stream));
+}
+
+bcf_status bcf_profile_set_smem_floor(uint32_t bytes) {
+  if (bytes > kMaxSmemFloor) return BCF_EINVAL;
+  g_smem_floor.store(bytes, std::memory_order_relaxed);
+  return BCF_OK;
 }
 
 bcf_status bcf_sort_plan(uint64_t n, bcf_dtype kt, int has_vals, bcf_plan* out) {

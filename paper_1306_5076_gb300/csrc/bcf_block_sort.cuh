@@ -136,7 +136,8 @@ template <typename K, bool PAIRS, int E, int NT>
 static cudaError_t launch_bs(const BlockSortArgs& a, cudaStream_t s) {
   constexpr int T = E * NT;
   constexpr int W = Frag<K, PAIRS, E>::W;
-  const size_t smem = static_cast<size_t>(W) * padded_words(T) * sizeof(uint32_t);
+  const size_t need = static_cast<size_t>(W) * padded_words(T) * sizeof(uint32_t);
+  const size_t smem = need > smem_floor_bytes() ? need : smem_floor_bytes();
   const uint64_t tiles = (a.n + T - 1) / T;
   if (tiles == 0) return cudaSuccess;
   const bool map = (a.mode_in | a.mode_out) != 0;

@@ -253,7 +253,7 @@ __device__ __forceinline__ void cps_tile(const CpsArgs& a, uint32_t* sm, uint64_
             const uint64_t now = globaltimer_ns();
             if (t0 == 0) {
               t0 = now;
-            } else if (now - t0 > kWaitLimitNs) {
+            } else if (now - t0 > a.wait_ns) {
               if (j == 0) atomicOr(a.err, kErrLookbackTimeout);
               done = true;
             }
@@ -341,7 +341,9 @@ static cudaError_t launch_cps_t(const CpsArgs& a, size_t smem, cudaStream_t s) {
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
   if (err != cudaSuccess) return err;
-  kern<<<static_cast<unsigned>(a.ntiles), NT, smem, s>>>(a);
+  CpsArgs b = a;
+  b.wait_ns = wait_limit_ns();
+  kern<<<static_cast<unsigned>(a.ntiles), NT, smem, s>>>(b);
   return cudaGetLastError();
 }
 

@@ -31,7 +31,6 @@ namespace bcf {
 
 // ---------------------------------------------------------------- constants
 
-constexpr uint64_t kWaitLimitNs = 2000000000ull;  // bounded mbarrier waits: 2 s
 constexpr uint32_t kErrTmaTimeout = 1u;
 
 __host__ __device__ constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x >> 1); }
@@ -110,14 +109,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Wait for phase `parity` of the barrier, at most kWaitLimitNs.  On expiry the
+// Wait for phase `parity` of the barrier, at most limit_ns.  On expiry the
 // error word gets `code` and false is returned.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t* err,
-                                                  uint32_t code) {
+                                                  uint32_t code, uint64_t limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer_ns();
   while (!mbar_try_wait(bar, parity)) {
-    if (globaltimer_ns() - t0 > kWaitLimitNs) {
+    if (globaltimer_ns() - t0 > limit_ns) {
       if (err) atomicOr(err, code);
       return false;
     }

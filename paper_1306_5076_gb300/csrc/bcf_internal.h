@@ -8,6 +8,17 @@
 
 namespace bcf {
 
+// Library-wide run-time settings (bcf_api.cu).  wait_limit_ns(): the limit of
+// every device-side bounded wait (bcf_set_wait_limit_us); the launch wrappers
+// copy it into their kernels' arguments.  smem_floor_bytes(): the profiling
+// floor on the block sort's and merge pass's dynamic shared memory
+// (bcf_profile_set_smem_floor); 0 leaves every launch as built.
+uint64_t wait_limit_ns();
+uint32_t smem_floor_bytes();
+constexpr uint64_t kDefaultWaitLimitNs = 2000000000ull;  // 2 s
+constexpr uint32_t kMaxWaitLimitUs = 60000000u;          // 60 s
+constexpr uint32_t kMaxSmemFloor = 227u * 1024u;         // the opt-in maximum per CTA
+
 // One adjacent pair of sorted runs to merge: A = [off, off + na), B = [off + na,
 // off + na + nb) of the source array; the merged run occupies the same index
 // range of the destination.  `piece0` is the index of the pair's first work
@@ -56,6 +67,7 @@ struct MergeArgs {
   uint64_t nitems;      // work items (tile pieces) of this launch
   const void* samples_in;  // sample array of kin (key g / S at every g = 0 mod S), or nullptr
   void* samples_out;       // sample array of kout, or nullptr
+  uint64_t wait_ns;        // bounded-wait limit (set by launch_merge)
 };
 
 // Tuning configuration: elements per thread and threads per CTA.
@@ -76,6 +88,41 @@ constexpr int kNumMergeCfgs = sizeof(kMergeCfgs) / sizeof(kMergeCfgs[0]);
 // Is the configuration compiled for this key width / payload flag?
 bool block_cfg_supported(int key_bytes, bool pairs, int cfg);
 bool merge_cfg_supported(int key_bytes, bool pairs, int cfg);
+
+// ---------------------------------------------------------------- sort workspace
+
+constexpr size_t kAlign = 256;
+constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Smallest merge tile over all configurations: bounds the split arrays.
+constexpr uint64_t kMinMergeTile = 2048;
+constexpr bool merge_tiles_at_least(uint64_t t) {
+  for (int i = 0; i < kNumMergeCfgs; ++i)
+    if (static_cast<uint64_t>(kMergeCfgs[i].tile()) < t) return false;
+  return true;
+}
+static_assert(merge_tiles_at_least(kMinMergeTile), "a merge tile is below kMinMergeTile");
+
+struct WsLayout {
+  size_t splits, samples0, samples1, keys, vals, total;
+};
+
+// Workspace of a sort or a merge of runs_or_segs runs:
+// [header | splits | samples of the output buffer | samples of the workspace
+// copy | keys copy | values copy].  constexpr so that fixed-size scratch
+// (bcf_static.cu) is sized by the same formula at compile time.
+constexpr WsLayout ws_layout(uint64_t n, uint64_t runs_or_segs, int kb, bool pairs) {
+  WsLayout w{};
+  const uint64_t items = (n + kMinMergeTile - 1) / kMinMergeTile + runs_or_segs + 2;
+  const uint64_t nsamp = n / kSampleStride + 2;
+  w.splits = kAlign;
+  w.samples0 = align_up(w.splits + items * sizeof(uint64_t), kAlign);
+  w.samples1 = align_up(w.samples0 + nsamp * kb, kAlign);
+  w.keys = align_up(w.samples1 + nsamp * kb, kAlign);
+  w.vals = align_up(w.keys + n * kb, kAlign);
+  w.total = align_up(w.vals + (pairs ? n * 4 : 0), kAlign);
+  return w;
+}
 
 // Segmented sort (persistent kernel); tile = merge tile = E * NT.
 constexpr TileCfg kSegCfgs[] = {{16, 256}, {16, 128}, {32, 128}, {32, 256}, {32, 512}};
@@ -106,6 +153,12 @@ bool seg_cfg_supported(int key_bytes, bool pairs, int cfg);
 cudaError_t launch_segmented(int key_bytes, bool pairs, int cfg, const SegLaunch& L,
                              cudaStream_t s);
 size_t seg_work_bytes();
+// One CTA of the 32-bit worker on a queue whose only announced slot is never
+// published: its bounded wait runs out (failure-path self-test).  ws: at
+// least kSegSelftestBytes of device memory, 256-byte aligned.
+constexpr size_t kSegSelftestBytes = 512;
+cudaError_t launch_segmented_wait_selftest(void* ws, uint64_t wait_ns, uint32_t* err,
+                                           cudaStream_t s);
 size_t seg_ctl_bytes();
 
 cudaError_t launch_block_sort(int key_bytes, bool pairs, int cfg, const BlockSortArgs& a,
@@ -141,6 +194,7 @@ struct CpsArgs {
   unsigned long long* status;  // ntiles * d words
   uint32_t* counter;     // next tile
   uint32_t* err;
+  uint64_t wait_ns;      // bounded-wait limit of the look-back (set by launch_cps)
 };
 // layout 0: one shared-memory bank per thread (the paper's conflict-free
 // layout); layout 1: each thread's d counters contiguous (the conflicting one).

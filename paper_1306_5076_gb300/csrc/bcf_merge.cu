@@ -320,8 +320,8 @@ __global__ void __launch_bounds__(NT) merge_kernel(const MergeArgs a,
       stage_bulk(svB, a.vin, gb0, gb1, bar);
     }
     // one thread waits (bounded); the barrier below releases the others
-    bool ok = mbar_wait_bounded(bar, 0, a.err, kErrTmaTimeout);
-    if (!ok) mbar_wait_bounded(bar, 0, nullptr, 0);  // let copies in flight land
+    bool ok = mbar_wait_bounded(bar, 0, a.err, kErrTmaTimeout, a.wait_ns);
+    if (!ok) mbar_wait_bounded(bar, 0, nullptr, 0, a.wait_ns);  // let copies in flight land
     s_ok = ok ? 1 : 0;
   } else if (tid >= 32 && tid < 64) {
     const uint32_t lane = tid - 32;
@@ -454,10 +454,13 @@ template <typename K, bool PAIRS, int E, int NT, bool IRREG, bool MAP, bool SMP>
 static cudaError_t launch_m3(const MergeArgs& a, const PairParam<IRREG>& pl, cudaStream_t s) {
   using S = MergeSmem<K, PAIRS, E, NT>;
   auto kern = merge_kernel<K, PAIRS, E, NT, IRREG, MAP, SMP>;
+  const uint32_t smem = S::kTotal > smem_floor_bytes() ? S::kTotal : smem_floor_bytes();
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         S::kTotal);
+                                         static_cast<int>(smem));
   if (err != cudaSuccess) return err;
-  kern<<<static_cast<unsigned>(a.nitems), NT, S::kTotal, s>>>(a, pl);
+  MergeArgs b = a;
+  b.wait_ns = wait_limit_ns();
+  kern<<<static_cast<unsigned>(a.nitems), NT, smem, s>>>(b, pl);
   return cudaGetLastError();
 }
 

@@ -158,6 +158,7 @@ cudaError_t launch_segmented(int key_bytes, bool pairs, int cfg, const SegLaunch
   a.piece_split = L.piece_split;
   a.ctl = static_cast<SegCtl*>(L.ctl);
   a.err = L.err;
+  a.wait_ns = wait_limit_ns();
   return key_bytes == 4 ? launch_segmented_typed<uint32_t>(pairs, cfg, a, s)
                          : launch_segmented_typed<uint64_t>(pairs, cfg, a, s);
 }

@@ -82,6 +82,7 @@ struct SegArgs {
   uint64_t* piece_split;  // per tile: merge-path split (A-keys before the piece) of its piece
   SegCtl* ctl;
   uint32_t* err;
+  uint64_t wait_ns;       // limit of every wait for a queue slot
 };
 
 // The plan kernel lives in bcf_segmented.cu.
@@ -419,12 +420,12 @@ __device__ __forceinline__ void merge_piece_item(const SegArgs& a, const SegGeo&
 
 // ---------------------------------------------------------------- worker
 
-__device__ __forceinline__ bool wait_ready(const SegWork* slot, uint32_t* err) {
+__device__ __forceinline__ bool wait_ready(const SegWork* slot, uint32_t* err, uint64_t limit_ns) {
   const volatile uint32_t* meta = &slot->meta;
   if (*meta & kReady) return true;
   const uint64_t t0 = globaltimer_ns();
   while (!(*meta & kReady)) {
-    if (globaltimer_ns() - t0 > kWaitLimitNs) {
+    if (globaltimer_ns() - t0 > limit_ns) {
       atomicOr(err, kErrQueueTimeout);
       return false;
     }
@@ -447,7 +448,7 @@ __device__ __forceinline__ void seg_worker_body(const SegArgs& a) {
     if (tid == 0) {
       const unsigned long long idx = atomicAdd(&a.ctl->head, 1ull);
       int go = 0;
-      if (idx < __ldcg(&a.ctl->total) && wait_ready(a.queue + idx, a.err)) {
+      if (idx < __ldcg(&a.ctl->total) && wait_ready(a.queue + idx, a.err, a.wait_ns)) {
         __threadfence();
         // the slot may have been written by another SM during this launch
         SegWork w;

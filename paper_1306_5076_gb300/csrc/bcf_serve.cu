@@ -38,15 +38,19 @@ constexpr uint64_t align_up(uint64_t x) { return (x + kAlignB - 1) / kAlignB * k
 
 // ---------------------------------------------------------------- arena allocator
 
-// First-fit allocator over [0, bytes) with a coalescing free list.
+// First-fit allocator over [0, bytes) with a coalescing free list.  Live
+// allocations are tracked so that a free must name one exactly (a double free
+// or a wrong range is refused instead of corrupting the free list).
 struct Arena {
   uint64_t bytes = 0, used = 0, peak = 0;
   std::map<uint64_t, uint64_t> free_;  // offset -> size
+  std::map<uint64_t, uint64_t> live_;  // offset -> size (rounded)
 
   void init(uint64_t b) {
     bytes = b / kAlignB * kAlignB;
     used = peak = 0;
     free_.clear();
+    live_.clear();
     if (bytes) free_[0] = bytes;
   }
   bool alloc(uint64_t sz, uint64_t* off) {
@@ -58,6 +62,7 @@ struct Arena {
         const uint64_t next = it->first + sz;
         free_.erase(it);
         if (rest) free_[next] = rest;
+        live_[*off] = sz;
         used += sz;
         if (used > peak) peak = used;
         return true;
@@ -65,8 +70,12 @@ struct Arena {
     }
     return false;
   }
-  void release(uint64_t off, uint64_t sz) {
+  // false (nothing changed) unless [off, off + sz) is a live allocation
+  bool release(uint64_t off, uint64_t sz) {
     sz = align_up(sz ? sz : 1);
+    auto lv = live_.find(off);
+    if (lv == live_.end() || lv->second != sz) return false;
+    live_.erase(lv);
     used -= sz;
     auto it = free_.emplace(off, sz).first;
     auto nx = std::next(it);
@@ -81,6 +90,7 @@ struct Arena {
         free_.erase(it);
       }
     }
+    return true;
   }
   uint64_t largest_free() const {
     uint64_t m = 0;
@@ -532,8 +542,7 @@ bcf_status bcf_arena_alloc(bcf_arena* p, uint64_t bytes, uint64_t* offset) {
 }
 bcf_status bcf_arena_free(bcf_arena* p, uint64_t offset, uint64_t bytes) {
   if (!p) return BCF_EINVAL;
-  p->a.release(offset, bytes);
-  return BCF_OK;
+  return p->a.release(offset, bytes) ? BCF_OK : BCF_EINVAL;
 }
 bcf_status bcf_arena_usage(const bcf_arena* p, uint64_t* used, uint64_t* largest_free) {
   if (!p) return BCF_EINVAL;

@@ -3,11 +3,11 @@
 //
 // Who needs it: callers that cannot call cudaMalloc at all -- for example a
 // plugin or kernel-hosting framework that owns every device allocation and
-// hands out only input and output buffers, code that runs while another
-// thread captures a CUDA graph in global capture mode (where cudaMalloc is an
-// error), or a latency-critical loop that must never hit cudaMalloc's
-// implicit device-wide synchronisation.  Such callers pass inputs and outputs
-// only; the ping-pong buffer and split array of the merge passes live in
+// hands a plugin only its input and output buffers, a process whose device
+// memory is carved up by an external pool it must not go around, or a
+// latency-critical loop that must never hit cudaMalloc's implicit
+// device-wide synchronisation.  Such callers pass inputs and outputs only;
+// the ping-pong buffer and split array of the merge passes live in
 // g_static_workspace below, reserved when the library is loaded on a GPU.
 //
 // Costs and rules:
@@ -25,19 +25,17 @@
 
 #include <mutex>
 
+#include "bcf_internal.h"
 #include "bcfsort.h"
 
 namespace {
 
 // The sort's workspace for BCF_STATIC_MAX_KEYS keys of the widest type (u64),
-// keys only: a 256-byte header, one u64 split per 2048-key merge tile (+2),
-// two sample arrays of one key per 256 (+2), each rounded to 256 bytes, then
-// one copy of the keys.  A spare page on top.
+// keys only, by the same formula bcf_workspace_bytes uses (a workspace for
+// fewer or narrower keys is never larger).
 constexpr size_t kMaxKeys = BCF_STATIC_MAX_KEYS;
-constexpr size_t round256(size_t x) { return (x + 255) / 256 * 256; }
-constexpr size_t kSplitBytes = round256(256 + (kMaxKeys / 2048 + 2) * 8);
-constexpr size_t kSampleBytes = round256((kMaxKeys / 256 + 2) * 8);
-constexpr size_t kStaticBytes = kSplitBytes + 2 * kSampleBytes + kMaxKeys * 8 + 4096;
+constexpr size_t kStaticBytes = bcf::ws_layout(kMaxKeys, 0, 8, false).total;
+static_assert(kStaticBytes < (size_t(9) << 20), "static scratch larger than documented");
 
 static __device__ __align__(256) unsigned char g_static_workspace[kStaticBytes];
 
@@ -65,10 +63,11 @@ extern "C" bcf_status bcf_sort_keys_static(void* keys_out, const void* keys_in, 
   if (n > kMaxKeys) return BCF_EUNSUPPORTED;
   // 16-bit keys need widened copies the static array has no room for
   if (kt == BCF_U16 || kt == BCF_I16) return BCF_EUNSUPPORTED;
-  // the static array is sized for the merge path: the algorithm choice is ignored
+  // the static array is sized for the merge path: pivot buckets take it too;
+  // any other algorithm value reaches bcf_sort_keys and is rejected there
   bcf_opts o{};
   if (opts) o = *opts;
-  o.algorithm = BCF_ALGO_MERGE;
+  if (o.algorithm == BCF_ALGO_PIVOT_BUCKETS) o.algorithm = BCF_ALGO_MERGE;
   if (n == 0) return bcf_sort_keys(keys_out, keys_in, 0, kt, &o, nullptr, 0, stream);
   void* ws = static_workspace();
   if (!ws) return BCF_ECUDA;

@@ -215,3 +215,25 @@ def test_profile_collect_launches_without_records(lib):
 def test_selftest_wait_rejects_bad_limits_before_any_launch(lib):
     assert lib.bcf_selftest_bounded_wait(0, None) == 1
     assert lib.bcf_selftest_bounded_wait(2000001, None) == 1
+
+
+def test_wait_limit_setting_range(lib):
+    assert lib.bcf_wait_limit_us() == 2_000_000  # default: 2 s
+    assert lib.bcf_set_wait_limit_us(60_000_001) == 1
+    assert lib.bcf_wait_limit_us() == 2_000_000  # a rejected value changes nothing
+    assert lib.bcf_set_wait_limit_us(1500) == 0
+    assert lib.bcf_wait_limit_us() == 1500
+    assert lib.bcf_set_wait_limit_us(0) == 0  # back to the default
+    assert lib.bcf_wait_limit_us() == 2_000_000
+
+
+def test_segmented_wait_selftest_checks_its_scratch_before_any_launch(lib):
+    assert lib.bcf_selftest_segmented_wait(None, 4096, None) == 2  # BCF_ENOMEM
+    assert lib.bcf_selftest_segmented_wait(ctypes.c_void_p(1 << 20), 511, None) == 2
+    assert lib.bcf_selftest_segmented_wait(ctypes.c_void_p((1 << 20) + 16), 4096, None) == 1
+
+
+def test_smem_floor_range(lib):
+    assert lib.bcf_profile_set_smem_floor(227 * 1024 + 1) == 1
+    assert lib.bcf_profile_set_smem_floor(200 * 1024) == 0
+    assert lib.bcf_profile_set_smem_floor(0) == 0

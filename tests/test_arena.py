@@ -85,3 +85,33 @@ def test_arena_exhaustion_and_exact_fit():
     a.free(2048, 1024)
     assert a.usage() == (2048, 2048)
     assert a.alloc(2048) == 1024
+
+
+def test_arena_refuses_double_free_and_wrong_ranges():
+    build.build()
+    from paper_1306_5076_gb300 import _native
+
+    lib = _native.load()
+    import ctypes
+
+    h = ctypes.c_void_p()
+    assert lib.bcf_arena_create(1 << 20, ctypes.byref(h)) == 0
+    off = ctypes.c_uint64()
+    assert lib.bcf_arena_alloc(h, 1000, ctypes.byref(off)) == 0
+    first = off.value
+    assert lib.bcf_arena_alloc(h, 5000, ctypes.byref(off)) == 0
+    second = off.value
+    used, largest = ctypes.c_uint64(), ctypes.c_uint64()
+    assert lib.bcf_arena_usage(h, ctypes.byref(used), ctypes.byref(largest)) == 0
+    before = (used.value, largest.value)
+    assert lib.bcf_arena_free(h, first + 256, 1000) == 1  # not the start of an allocation
+    assert lib.bcf_arena_free(h, first, 4096) == 1  # wrong size
+    assert lib.bcf_arena_free(h, (1 << 20) - 256, 256) == 1  # a free range
+    assert lib.bcf_arena_usage(h, ctypes.byref(used), ctypes.byref(largest)) == 0
+    assert (used.value, largest.value) == before  # nothing changed
+    assert lib.bcf_arena_free(h, first, 1000) == 0
+    assert lib.bcf_arena_free(h, first, 1000) == 1  # double free
+    assert lib.bcf_arena_free(h, second, 5000) == 0
+    assert lib.bcf_arena_usage(h, ctypes.byref(used), ctypes.byref(largest)) == 0
+    assert (used.value, largest.value) == (0, 1 << 20)
+    assert lib.bcf_arena_destroy(h) == 0
