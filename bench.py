@@ -205,8 +205,12 @@ def cpu_cores():
         return os.cpu_count() or 1
 
 
-def oracle_keys_per_s(sample_log2n=SAMPLE_LOG2N, reps=1):
-    """The CPU oracle as it stands, all host cores, on a sample of the workload."""
+SINGLE_LOG2N = 22  # oracle sample for the single-threaded timing
+
+
+def oracle_keys_per_s(sample_log2n=SAMPLE_LOG2N, reps=1, threads=None):
+    """The CPU oracle as it stands, on a sample of the workload: all host cores
+    (threads None) or the given number of threads."""
     import numpy as np
 
     import oracle
@@ -214,7 +218,7 @@ def oracle_keys_per_s(sample_log2n=SAMPLE_LOG2N, reps=1):
 
     n = 1 << sample_log2n
     keys = workloads.keys("uniform", "u32", n, seed=workloads.large_sort_seed("uniform", "u32", N))
-    cores = cpu_cores()
+    cores = cpu_cores() if threads is None else threads
     oracle.sort(keys[: 1 << 12], nthreads=cores)  # load the library outside the timing
     times = []
     for _ in range(reps):
@@ -223,6 +227,56 @@ def oracle_keys_per_s(sample_log2n=SAMPLE_LOG2N, reps=1):
         times.append(time.perf_counter() - t0)
     del np
     return n / statistics.median(times), cores, n, times
+
+
+def oracle_table():
+    """The CPU oracle as it stands on bounded samples of every workload, one
+    host core and all host cores: context for the GPU numbers (keys/s)."""
+    import numpy as np
+
+    import oracle
+    import workloads
+
+    cores = cpu_cores()
+
+    def rate(fn, n, reps=3):
+        fn()  # load the library, touch the inputs
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            fn()
+            ts.append(time.perf_counter() - t0)
+        return n / statistics.median(ts)
+
+    out = {"cores": cores, "cpu_model": host_cpu_model()}
+    k = workloads.keys("uniform", "u32", 1 << 20, seed=0)
+    out["C1 2^20 u32 uniform"] = {"one_core": rate(lambda: oracle.sort(k), k.size),
+                                  "all_cores": rate(lambda: oracle.sort(k, nthreads=cores), k.size)}
+    n1, na = 1 << 22, 1 << 24
+    for key in ("u32", "f32", "u64"):
+        for dist in (GRID_DISTS if key == "u32" else ("uniform",)):
+            k1 = workloads.keys(dist, key, n1)
+            ka = workloads.keys(dist, key, na)
+            for pairs in (False, True):
+                v1 = np.arange(n1, dtype=np.uint32) if pairs else None
+                va = np.arange(na, dtype=np.uint32) if pairs else None
+                out[f"C2 {key}{'+u32' if pairs else ''} {dist}"] = {
+                    "one_core": rate(lambda: oracle.sort(k1, v1), n1, reps=1),
+                    "all_cores": rate(lambda: oracle.sort(ka, va, nthreads=cores), na, reps=1)}
+    for kr in (2, 16, 256):
+        keys, offs = workloads.sorted_runs(kr, n1)
+        out[f"C3 merge k={kr}"] = {
+            "one_core": rate(lambda: oracle.merge_runs(keys, None, offs), n1, reps=1),
+            # merge_runs is defined as the stable sort of the concatenated runs
+            "all_cores": rate(lambda: oracle.sort(keys, nthreads=cores), n1, reps=1)}
+    keys, offs = workloads.segments(500, 1 << 18, "u32", seed=4000)
+    out["C4 segmented (500 segments of the law)"] = {
+        "one_core": rate(lambda: oracle.segmented_sort(keys, None, offs), keys.size, reps=1),
+        "all_cores": None}
+    out["samples"] = ("C1: the 2^20-key input itself; C2: 2^22 keys (one core) and 2^24 keys "
+                      "(all cores) per case; C3: 2^22 keys in k runs; C4: 500 segments "
+                      f"({int(offs[-1])} keys) of the 100,000-segment law")
+    return out
 
 
 def run_reference(args, world, rank):
@@ -582,6 +636,221 @@ def merge_runs_bench(torch, dev, bcf, peak):
     return {"total_keys": total, "results": out}
 
 
+def host_cpu_model():
+    """The host CPU's model name as lscpu reports it (Grace on the GB300 host)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+    except Exception:
+        return None
+    fields = {}
+    for ln in out.splitlines():
+        if ":" in ln:
+            k, v = ln.split(":", 1)
+            fields[k.strip()] = v.strip()
+    model = fields.get("Model name")
+    vendor = fields.get("Vendor ID")
+    arch = fields.get("Architecture")
+    return ", ".join(x for x in (vendor, model, arch) if x) or None
+
+
+# ---- the large-sort family (uniform, gaussian, sorted, reverse, distinct16,
+# zipf) drawn on the device.  Same laws as workloads.keys (which the parity
+# tests use), drawn with torch's seeded device generator instead of numpy, so
+# that 2^28-key inputs take milliseconds to make.  Seed = the family's rule
+# (1000 * distribution + 10 * key type + log2 n).
+GRID_DISTS = ("uniform", "gaussian", "sorted", "reverse", "distinct16", "zipf")
+
+
+def device_u32_values(torch, dev, dist, n, seed):
+    """u32 values (as int64 in [0, 2^32)) of one distribution of the family."""
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    if dist == "uniform":
+        return torch.randint(0, 1 << 32, (n,), dtype=torch.int64, device=dev, generator=g)
+    if dist == "gaussian":
+        x = torch.normal(2.0**31, 2.0**28, (n,), dtype=torch.float64, device=dev, generator=g)
+        return x.round_().clamp_(0, 2.0**32 - 1).to(torch.int64)
+    if dist in ("sorted", "reverse"):
+        e = torch.empty(n + 1, dtype=torch.float64, device=dev).exponential_(1.0, generator=g)
+        s = torch.cumsum(e, 0)
+        x = torch.floor(s[:-1] / s[-1] * 2.0**32).clamp_(max=2.0**32 - 1).to(torch.int64)
+        x = torch.cummax(x, 0).values  # exponential spacings: sorted by construction
+        return x.flip(0) if dist == "reverse" else x
+    if dist == "distinct16":
+        pool = torch.randint(0, 1 << 32, (16,), dtype=torch.int64, device=dev, generator=g)
+        return pool[torch.randint(0, 16, (n,), device=dev, generator=g)]
+    if dist == "zipf":
+        w = torch.arange(1, (1 << 20) + 1, dtype=torch.float64, device=dev).pow_(-1.1)
+        cdf = torch.cumsum(w, 0)
+        cdf /= cdf[-1].clone()
+        u = torch.rand(n, dtype=torch.float64, device=dev, generator=g)
+        r = torch.searchsorted(cdf, u).clamp_(max=(1 << 20) - 1)
+        return (r * 0x9E3779B1) & 0xFFFFFFFF
+    raise ValueError(dist)
+
+
+def device_keys(torch, dev, dist, key, n):
+    """Keys of the family for key type key in {u32, f32, u64}, as a tensor of the
+    key width (int32 / int64 bits)."""
+    import workloads
+
+    seed = workloads.large_sort_seed(dist, key, n)
+    if key == "u64" and dist in ("uniform", "distinct16"):
+        g = torch.Generator(device=dev)
+        g.manual_seed(seed)
+        if dist == "uniform":
+            return torch.randint(-2**63, 2**63 - 1, (n,), dtype=torch.int64, device=dev,
+                                 generator=g)
+        pool = torch.randint(-2**63, 2**63 - 1, (16,), dtype=torch.int64, device=dev, generator=g)
+        return pool[torch.randint(0, 16, (n,), device=dev, generator=g)]
+    if key == "u64" and dist == "zipf":
+        g = torch.Generator(device=dev)
+        g.manual_seed(seed)
+        w = torch.arange(1, (1 << 20) + 1, dtype=torch.float64, device=dev).pow_(-1.1)
+        cdf = torch.cumsum(w, 0)
+        cdf /= cdf[-1].clone()
+        u = torch.rand(n, dtype=torch.float64, device=dev, generator=g)
+        r = torch.searchsorted(cdf, u).clamp_(max=(1 << 20) - 1)
+        return r * 0x9E3779B97F4A7C15  # wraps mod 2^64
+    if key == "f32" and dist in ("uniform", "distinct16"):
+        key = "u32"  # random bit patterns: NaNs, infinities, subnormals and zeros included
+        seed = workloads.large_sort_seed(dist, "f32", n)
+    v = device_u32_values(torch, dev, dist, n, seed)
+    if key == "u32":
+        return (v - (v >> 31 << 32)).to(torch.int32)  # the same 32 bits
+    if key == "u64":
+        return v
+    return v.to(torch.float32).view(torch.int32)  # f32: float32 of the u32 value
+
+
+def order_bits(torch, k, key):
+    """Keys as int64 whose signed order is the key order (totalOrder for f32)."""
+    if key == "u64":
+        return k ^ (-2**63)  # unsigned order as signed
+    u = k.to(torch.int64) & 0xFFFFFFFF
+    if key == "f32":
+        neg = (u >> 31) == 1
+        u = torch.where(neg, u ^ 0xFFFFFFFF, u | 0x80000000)
+    return u
+
+
+def check_sorted_pairs(torch, kin, kout, vout, key):
+    """Exact device checks of a stable sort whose payloads are the input
+    positions: keys in order, payloads a permutation, every payload's input key
+    equals its output key (keys and values travel together), equal keys in
+    input order.  Keys only (vout None): in order and the same multiset
+    (two modular fingerprints)."""
+    o = order_bits(torch, kout, key)
+    ok = bool((o[1:] >= o[:-1]).all().item())
+    if vout is None:
+        i = order_bits(torch, kin, key)
+        p = 1000000007
+        ok = ok and bool(((i % p).sum() == (o % p).sum()).item()) and bool(
+            (((i % p) * (i % p) % p).sum() == ((o % p) * (o % p) % p).sum()).item())
+        return ok
+    v = vout.to(torch.int64) & 0xFFFFFFFF
+    n = v.numel()
+    ok = ok and bool((torch.bincount(v, minlength=n) == 1).all().item())
+    ok = ok and bool((kin[v] == kout).all().item())
+    ties = o[1:] == o[:-1]
+    ok = ok and bool((~ties | (v[1:] > v[:-1])).all().item())
+    return ok
+
+
+def c2_grid(torch, dev, bcf, peak, sizes=(24, 26, 28), reps=3):
+    """The large-sort grid: n in 2^sizes x the six distributions x {u32, f32,
+    u64} keys x {keys only, u32 payloads}: whole-sort ms, keys/s and the merge
+    pass's mean time against the HBM roofline, every output checked exactly on
+    the device."""
+    stream = torch.cuda.current_stream(dev)
+    codes = {"u32": bcf.BCF_U32, "f32": bcf.BCF_F32, "u64": bcf.BCF_U64}
+    out = {}
+    all_ok = True
+    for lg in sizes:
+        n = 1 << lg
+        for key in ("u32", "f32", "u64"):
+            kt = codes[key]
+            ws = torch.empty(bcf.bcf_workspace_bytes(bcf.BCF_OP_SORT, n, 0, kt, True),
+                             dtype=torch.uint8, device=dev)
+            for dist in GRID_DISTS:
+                kd = device_keys(torch, dev, dist, key, n)
+                ko = torch.empty_like(kd)
+                for pairs in (False, True):
+                    vd = torch.arange(n, dtype=torch.int32, device=dev) if pairs else None
+                    vo = torch.empty_like(vd) if pairs else None
+                    if pairs:
+                        fn = lambda: bcf.bcf_sort_pairs(ko, vo, kd, vd, kt=kt, ws=ws,  # noqa: E731
+                                                        stream=stream)
+                    else:
+                        fn = lambda: bcf.bcf_sort_keys(ko, kd, kt=kt, ws=ws,  # noqa: E731
+                                                       stream=stream)
+                    fn()
+                    torch.cuda.synchronize()
+                    bcf.bcf_profile_collect()
+                    bcf.bcf_profile_enable(True)
+                    ms = timed_ms(torch, stream, fn, warmup=0, reps=reps)
+                    bcf.bcf_profile_enable(False)
+                    prof = bcf.bcf_profile_collect()
+                    ok = check_sorted_pairs(torch, kd, ko, vo, key)
+                    all_ok = all_ok and ok
+                    plan = bcf.bcf_sort_plan(n, kt, pairs)
+                    m = prof["merge"]
+                    merge_ms = m["total_ms"] / max(m["launches"], 1)
+                    frac = (plan["bytes_per_pass"] / (merge_ms * 1e-3) / 1e9 / peak
+                            if m["launches"] else None)
+                    out[f"2^{lg} {key}{'+u32' if pairs else ''} {dist}"] = {
+                        "ms": round(ms, 4), "gkeys_s": round(n / (ms * 1e-3) / 1e9, 3),
+                        "merge_frac": None if frac is None else round(frac, 3), "exact": ok}
+                    del vd, vo
+                del kd, ko
+            del ws
+            torch.cuda.empty_cache()
+    return {"laws": "the workload family's six laws, drawn on the device (torch generator, "
+                    "seed rule 1000*dist+10*key+log2n); u32 payload = input position",
+            "all_exact": all_ok, "results": out}
+
+
+def c1_latency(torch, dev, bcf, calls=60):
+    """The small plain sort: 2^20 uniform u32 keys, seed 0, ascending, keys
+    only: per-call latency of one bcf_sort_keys (one launch chain), each call
+    timed alone with CUDA events and by the host clock (launch to completion
+    seen by the host), median of the last calls - 10; and back-to-back
+    throughput.  4 MiB of keys: L2-resident, so no roofline claim."""
+    import numpy as np
+
+    import workloads
+
+    n = 1 << 20
+    keys = workloads.keys("uniform", "u32", n, seed=0)
+    kd = torch.from_numpy(keys.view(np.int32)).to(dev)
+    ko = torch.empty_like(kd)
+    ws = torch.empty(bcf.bcf_workspace_bytes(bcf.BCF_OP_SORT, n, 0, bcf.BCF_U32, False),
+                     dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ev, host = [], []
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    for _ in range(calls):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        a.record(stream)
+        bcf.bcf_sort_keys(ko, kd, kt=bcf.BCF_U32, ws=ws, stream=stream)
+        b.record(stream)
+        b.synchronize()
+        host.append((time.perf_counter() - t0) * 1e3)
+        ev.append(a.elapsed_time(b))
+    ev, host = ev[10:], host[10:]
+    thr_ms = timed_ms(torch, stream, lambda: bcf.bcf_sort_keys(ko, kd, kt=bcf.BCF_U32, ws=ws,
+                                                              stream=stream), warmup=3, reps=50)
+    ok = check_sorted_pairs(torch, kd, ko, None, "u32")
+    plan = bcf.bcf_sort_plan(n, bcf.BCF_U32, False)
+    return {"n": n, "seed": 0, "launches_per_call": plan["launches"],
+            "latency_ms_median": statistics.median(ev), "latency_ms_p90": sorted(ev)[int(0.9 * len(ev))],
+            "host_latency_ms_median": statistics.median(host),
+            "back_to_back_ms": thr_ms, "keys_per_s": n / (thr_ms * 1e-3),
+            "calls_timed": len(ev), "exact": ok}
+
+
 def profile_case(args):
     """A small case of one path, for ncu captures (inputs larger than L2, a
     few launches): 'cps' = colored prefix sums of 2^26 elements, 16 colors,
@@ -641,6 +910,63 @@ def profile_case(args):
         raise RuntimeError("device error word set")
     print(json.dumps({"profile_case": args.profile_case, "n": n, "ok": True}))
     return 0
+
+
+def summary_of(line, peak):
+    """A compact digest of the sections, placed last in the JSON line so that a
+    reader who keeps only its tail still sees every headline number."""
+    r3 = lambda x: None if x is None else round(float(x), 3)  # noqa: E731
+    s = {"sort_2p28_u32_ms": r3(line["ms_per_step"]),
+         "merge_pass_frac": r3(line["roofline"]["frac"]),
+         "e2e_gkeys_s": r3(line["e2e"]["value"] / 1e9)}
+    pp = line.get("per_kernel_ms") or {}
+    s["block_sort_ms"], s["partition_ms"] = r3(pp.get("block_sort")), r3(pp.get("partition"))
+    cpu = line.get("cpu_baseline")
+    if cpu:
+        s["oracle_mkeys_s"] = {"all_cores": r3(cpu["value"] / 1e6), "cores": cpu["cores"],
+                               "one_core": r3(cpu["single_thread"]["value"] / 1e6),
+                               "cpu": cpu.get("cpu_model")}
+    sv = line.get("serving")
+    if sv:
+        s["serving_p50_p99_ms"] = {
+            f"{tr}_{mode}": [r3(sv[tr][mode]["p50_ms"]), r3(sv[tr][mode]["p99_ms"])]
+            for tr in ("nominal", "stress_8x") for mode in ("served", "plain")}
+        s["serving_gkeys_s"] = {f"{tr}_{mode}": r3(sv[tr][mode]["keys_per_s"] / 1e9)
+                                for tr in ("nominal", "stress_8x") for mode in ("served", "plain")}
+        s["serving_batches"] = {tr: sv[tr]["served"]["coalesced_batches"]
+                                for tr in ("nominal", "stress_8x")}
+    c1 = line.get("small_sort_2p20")
+    if c1:
+        s["c1_2p20"] = {"latency_ms": r3(c1["latency_ms_median"]),
+                        "gkeys_s": r3(c1["keys_per_s"] / 1e9), "exact": c1["exact"]}
+    g = line.get("large_sort_grid")
+    if g:
+        res = g["results"]
+        s["c2_exact"] = g["all_exact"]
+        s["c2_gkeys_s_min_max"] = {}
+        for lg in (24, 26, 28):
+            for kind in ("u32", "u32+u32", "f32", "f32+u32", "u64", "u64+u32"):
+                v = [x["gkeys_s"] for k, x in res.items() if k.startswith(f"2^{lg} {kind} ")]
+                if v:
+                    s["c2_gkeys_s_min_max"][f"2^{lg} {kind}"] = [min(v), max(v)]
+    kt = line.get("key_types")
+    if kt:
+        s["merge_pass_frac_by_key"] = {k: r3(v.get("merge_pass_frac"))
+                                       for k, v in kt["results"].items() if "merge_pass_frac" in v}
+    mr = line.get("merge_runs")
+    if mr:
+        s["merge_runs_frac"] = {k: r3(v["frac"]) for k, v in mr["results"].items()}
+    sg = line.get("segmented")
+    if sg:
+        s["segmented_ms"] = {k: r3(v["ms"]) for k, v in sg["results"].items()}
+    pb = line.get("pivot_buckets")
+    if pb:
+        s["pivot_bucket_speedup"] = {k: r3(v["speedup"]) for k, v in pb["results"].items()}
+    cps = line.get("colored_prefix_sums")
+    if cps:
+        s["cps_frac_banked"] = {d: r3(v["frac"]) for d, v in cps["banked"].items()}
+    s["peak_gbs"] = peak
+    return s
 
 
 def run_gpu(args, world, rank, local, pg):
@@ -797,7 +1123,9 @@ def run_gpu(args, world, rank, local, pg):
     peak, peak_kind = measured_peaks()
     extras = None
     if not args.no_extras:
-        extras = {"key_types": key_types_bench(torch, dev, bcf, peak),
+        extras = {"small_sort_2p20": c1_latency(torch, dev, bcf),
+                  "large_sort_grid": c2_grid(torch, dev, bcf, peak),
+                  "key_types": key_types_bench(torch, dev, bcf, peak),
                   "colored_prefix_sums": cps_bench(torch, dev, bcf, peak),
                   "pivot_buckets": pb_bench(torch, dev, bcf),
                   "merge_runs": merge_runs_bench(torch, dev, bcf, peak),
@@ -815,9 +1143,14 @@ def run_gpu(args, world, rank, local, pg):
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         kps, cores, n, t = oracle_keys_per_s()
+        kps1, _, n1, t1 = oracle_keys_per_s(SINGLE_LOG2N, threads=1)
         cpu = {"value": kps, "unit": "keys/s", "cores": cores, "kind": "oracle",
                "sample": f"2^{SAMPLE_LOG2N} keys of the same workload, one stable merge sort "
-                         f"(C, {cores} threads), {t[0]:.2f} s"}
+                         f"(C, {cores} threads), {t[0]:.2f} s",
+               "single_thread": {"value": kps1, "unit": "keys/s", "cores": 1,
+                                 "sample": f"2^{SINGLE_LOG2N} keys of the same workload, "
+                                           f"{t1[0]:.2f} s"},
+               "cpu_model": host_cpu_model()}
     line = {
         "metric": METRIC,
         "value": job_keys_per_s(world, N, ms),
@@ -861,6 +1194,7 @@ def run_gpu(args, world, rank, local, pg):
         line["serving"] = serving
     if extras is not None:
         line.update(extras)
+    line["summary"] = summary_of(line, peak)
     print(json.dumps(line))
     return 0
 
@@ -879,6 +1213,9 @@ def main():
                          "pivot-bucket comparison")
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="length of the served-vs-plain request trace (0: skip)")
+    ap.add_argument("--oracle-table", action="store_true",
+                    help="time the CPU oracle on bounded samples of every workload (one core and "
+                         "all cores) and exit; no GPU is used")
     ap.add_argument("--smem-floor", type=int, default=0,
                     help="profiling only: minimum dynamic shared memory (bytes) of the block "
                          "sort and merge launches, e.g. 200000 for one CTA per SM")
@@ -892,6 +1229,9 @@ def main():
         args.warmup = 3
     if args.profile_case:
         return profile_case(args)
+    if args.oracle_table:
+        print(json.dumps({"oracle_table": oracle_table()}))
+        return 0
     world, rank, local, pg = dist_setup(args)
     try:
         if args.impl == "reference":

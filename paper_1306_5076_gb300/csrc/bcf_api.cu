@@ -369,6 +369,7 @@ bcf_status run_sort(void* ko, uint32_t* vo, const void* ki, const uint32_t* vi, 
     ma.vout = vbuf[buf(i)];
     ma.n = n;
     ma.run = static_cast<uint64_t>(plan.T) << (i - 1);
+    ma.run_log2 = static_cast<uint32_t>(ilog2_u64(plan.T)) + static_cast<uint32_t>(i - 1);
     ma.splits = splits;
     ma.mode_in = 0;
     ma.mode_out = i == m ? mode : 0;

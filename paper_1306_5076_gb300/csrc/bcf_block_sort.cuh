@@ -100,9 +100,7 @@ __global__ void __launch_bounds__(NT) block_sort_kernel(const BlockSortArgs a) {
     }
   }
 
-  // (measured: kFmaKeys64 makes the u64 block sort 3 % faster; kFmaPairs made
-  // the pairs block sort 4 % slower)
-  block_sort_tile<NT, kFmaKeys | kFmaKeys64>(f, sm);
+  block_sort_tile<NT, CeForms<K, PAIRS>::kBlockBlk, CeForms<K, PAIRS>::kBlockOth>(f, sm);
 
   K* kout = static_cast<K*>(a.kout) + base;
   uint32_t* vout = PAIRS ? a.vout + base : nullptr;

@@ -155,6 +155,20 @@ __device__ __forceinline__ uint64_t lds_pred(const uint64_t* p, bool pred, uint6
   return v;
 }
 
+// Shared store issued only by lanes whose predicate is set (one instruction of
+// its own: lanes storing to two different arrays through two such calls never
+// share a request).
+__device__ __forceinline__ void sts_pred(uint32_t* p, bool pred, uint32_t v) {
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q st.shared.b32 [%0], %1;\n\t}"
+               ::"r"(smem_u32(p)), "r"(v), "r"((uint32_t)pred)
+               : "memory");
+}
+__device__ __forceinline__ void sts_pred(uint64_t* p, bool pred, uint64_t v) {
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q st.shared.b64 [%0], %1;\n\t}"
+               ::"r"(smem_u32(p)), "l"(v), "r"((uint32_t)pred)
+               : "memory");
+}
+
 // 32-byte global stores (sm_100 and later): each thread writes one whole
 // 32-byte sector, so a warp storing its threads' consecutive runs touches
 // full sectors only, with half the store instructions of 16-byte vectors.
@@ -242,7 +256,19 @@ __device__ __forceinline__ bool after(K kx, uint32_t ix, K ky, uint32_t iy) {
     const uint64_t y = (static_cast<uint64_t>(ky) << 32) | iy;
     return x > y;
   } else {
-    return kx > ky || (kx == ky && ix > iy);
+    // (key, index) as one 96-bit number: y - x with a borrow chain over the
+    // three words borrows exactly when x > y
+    uint32_t r;
+    asm("{\n\t.reg .u32 t;\n\t"
+        "sub.cc.u32 t, %1, %2;\n\t"
+        "subc.cc.u32 t, %3, %4;\n\t"
+        "subc.cc.u32 t, %5, %6;\n\t"
+        "subc.u32 %0, 0, 0;\n\t}"
+        : "=r"(r)
+        : "r"(iy), "r"(ix), "r"(static_cast<uint32_t>(ky)), "r"(static_cast<uint32_t>(kx)),
+          "r"(static_cast<uint32_t>(static_cast<uint64_t>(ky) >> 32)),
+          "r"(static_cast<uint32_t>(static_cast<uint64_t>(kx) >> 32)));
+    return r != 0;
   }
 }
 
@@ -250,84 +276,118 @@ __device__ __forceinline__ bool after(K kx, uint32_t ix, K ky, uint32_t iy) {
 // read once per thread into Frag::one.
 static __device__ uint32_t g_unit_multiplier = 1;
 
-// Work moved from the ALU pipe, which the sorting networks keep saturated, to
-// the FMA pipe (integer multiply-adds with a multiplier of Frag::one), in the
-// compare-exchanges of the stages that ask for it (measured: the BLK-layout
-// stages).  Both forms are exact in modular arithmetic.
-//   kFmaKeys  (32-bit keys, no payloads): the maximum is x * 1 + y - min(x, y)
-//             instead of a second min/max;
-//   kFmaPairs (32-bit keys with payloads): each of the three words is swapped
-//             as x + s * (y - x), y' = x + y - x' with s = 0 or 1, instead of
-//             two selects;
-//   kFmaKeys64 (64-bit keys, no payloads): the same swap of the two halves
-//             after one 64-bit comparison, instead of four selects.
-enum : int { kFmaKeys = 1, kFmaPairs = 2, kFmaKeys64 = 4 };
+// Compare-exchange forms.  The networks' integer minima, maxima, comparisons
+// and selects run on the ALU pipe, which takes them at half the issue rate;
+// the FMA pipe, which runs integer multiply-adds at the full rate, is idle.
+// The forms below move work there (with a multiplier of Frag::one); all are
+// exact in modular arithmetic.
+//   kFmaKeys    (32-bit keys, no payloads): the maximum is x * 1 + y - min(x, y),
+//               two multiply-adds instead of a second min / max;
+//   kFmaWord(w) (every other kind of element): after the one comparison that
+//               decides the swap, word w is swapped as x' = x + s (y - x),
+//               y' = x + y - x' with s in {0, 1} -- four multiply-adds instead
+//               of two selects.  Words: 0 the key (its low half for 64-bit
+//               keys), 1 the high half of a 64-bit key, 2 the tie-break index,
+//               3 the payload.
+// Which words take the FMA form is chosen per kernel and element kind
+// (CeForms below): the best split balances the two pipes against the issue
+// rate.
+enum : int { kFmaKeys = 1 };
+__host__ __device__ constexpr int kFmaWord(int w) { return 1 << (4 + w); }
+
+// x' = x + s (y - x), y' = x + y - x' on the FMA pipe (s = 0 or 1 = one).
+__device__ __forceinline__ void fma_swap(uint32_t& xr, uint32_t& yr, uint32_t s, uint32_t one) {
+  const uint32_t x = xr, y = yr, neg = 0u - one;
+  uint32_t d, nx, t, ny;
+  asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(x), "r"(neg), "r"(y));    // y - x
+  asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(nx) : "r"(s), "r"(d), "r"(x));     // x + s(y - x)
+  asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(t) : "r"(x), "r"(one), "r"(y));    // x + y
+  asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(ny) : "r"(nx), "r"(neg), "r"(t));  // x + y - x'
+  xr = nx;
+  yr = ny;
+}
+__device__ __forceinline__ void sel_swap(uint32_t& xr, uint32_t& yr, bool sw) {
+  const uint32_t x = xr, y = yr;
+  xr = sw ? y : x;
+  yr = sw ? x : y;
+}
 
 // Compare-exchange registers a < b: ascending puts the smaller element in a.
 template <typename K, bool PAIRS, int E>
 __device__ __forceinline__ void ce(Frag<K, PAIRS, E>& f, int a, int b, bool desc, int fma = 0) {
-  if (!PAIRS && sizeof(K) == 4 && (fma & kFmaKeys)) {
+  if constexpr (!PAIRS && sizeof(K) == 4) {
     const uint32_t x = static_cast<uint32_t>(f.k[a]), y = static_cast<uint32_t>(f.k[b]);
     const uint32_t lo = x < y ? x : y;
     uint32_t hi;
-    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(hi) : "r"(x), "r"(f.one), "r"(y));
-    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(hi) : "r"(lo), "r"(0u - f.one), "r"(hi));
+    if (fma & kFmaKeys) {
+      asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(hi) : "r"(x), "r"(f.one), "r"(y));
+      asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(hi) : "r"(lo), "r"(0u - f.one), "r"(hi));
+    } else {
+      hi = x < y ? y : x;
+    }
     f.k[a] = static_cast<K>(desc ? hi : lo);
     f.k[b] = static_cast<K>(desc ? lo : hi);
-  } else if (!PAIRS && sizeof(K) == 8 && (fma & kFmaKeys64)) {
-    const uint64_t x = static_cast<uint64_t>(f.k[a]), y = static_cast<uint64_t>(f.k[b]);
-    const bool sw = (x > y) != desc;
-    const uint32_t s = sw ? f.one : 0u, one = f.one, neg = 0u - f.one;
-    uint32_t xw[2] = {static_cast<uint32_t>(x), static_cast<uint32_t>(x >> 32)};
-    uint32_t yw[2] = {static_cast<uint32_t>(y), static_cast<uint32_t>(y >> 32)};
-#pragma unroll
-    for (int w = 0; w < 2; ++w) {
-      uint32_t d, nx, t, ny;
-      asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(xw[w]), "r"(neg), "r"(yw[w]));
-      asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(nx) : "r"(s), "r"(d), "r"(xw[w]));
-      asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(t) : "r"(xw[w]), "r"(one), "r"(yw[w]));
-      asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(ny) : "r"(nx), "r"(neg), "r"(t));
-      xw[w] = nx;
-      yw[w] = ny;
-    }
-    f.k[a] = static_cast<K>(xw[0] | (static_cast<uint64_t>(xw[1]) << 32));
-    f.k[b] = static_cast<K>(yw[0] | (static_cast<uint64_t>(yw[1]) << 32));
-  } else if constexpr (!PAIRS) {
+  } else if (!PAIRS && (fma & (kFmaWord(0) | kFmaWord(1))) == 0) {
+    // 64-bit keys without payloads: a 64-bit minimum and maximum (measured
+    // 13 % faster in the block sort than one comparison and four selects)
     const K x = f.k[a], y = f.k[b];
     const K lo = x < y ? x : y, hi = x < y ? y : x;
     f.k[a] = desc ? hi : lo;
     f.k[b] = desc ? lo : hi;
-  } else if (sizeof(K) == 4 && (fma & kFmaPairs)) {
-    const bool sw = after(f.k[a], f.ix[a], f.k[b], f.ix[b]) != desc;
-    const uint32_t s = sw ? f.one : 0u, one = f.one, neg = 0u - f.one;
-    const auto swap_word = [&](uint32_t& xr, uint32_t& yr) {
-      const uint32_t x = xr, y = yr;
-      uint32_t d, nx, t, ny;
-      asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(x), "r"(neg), "r"(y));    // y - x
-      asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(nx) : "r"(s), "r"(d), "r"(x));     // x + s(y - x)
-      asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(t) : "r"(x), "r"(one), "r"(y));    // x + y
-      asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(ny) : "r"(nx), "r"(neg), "r"(t));  // x + y - x'
-      xr = nx;
-      yr = ny;
-    };
-    uint32_t ka = static_cast<uint32_t>(f.k[a]), kb = static_cast<uint32_t>(f.k[b]);
-    swap_word(ka, kb);
-    f.k[a] = static_cast<K>(ka);
-    f.k[b] = static_cast<K>(kb);
-    swap_word(f.ix[a], f.ix[b]);
-    swap_word(f.v[a], f.v[b]);
   } else {
-    const bool sw = after(f.k[a], f.ix[a], f.k[b], f.ix[b]) != desc;
-    const K ka = f.k[a], kb = f.k[b];
-    const uint32_t ia = f.ix[a], ib = f.ix[b], va = f.v[a], vb = f.v[b];
-    f.k[a] = sw ? kb : ka;
-    f.k[b] = sw ? ka : kb;
-    f.ix[a] = sw ? ib : ia;
-    f.ix[b] = sw ? ia : ib;
-    f.v[a] = sw ? vb : va;
-    f.v[b] = sw ? va : vb;
+    bool sw;  // a and b trade places
+    if constexpr (PAIRS)
+      sw = after(f.k[a], f.ix[a], f.k[b], f.ix[b]) != desc;
+    else
+      sw = (f.k[a] > f.k[b]) != desc;
+    const uint32_t s = sw ? f.one : 0u;
+    const auto word = [&](uint32_t& xr, uint32_t& yr, int w) {
+      if (fma & kFmaWord(w))
+        fma_swap(xr, yr, s, f.one);
+      else
+        sel_swap(xr, yr, sw);
+    };
+    if constexpr (sizeof(K) == 4) {
+      uint32_t ka = static_cast<uint32_t>(f.k[a]), kb = static_cast<uint32_t>(f.k[b]);
+      word(ka, kb, 0);
+      f.k[a] = static_cast<K>(ka);
+      f.k[b] = static_cast<K>(kb);
+    } else {
+      const uint64_t xa = static_cast<uint64_t>(f.k[a]), xb = static_cast<uint64_t>(f.k[b]);
+      uint32_t la = static_cast<uint32_t>(xa), lb = static_cast<uint32_t>(xb);
+      uint32_t ha = static_cast<uint32_t>(xa >> 32), hb = static_cast<uint32_t>(xb >> 32);
+      word(la, lb, 0);
+      word(ha, hb, 1);
+      f.k[a] = static_cast<K>(la | (static_cast<uint64_t>(ha) << 32));
+      f.k[b] = static_cast<K>(lb | (static_cast<uint64_t>(hb) << 32));
+    }
+    if constexpr (PAIRS) {
+      word(f.ix[a], f.ix[b], 2);
+      word(f.v[a], f.v[b], 3);
+    }
   }
 }
+
+// The compare-exchange forms each kernel uses, per element kind: in the
+// BLK-layout stages (Blk) and in the other stages and the per-thread network
+// (Oth).  Measured on GB300 (sweeps over the word choices).
+template <typename K, bool PAIRS> struct CeForms;
+template <> struct CeForms<uint32_t, false> {
+  static constexpr int kBlockBlk = kFmaKeys, kBlockOth = 0;
+  static constexpr int kMergeBlk = kFmaKeys, kMergeOth = 0;
+};
+template <> struct CeForms<uint32_t, true> {
+  static constexpr int kBlockBlk = 0, kBlockOth = 0;
+  static constexpr int kMergeBlk = kFmaWord(3), kMergeOth = kFmaWord(3);
+};
+template <> struct CeForms<uint64_t, false> {
+  static constexpr int kBlockBlk = kFmaWord(0) | kFmaWord(1), kBlockOth = 0;
+  static constexpr int kMergeBlk = 0, kMergeOth = 0;
+};
+template <> struct CeForms<uint64_t, true> {
+  static constexpr int kBlockBlk = kFmaWord(1) | kFmaWord(3), kBlockOth = kFmaWord(1) | kFmaWord(3);
+  static constexpr int kMergeBlk = 0, kMergeOth = 0;
+};
 
 // Batcher's odd-even merge sort network on N inputs (Knuth vol. 3, Sec.
 // 5.3.4, Algorithm M), listed as comparator pairs at compile time.
@@ -350,11 +410,11 @@ struct OemNetwork {
 
 // The "BATCHERS-ODD-EVEN-MERGESORT(R)" register network of Algorithms 1 and
 // 2: sorts one thread's E registers, direction chosen per thread.
-template <typename K, bool PAIRS, int E>
+template <int FMA = 0, typename K, bool PAIRS, int E>
 __device__ __forceinline__ void thread_sort(Frag<K, PAIRS, E>& f, bool desc) {
   constexpr OemNetwork<E> net{};
 #pragma unroll
-  for (int c = 0; c < net.n; ++c) ce(f, net.a[c], net.b[c], desc);
+  for (int c = 0; c < net.n; ++c) ce(f, net.a[c], net.b[c], desc, FMA);
 }
 
 // ---------------------------------------------------------------- layouts
@@ -471,15 +531,16 @@ __device__ __forceinline__ void stages(Frag<K, PAIRS, E>& f) {
 // ascending result in BLK layout.  Stages on bits t-1 .. 0 in STR, MID, BLK.
 // Both layout changes reuse one buffer (a second buffer would save two
 // barriers but halves the CTAs per SM, which was measured slower).
-// FMA_BLK: the kFma* forms of the BLK stages (Frag::one must be set).
-template <int NT, int FMA_BLK = 0, typename K, bool PAIRS, int E>
+// FMA_BLK / FMA_OTH: the compare-exchange forms of the BLK stages / of the
+// others (Frag::one must be set when either is non-zero).
+template <int NT, int FMA_BLK = 0, int FMA_OTH = 0, typename K, bool PAIRS, int E>
 __device__ __forceinline__ void bitonic_merge_str(Frag<K, PAIRS, E>& f, uint32_t* sm) {
   using G = Geo<E, NT>;
   constexpr int r = G::r, t = G::t;
-  stages<kSTR, t - 1, t - r, NT>(f);
+  stages<kSTR, t - 1, t - r, NT, FMA_OTH>(f);
   if constexpr (t - r - 1 >= r) {
     relayout<kSTR, kMID, 0, NT>(f, sm);
-    stages<kMID, t - r - 1, r, NT>(f);
+    stages<kMID, t - r - 1, r, NT, FMA_OTH>(f);
     relayout<kMID, kBLK, 0, NT>(f, sm);
   } else {
     relayout<kSTR, kBLK, 0, NT>(f, sm);
@@ -487,51 +548,140 @@ __device__ __forceinline__ void bitonic_merge_str(Frag<K, PAIRS, E>& f, uint32_t
   stages<kBLK, r - 1, 0, NT, FMA_BLK>(f);
 }
 
+// Lane exchange of a compare-exchange whose two elements sit in lanes
+// l and l ^ m of one warp: this lane's register a meets the partner lane's
+// register b; the lower lane keeps the smaller element, the upper the larger.
+// (key, tie-break index) order for pairs; the payload follows.
+template <typename K, bool PAIRS, int E>
+struct LaneVal {
+  K k;
+  uint32_t ix, v;
+};
+template <typename K, bool PAIRS, int E>
+__device__ __forceinline__ LaneVal<K, PAIRS, E> lane_fetch(const Frag<K, PAIRS, E>& f, int b,
+                                                           uint32_t m) {
+  LaneVal<K, PAIRS, E> y;
+  y.k = __shfl_xor_sync(0xFFFFFFFFu, f.k[b], m);
+  if constexpr (PAIRS) {
+    y.ix = __shfl_xor_sync(0xFFFFFFFFu, f.ix[b], m);
+    y.v = __shfl_xor_sync(0xFFFFFFFFu, f.v[b], m);
+  }
+  return y;
+}
+template <typename K, bool PAIRS, int E>
+__device__ __forceinline__ void lane_keep(Frag<K, PAIRS, E>& f, int a,
+                                          const LaneVal<K, PAIRS, E>& y, bool upper) {
+  if constexpr (!PAIRS) {
+    const K x = f.k[a];
+    f.k[a] = upper ? (x > y.k ? x : y.k) : (x < y.k ? x : y.k);
+  } else {
+    const bool y_after = after(y.k, y.ix, f.k[a], f.ix[a]);
+    const bool take = upper ? y_after : !y_after;
+    f.k[a] = take ? y.k : f.k[a];
+    f.ix[a] = take ? y.ix : f.ix[a];
+    f.v[a] = take ? y.v : f.v[a];
+  }
+}
+
+// Levels J with J - r <= shuffle_levels<K, PAIRS>() take their lane stages
+// (k bits J-1 .. r, the lane bits of BLK) as warp shuffles instead of a BLK ->
+// MID -> BLK round trip through shared memory: J - r shuffles of each word per
+// element and no barrier, against two shared stores and two shared loads of
+// each word and four barriers.  Measured on GB300 (block sort at 2^28): 32-bit
+// keys gain up to four shuffle levels (1.84 -> 1.76 ms), elements of more than
+// one word up to two (u64 keys 4.27 -> 4.19 ms, u64 + u32 payload 11.03 ->
+// 10.69 ms; more levels were slower).
+template <typename K, bool PAIRS>
+__host__ __device__ constexpr int shuffle_levels() {
+  return (!PAIRS && sizeof(K) == 4) ? 4 : 2;
+}
+
+// One level J of the bitonic sort in BLK layout with its lane stages done by
+// shuffles.  The flip stage pairs element k with k ^ (2^J - 1): register e of
+// lane l meets register E-1-e of lane l ^ (2^(J-r) - 1); the lower lane (k bit
+// J-1 clear) keeps the minimum.  Then half-cleaners on lane bits, then the
+// register stages r-1 .. 0.
+template <int J, int NT, int FMA_BLK, int FMA_OTH, typename K, bool PAIRS, int E>
+__device__ __forceinline__ void sort_level_shuffle(Frag<K, PAIRS, E>& f) {
+  constexpr int r = ilog2(E);
+  static_assert(J > r && J - r <= 5, "lane stages only");
+  const uint32_t lane = threadIdx.x & 31u;
+  {
+    constexpr uint32_t m = (1u << (J - r)) - 1u;
+    const bool upper = ((lane >> (J - 1 - r)) & 1u) != 0;
+#pragma unroll
+    for (int e = 0; e < E / 2; ++e) {
+      const LaneVal<K, PAIRS, E> y1 = lane_fetch(f, E - 1 - e, m);  // meets my e
+      const LaneVal<K, PAIRS, E> y2 = lane_fetch(f, e, m);          // meets my E-1-e
+      lane_keep(f, e, y1, upper);
+      lane_keep(f, E - 1 - e, y2, upper);
+    }
+  }
+#pragma unroll
+  for (int b = J - 2; b >= r; --b) {
+    const uint32_t m = 1u << (b - r);
+    const bool upper = (lane & m) != 0;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const LaneVal<K, PAIRS, E> y = lane_fetch(f, e, m);
+      lane_keep(f, e, y, upper);
+    }
+  }
+  stages<kBLK, r - 1, 0, NT, FMA_BLK>(f);
+}
+
 // One level J of the bitonic sort (r < J <= t): the tile's blocks of 2^(J-1)
 // are ascending; merge pairs of them into ascending blocks of 2^J.  Enters and
-// leaves in BLK layout.
-template <int J, int NT, int FMA_BLK, typename K, bool PAIRS, int E>
+// leaves in BLK layout.  Low levels use lane shuffles (above).  A level whose
+// top bit lies in the MID window [r, 2r) needs two layout changes (BLK -> MID
+// -> BLK); only a level whose top bit lies above it goes through STR (three).
+template <int J, int NT, int FMA_BLK, int FMA_OTH, typename K, bool PAIRS, int E>
 __device__ __forceinline__ void sort_level(Frag<K, PAIRS, E>& f, uint32_t* sm) {
   using G = Geo<E, NT>;
   constexpr int r = G::r, t = G::t, top = J - 1;
-  if constexpr (top >= t - r) {
+  if constexpr (J - r <= shuffle_levels<K, PAIRS>()) {
+    sort_level_shuffle<J, NT, FMA_BLK, FMA_OTH>(f);
+    return;
+  } else if constexpr (top >= 2 * r) {
     relayout<kBLK, kSTR, J, NT>(f, sm);
-    stages<kSTR, top, t - r, NT>(f);
+    stages<kSTR, top, t - r, NT, FMA_OTH>(f);
     if constexpr (t - r - 1 >= r) {
       relayout<kSTR, kMID, 0, NT>(f, sm);
-      stages<kMID, t - r - 1, r, NT>(f);
+      stages<kMID, t - r - 1, r, NT, FMA_OTH>(f);
       relayout<kMID, kBLK, 0, NT>(f, sm);
     } else {
       relayout<kSTR, kBLK, 0, NT>(f, sm);
     }
   } else {
     relayout<kBLK, kMID, J, NT>(f, sm);
-    stages<kMID, top, r, NT>(f);
+    stages<kMID, top, r, NT, FMA_OTH>(f);
     relayout<kMID, kBLK, 0, NT>(f, sm);
   }
   stages<kBLK, r - 1, 0, NT, FMA_BLK>(f);
 }
 
-template <int J, int NT, int FMA_BLK, typename K, bool PAIRS, int E,
+template <int J, int NT, int FMA_BLK, int FMA_OTH, typename K, bool PAIRS, int E,
           bool DONE = (J > ilog2(E * NT))>
 struct SortLevels {
   __device__ static __forceinline__ void run(Frag<K, PAIRS, E>& f, uint32_t* sm) {
-    sort_level<J, NT, FMA_BLK>(f, sm);
-    SortLevels<J + 1, NT, FMA_BLK, K, PAIRS, E>::run(f, sm);
+    sort_level<J, NT, FMA_BLK, FMA_OTH>(f, sm);
+    SortLevels<J + 1, NT, FMA_BLK, FMA_OTH, K, PAIRS, E>::run(f, sm);
   }
 };
-template <int J, int NT, int FMA_BLK, typename K, bool PAIRS, int E>
-struct SortLevels<J, NT, FMA_BLK, K, PAIRS, E, true> {
+template <int J, int NT, int FMA_BLK, int FMA_OTH, typename K, bool PAIRS, int E>
+struct SortLevels<J, NT, FMA_BLK, FMA_OTH, K, PAIRS, E, true> {
   __device__ static __forceinline__ void run(Frag<K, PAIRS, E>&, uint32_t*) {}
 };
 
 // Sort of the whole CTA tile: each thread's registers with Batcher's network
 // (levels 1..r), then levels r+1..t; ascending result in BLK layout.
-// FMA_BLK: the kFma* forms of the BLK stages (Frag::one must be set).
-template <int NT, int FMA_BLK = 0, typename K, bool PAIRS, int E>
+// FMA_BLK / FMA_OTH: the compare-exchange forms of the BLK stages / of the
+// per-thread network and the other stages (Frag::one must be set when either
+// is non-zero).
+template <int NT, int FMA_BLK = 0, int FMA_OTH = 0, typename K, bool PAIRS, int E>
 __device__ __forceinline__ void block_sort_tile(Frag<K, PAIRS, E>& f, uint32_t* sm) {
-  thread_sort(f, false);
-  SortLevels<ilog2(E) + 1, NT, FMA_BLK, K, PAIRS, E>::run(f, sm);
+  thread_sort<FMA_OTH>(f, false);
+  SortLevels<ilog2(E) + 1, NT, FMA_BLK, FMA_OTH, K, PAIRS, E>::run(f, sm);
 }
 
 }  // namespace bcf

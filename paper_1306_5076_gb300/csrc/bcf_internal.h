@@ -60,6 +60,7 @@ struct MergeArgs {
   uint32_t* vout;
   uint64_t n;           // regular mode: elements of the array
   uint64_t run;         // regular mode: run length L (pairs of runs are 2L apart)
+  uint32_t run_log2;    // regular mode: log2 L (L is a power of two)
   uint64_t* splits;     // per work item: A-split at the item's first output diagonal
   int mode_in;
   int mode_out;
@@ -90,6 +91,8 @@ bool block_cfg_supported(int key_bytes, bool pairs, int cfg);
 bool merge_cfg_supported(int key_bytes, bool pairs, int cfg);
 
 // ---------------------------------------------------------------- sort workspace
+
+constexpr int ilog2_u64(uint64_t x) { return x <= 1 ? 0 : 1 + ilog2_u64(x >> 1); }
 
 constexpr size_t kAlign = 256;
 constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }

@@ -10,8 +10,9 @@
 // so every CTA does the same amount of work in every pass, which is what the
 // paper's distribution step is for.  The CTA then
 //   1. stages its A-window and B-window into shared memory with bulk copies
-//      (cp.async.bulk, completion on an mbarrier; 16-byte-misaligned edges
-//      are read with plain loads);
+//      (cp.async.bulk, completion on an mbarrier), each rounded out to whole
+//      16-byte blocks (only the array's last partial block is read with plain
+//      loads);
 //   2. reads the bitonic sequence [pads_min, A, pads_max, reversed B] into
 //      registers in STR layout (a warp reads 32 consecutive shared words;
 //      rows that contain both A- and B-lanes issue two predicated loads so
@@ -46,8 +47,8 @@ __device__ __forceinline__ Piece piece_regular(const MergeArgs& a, uint64_t item
   Piece p;
   const uint64_t L = a.run;
   const uint64_t out0 = item * static_cast<uint64_t>(Tm);
-  const uint64_t pair = out0 / (2 * L);
-  p.src = pair * 2 * L;
+  // runs are powers of two long: the pair's start is out0 rounded down to 2L
+  p.src = (out0 >> (a.run_log2 + 1)) << (a.run_log2 + 1);
   const uint64_t left = a.n - p.src;
   p.na_tot = left < L ? left : L;
   const uint64_t rest = left - p.na_tot;
@@ -206,32 +207,51 @@ __global__ void __launch_bounds__(256) partition_kernel(const MergeArgs a, int T
   a.splits[item] = merge_path_bs<K, MAP>(A, B, d, lo, hi, a.mode_in);
 }
 
-// Stage elements [g0, g1) of `src` (absolute indices; src 16-byte aligned)
-// into shared memory at `dst` (16-byte aligned) so that element x lands at
-// dst[x - align_down(g0)].  The 16-byte-aligned body goes by one bulk copy
-// issued by the calling thread; the ragged tail is left to stage_tail().
+// Stage elements [g0, g1) of `src` (absolute indices into an array of n
+// elements; src 16-byte aligned) into shared memory at `dst` (16-byte
+// aligned) so that element x lands at dst[x - align_down(g0)].  The bulk copy
+// covers the window rounded out to whole 16-byte blocks: the up to V - 1
+// elements it reads before g0 and after g1 belong to the same array (the
+// neighbouring window) and are never used.  Only where rounding up would pass
+// the array's end is the ragged tail left out of the copy and staged by
+// stage_tail() -- in the last window of the array alone -- so the CTA's own
+// shared stores never overlap its bulk copies anywhere else.
 template <typename T>
-__device__ __forceinline__ uint32_t body_bytes(uint64_t g0, uint64_t g1) {
+__device__ __forceinline__ uint64_t bulk_end(uint64_t g1, uint64_t n) {
   constexpr uint64_t V = 16 / sizeof(T);
-  const uint64_t a0 = g0 & ~(V - 1), a1 = g1 & ~(V - 1);
+  const uint64_t up = (g1 + V - 1) & ~(V - 1);
+  return up <= n ? up : (g1 & ~(V - 1));
+}
+template <typename T>
+__device__ __forceinline__ uint32_t body_bytes(uint64_t g0, uint64_t g1, uint64_t n) {
+  constexpr uint64_t V = 16 / sizeof(T);
+  const uint64_t a0 = g0 & ~(V - 1), a1 = bulk_end<T>(g1, n);
   return (g1 > g0 && a1 > a0) ? static_cast<uint32_t>((a1 - a0) * sizeof(T)) : 0u;
 }
 template <typename T>
 __device__ __forceinline__ void stage_bulk(T* dst, const T* src, uint64_t g0, uint64_t g1,
-                                           uint64_t* bar) {
+                                           uint64_t n, uint64_t* bar) {
   constexpr uint64_t V = 16 / sizeof(T);
-  const uint32_t bytes = body_bytes<T>(g0, g1);
+  const uint32_t bytes = body_bytes<T>(g0, g1, n);
   if (bytes) bulk_g2s(dst, src + (g0 & ~(V - 1)), bytes, bar);
 }
+// The ragged tail of a window that ends in the array's last partial 16-byte
+// block: lanes [lane0, lane0 + V) of the calling warp copy its at most V - 1
+// elements.  Each window's tail is written by its own shared store
+// instruction (a predicated store that only those lanes issue), so the tails
+// of two windows never share a request.
 template <typename T>
 __device__ __forceinline__ void stage_tail(T* dst, const T* src, uint64_t g0, uint64_t g1,
-                                           uint32_t lane) {
+                                           uint64_t n, uint32_t lane, uint32_t lane0) {
   constexpr uint64_t V = 16 / sizeof(T);
-  if (g1 <= g0) return;
-  const uint64_t a0 = g0 & ~(V - 1), a1 = g1 & ~(V - 1);
+  const uint64_t a0 = g0 & ~(V - 1), a1 = bulk_end<T>(g1, n);
   const uint64_t t0 = a1 > g0 ? a1 : g0;
-  const uint64_t x = t0 + lane;
-  if (lane < V && x < g1) dst[x - a0] = src[x];
+  const uint64_t x = t0 + (lane - lane0);
+  const bool mine = g1 > g0 && lane >= lane0 && lane < lane0 + V && x < g1;
+  if (!__any_sync(0xFFFFFFFFu, mine)) return;  // no tail here (every window but the last)
+  T v = 0;
+  if (mine) v = src[x];
+  sts_pred(dst + (mine ? x - a0 : 0), mine, v);
 }
 
 template <typename K, bool PAIRS, int E, int NT>
@@ -310,14 +330,16 @@ __global__ void __launch_bounds__(NT) merge_kernel(const MergeArgs a,
     mbar_init(bar, 1);
     fence_mbar_init();
     // the total byte count is announced before any copy can complete
-    uint32_t total = body_bytes<K>(ga0, ga1) + body_bytes<K>(gb0, gb1);
-    if constexpr (PAIRS) total += body_bytes<uint32_t>(ga0, ga1) + body_bytes<uint32_t>(gb0, gb1);
+    const uint64_t n = a.n;
+    uint32_t total = body_bytes<K>(ga0, ga1, n) + body_bytes<K>(gb0, gb1, n);
+    if constexpr (PAIRS)
+      total += body_bytes<uint32_t>(ga0, ga1, n) + body_bytes<uint32_t>(gb0, gb1, n);
     mbar_arrive_expect_tx(bar, total);
-    stage_bulk(smA, kin, ga0, ga1, bar);
-    stage_bulk(smB, kin, gb0, gb1, bar);
+    stage_bulk(smA, kin, ga0, ga1, n, bar);
+    stage_bulk(smB, kin, gb0, gb1, n, bar);
     if constexpr (PAIRS) {
-      stage_bulk(svA, a.vin, ga0, ga1, bar);
-      stage_bulk(svB, a.vin, gb0, gb1, bar);
+      stage_bulk(svA, a.vin, ga0, ga1, n, bar);
+      stage_bulk(svB, a.vin, gb0, gb1, n, bar);
     }
     // one thread waits (bounded); the barrier below releases the others
     bool ok = mbar_wait_bounded(bar, 0, a.err, kErrTmaTimeout, a.wait_ns);
@@ -325,11 +347,14 @@ __global__ void __launch_bounds__(NT) merge_kernel(const MergeArgs a,
     s_ok = ok ? 1 : 0;
   } else if (tid >= 32 && tid < 64) {
     const uint32_t lane = tid - 32;
-    // lanes 0-7: A keys, 8-15: B keys, 16-23: A values, 24-31: B values
-    if (lane < 8) stage_tail(smA, kin, ga0, ga1, lane);
-    else if (lane < 16) stage_tail(smB, kin, gb0, gb1, lane - 8);
-    else if (PAIRS && lane < 24) stage_tail(svA, a.vin, ga0, ga1, lane - 16);
-    else if (PAIRS) stage_tail(svB, a.vin, gb0, gb1, lane - 24);
+    // lanes 0-7: A keys, 8-15: B keys, 16-23: A values, 24-31: B values, one
+    // store instruction per window
+    stage_tail(smA, kin, ga0, ga1, a.n, lane, 0);
+    stage_tail(smB, kin, gb0, gb1, a.n, lane, 8);
+    if constexpr (PAIRS) {
+      stage_tail(svA, a.vin, ga0, ga1, a.n, lane, 16);
+      stage_tail(svB, a.vin, gb0, gb1, a.n, lane, 24);
+    }
   }
   __syncthreads();
   if (!s_ok) return;
@@ -362,10 +387,9 @@ __global__ void __launch_bounds__(NT) merge_kernel(const MergeArgs a,
     }
   }
 
-  // FMA-pipe forms in the BLK stages (32-bit keys; kFmaKeys64 measured 3 %
-  // slower here)
   f.one = g_unit_multiplier;
-  bitonic_merge_str<NT, kFmaKeys | kFmaPairs>(f, reinterpret_cast<uint32_t*>(body));
+  bitonic_merge_str<NT, CeForms<K, PAIRS>::kMergeBlk, CeForms<K, PAIRS>::kMergeOth>(
+      f, reinterpret_cast<uint32_t*>(body));
   // samples of the output for the next pass's merge-path search: the keys at
   // array positions that are multiples of S, still in mapped order (a pass
   // with a successor writes no unmapped keys)

@@ -442,6 +442,7 @@ __device__ __forceinline__ void seg_worker_body(const SegArgs& a) {
   __shared__ SegWork s_w;
   __shared__ int s_go;
   __shared__ int s_publish;
+  __shared__ unsigned long long s_base;
   __shared__ uint64_t s_split[2];
   const uint32_t tid = threadIdx.x;
   for (;;) {
@@ -491,23 +492,26 @@ __device__ __forceinline__ void seg_worker_body(const SegArgs& a) {
       // last item of this pass: the CTA finds the next pass's splits, then
       // publishes the segment's next pass
       if (splits_published<NT>(g)) publish_splits<K, NT>(a, g, w.seg, pass + 1, T);
-      __syncthreads();
+      const uint32_t m = g.pieces;
       if (tid == 0) {
-        const uint32_t m = g.pieces;
         a.items_left[w.seg] = m;
-        const unsigned long long base = atomicAdd(&a.ctl->reserve, static_cast<unsigned long long>(m));
-        if (base + m > a.capacity) {
-          atomicOr(a.err, kErrQueueOverflow);
-        } else {
-          for (uint32_t j = 0; j < m; ++j) {
-            a.queue[base + j].seg = w.seg;
-            a.queue[base + j].arg = j;
-          }
-          __threadfence();
-          for (uint32_t j = 0; j < m; ++j)
-            *const_cast<volatile uint32_t*>(&a.queue[base + j].meta) =
-                kReady | ((pass + 1) << 8) | kWPiece;
+        s_base = atomicAdd(&a.ctl->reserve, static_cast<unsigned long long>(m));
+        if (s_base + m > a.capacity) atomicOr(a.err, kErrQueueOverflow);
+      }
+      __syncthreads();
+      // every thread publishes a share of the pass's slots: each writes its
+      // slots' contents, makes them visible, then sets their ready bits (a
+      // segment of 2^31 keys publishes 524,288 slots per pass)
+      const unsigned long long base = s_base;
+      if (base + m <= a.capacity) {
+        for (uint32_t j = tid; j < m; j += NT) {
+          a.queue[base + j].seg = w.seg;
+          a.queue[base + j].arg = j;
         }
+        __threadfence();
+        for (uint32_t j = tid; j < m; j += NT)
+          *const_cast<volatile uint32_t*>(&a.queue[base + j].meta) =
+              kReady | ((pass + 1) << 8) | kWPiece;
       }
     }
     __syncthreads();

@@ -196,7 +196,7 @@ def simulate_block_sort(g, vals):
     r, t = g.r, g.t
     for J in range(r + 1, t + 1):
         top = J - 1
-        if top >= t - r:
+        if top >= 2 * r:  # the level's top bit lies above the MID window
             X = simulate_relayout(g, X, BLK, STR, J)
             simulate_stages(g, X, STR, top, t - r)
             if t - r - 1 >= r:
@@ -277,3 +277,28 @@ def test_simulated_merge_of_random_runs(E, NT):
         seqs.append(np.concatenate([A, B[::-1]]))
     seqs = np.array(seqs)
     assert np.array_equal(simulate_merge(g, seqs), np.sort(seqs, axis=1))
+
+
+@pytest.mark.parametrize("E", [16, 32])
+def test_lane_shuffle_levels_pair_the_bitonic_partners(E):
+    """The block sort's low levels exchange elements between lanes (BLK
+    layout, k = tid*E + e): the flip stage of level J pairs register e of
+    lane l with register E-1-e of lane l ^ (2^(J-r) - 1), a half-cleaner on
+    lane bit b-r pairs lanes l and l ^ 2^(b-r) at the same register, and the
+    lane with k bit J-1 (resp. b) set keeps the maximum.  These must be the
+    bitonic network's partners k ^ (2^J - 1) and k ^ 2^b."""
+    r = E.bit_length() - 1
+    for J in range(r + 1, r + 6):
+        m = (1 << (J - r)) - 1
+        for tid in range(64):
+            lane, warp = tid & 31, tid >> 5
+            for e in range(E):
+                k = tid * E + e
+                pk = ((warp << 5) | (lane ^ m)) * E + (E - 1 - e)
+                assert pk == k ^ ((1 << J) - 1)
+                assert (((lane >> (J - 1 - r)) & 1) == 1) == bool(k >> (J - 1) & 1)
+                for b in range(J - 2, r - 1, -1):
+                    mb = 1 << (b - r)
+                    pk = ((warp << 5) | (lane ^ mb)) * E + e
+                    assert pk == k ^ (1 << b)
+                    assert ((lane & mb) != 0) == bool(k >> b & 1)
