@@ -63,7 +63,8 @@ def source_digest(files):
 
 
 MERGE_SOURCES = ["paper_1306_5076_gb300/csrc/bcf_merge.cu",
-                 "paper_1306_5076_gb300/csrc/bcf_device.cuh"]
+                 "paper_1306_5076_gb300/csrc/bcf_device.cuh",
+                 "paper_1306_5076_gb300/csrc/bcf_internal.h"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "merge_kernel_u32_traffic.json.txt")
 
 

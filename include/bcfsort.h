@@ -79,19 +79,27 @@ typedef enum {
  * result; they differ in speed by input distribution. */
 enum {
     BCF_ALGO_MERGE = 0,        /* block sort + ceil(log2(n / T)) merge passes (Sec. 3.2) */
-    BCF_ALGO_PIVOT_BUCKETS = 1 /* BCFMergesortPB (Sec. 3.2, "Duplicate keys"): the block
+    BCF_ALGO_PIVOT_BUCKETS = 1, /* BCFMergesortPB (Sec. 3.2, "Duplicate keys"): the block
                                 * sort, then a distribution into 255 splitter buckets
                                 * plus one bucket per splitter for the keys equal to it;
                                 * the equal buckets are final, the others are sorted by
                                 * the segmented sort.  Fastest on duplicate-heavy keys;
                                 * needs bcf_workspace_bytes(BCF_OP_SORT_PB, ...) and
                                 * n < 2^32 (larger n takes the merge path). */
+    BCF_ALGO_AUTO = 2          /* one of the two, chosen per call: every 4096th key is
+                                * sampled and sorted, splitters are picked from it as
+                                * pivot buckets would, and pivot buckets are taken when
+                                * at least 2/3 of the sample equals a splitter (most keys
+                                * would be final after one distribution), else the merge
+                                * path.  Needs the BCF_OP_SORT_PB workspace.  The decision
+                                * reads one word back to the host, so the call
+                                * synchronises `stream` once (not for graph capture). */
 };
 
 typedef struct {
     int descending;      /* 0: ascending, 1: descending (ties keep input order) */
     int stable_required; /* accepted for API symmetry; output is always stable */
-    int algorithm;       /* BCF_ALGO_MERGE (default) or BCF_ALGO_PIVOT_BUCKETS */
+    int algorithm;       /* BCF_ALGO_MERGE (default), BCF_ALGO_PIVOT_BUCKETS or BCF_ALGO_AUTO */
 } bcf_opts;              /* a NULL bcf_opts* means ascending, BCF_ALGO_MERGE */
 
 /* Operation codes for bcf_workspace_bytes. */
@@ -105,8 +113,8 @@ enum { BCF_OP_SORT = 0, BCF_OP_MERGE = 1, BCF_OP_SEGMENTED = 2, BCF_OP_CPS = 3,
  *             BCF_OP_SEGMENTED: nseg_or_k segments totalling n keys;
  *             BCF_OP_CPS: colored prefix sums of n elements with nseg_or_k
  *             colors (kt must be BCF_U32, has_vals 0);
- *             BCF_OP_SORT_PB: sort n keys with BCF_ALGO_PIVOT_BUCKETS (pairs if
- *             has_vals; also enough for BCF_ALGO_MERGE);
+ *             BCF_OP_SORT_PB: sort n keys with BCF_ALGO_PIVOT_BUCKETS or
+ *             BCF_ALGO_AUTO (pairs if has_vals; also enough for BCF_ALGO_MERGE);
  *             BCF_OP_SORT_HOST / BCF_OP_SORT_HOST_PB: bcf_sort_*_host with the
  *             merge / pivot-bucket algorithm;
  *             BCF_OP_SORT_WIDE: bcf_sort_pairs_wide (either algorithm; the
@@ -493,7 +501,8 @@ bcf_status bcf_arena_destroy(bcf_arena* a);
  *
  *   - n <= BCF_STATIC_MAX_KEYS, else BCF_EUNSUPPORTED before any launch; keys
  *     only; 16-bit keys are not available here (BCF_EUNSUPPORTED);
- *     BCF_ALGO_PIVOT_BUCKETS takes the merge path (same result); otherwise
+ *     BCF_ALGO_PIVOT_BUCKETS and BCF_ALGO_AUTO take the merge path (same
+ *     result); otherwise
  *     the arguments, results and errors of bcf_sort_keys (an unknown
  *     opts->algorithm is BCF_EINVAL).
  *   - The array (about 8 MiB) is held by every GPU that loads the library until

@@ -83,14 +83,14 @@ def _stream(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-_ALGORITHMS = {"merge": 0, "pivot_buckets": 1}
+_ALGORITHMS = {"merge": 0, "pivot_buckets": 1, "auto": 2}
 
 
 def _opts(descending: bool, algorithm: str = "merge"):
     try:
         algo = _ALGORITHMS[algorithm]
     except KeyError:
-        raise ValueError(f"unknown algorithm {algorithm!r} (merge, pivot_buckets)") from None
+        raise ValueError(f"unknown algorithm {algorithm!r} (merge, pivot_buckets, auto)") from None
     return ctypes.byref(_native.BcfOpts(int(bool(descending)), 1, algo))
 
 
@@ -108,7 +108,7 @@ def bcf_workspace_bytes(op: int, n: int, nseg_or_k: int, kt: int, has_vals: bool
 
 
 def _sort_op(algorithm: str) -> int:
-    return BCF_OP_SORT_PB if algorithm == "pivot_buckets" else BCF_OP_SORT
+    return BCF_OP_SORT_PB if algorithm in ("pivot_buckets", "auto") else BCF_OP_SORT
 
 
 def bcf_sort_keys(keys_out, keys_in, *, descending=False, ws=None, stream=None, kt=None,
@@ -163,7 +163,8 @@ def bcf_sort_keys_host(keys_out, keys_in, *, descending=False, ws=None, stream=N
 
     kt = key_dtype_of(keys_in) if kt is None else kt
     n = keys_in.numel()
-    op = _native.BCF_OP_SORT_HOST_PB if algorithm == "pivot_buckets" else _native.BCF_OP_SORT_HOST
+    op = (_native.BCF_OP_SORT_HOST_PB if algorithm in ("pivot_buckets", "auto")
+          else _native.BCF_OP_SORT_HOST)
     device = device or torch.device("cuda", torch.cuda.current_device())
     ws, wsb = _workspace(op, n, 0, kt, False, ws, device)
     _check(_native.load().bcf_sort_keys_host(_host_ptr(keys_out), _host_ptr(keys_in), n, kt,
@@ -180,7 +181,8 @@ def bcf_sort_pairs_host(keys_out, vals_out, keys_in, vals_in, *, descending=Fals
 
     kt = key_dtype_of(keys_in) if kt is None else kt
     n = keys_in.numel()
-    op = _native.BCF_OP_SORT_HOST_PB if algorithm == "pivot_buckets" else _native.BCF_OP_SORT_HOST
+    op = (_native.BCF_OP_SORT_HOST_PB if algorithm in ("pivot_buckets", "auto")
+          else _native.BCF_OP_SORT_HOST)
     device = device or torch.device("cuda", torch.cuda.current_device())
     ws, wsb = _workspace(op, n, 0, kt, True, ws, device)
     _check(_native.load().bcf_sort_pairs_host(_host_ptr(keys_out), _host_ptr(vals_out),

@@ -16,7 +16,7 @@ BCF_U32, BCF_U64, BCF_F32, BCF_I32, BCF_I64, BCF_F64, BCF_U16, BCF_I16 = 0, 1, 2
 BCF_CPS_BANKED, BCF_CPS_ROWS = 0, 1
 (BCF_OP_SORT, BCF_OP_MERGE, BCF_OP_SEGMENTED, BCF_OP_CPS, BCF_OP_SORT_PB, BCF_OP_SORT_HOST,
  BCF_OP_SORT_HOST_PB, BCF_OP_SORT_WIDE) = 0, 1, 2, 3, 4, 5, 6, 7
-BCF_ALGO_MERGE, BCF_ALGO_PIVOT_BUCKETS = 0, 1
+BCF_ALGO_MERGE, BCF_ALGO_PIVOT_BUCKETS, BCF_ALGO_AUTO = 0, 1, 2
 STATUS = {0: "BCF_OK", 1: "BCF_EINVAL", 2: "BCF_ENOMEM", 3: "BCF_ECUDA", 4: "BCF_ETIMEOUT",
           5: "BCF_EUNSUPPORTED"}
 

@@ -17,6 +17,7 @@ bool block_cfg_supported(int key_bytes, bool pairs, int cfg) {
   if (cfg < 0 || cfg >= kNumBlockCfgs) return false;
   if (key_bytes != 4 && key_bytes != 8) return false;
   if (pairs && key_bytes == 8) return kBlockCfgs[cfg].E == 16;
+  if (kBlockCfgs[cfg].NT > 512) return !pairs && key_bytes == 4;
   return true;
 }
 

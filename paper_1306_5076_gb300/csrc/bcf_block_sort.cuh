@@ -162,6 +162,9 @@ cudaError_t launch_block_sort_typed(int cfg, const BlockSortArgs& a, cudaStream_
     case 3:
       if constexpr (!(PAIRS && sizeof(K) == 8)) return launch_bs<K, PAIRS, 32, 128>(a, s);
       break;
+    case 4:
+      if constexpr (!PAIRS && sizeof(K) == 4) return launch_bs<K, PAIRS, 32, 1024>(a, s);
+      break;
     default: break;
   }
   return cudaErrorInvalidValue;

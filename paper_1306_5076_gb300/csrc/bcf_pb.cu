@@ -44,7 +44,7 @@ template <typename K, bool MAP>
 __global__ void pb_sample_kernel(const PbArgs a) {
   const uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= a.ns) return;
-  const K x = static_cast<const K*>(a.kin)[i * kPbSampleStride];
+  const K x = static_cast<const K*>(a.kin)[i * a.sample_stride];
   static_cast<K*>(a.samples)[i] = MAP ? map_key(x, a.mode) : x;
 }
 
@@ -242,6 +242,26 @@ __global__ void __launch_bounds__(kPbThreads) pb_scatter_kernel(const PbArgs a) 
   }
 }
 
+// How many sorted samples equal one of the m splitters (binary search of the
+// splitters per sample): the share of keys that would land in equal buckets.
+template <typename K>
+__global__ void __launch_bounds__(kPbThreads) pb_equal_count_kernel(const PbArgs a) {
+  const uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  bool eq = false;
+  if (i < a.ns) {
+    const K v = static_cast<const K*>(a.sorted_samples)[i];
+    const K* sp = static_cast<const K*>(a.splitters);
+    uint32_t lo = 0, hi = *a.nsplit;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (sp[mid] < v) lo = mid + 1; else hi = mid;
+    }
+    eq = lo < *a.nsplit && sp[lo] == v;
+  }
+  const int cnt = __syncthreads_count(eq);
+  if (threadIdx.x == 0 && cnt) atomicAdd(a.equal_count, static_cast<uint32_t>(cnt));
+}
+
 __global__ void pb_segoff_kernel(const PbArgs a) {
   for (uint32_t b = threadIdx.x; b < kPbBuckets; b += blockDim.x)
     a.seg_off[b] = a.offsets[static_cast<uint64_t>(b) * a.ntiles];  // tile 0's piece: bucket start
@@ -283,6 +303,11 @@ cudaError_t launch_pb_typed(int step, bool pairs, const PbArgs& a, cudaStream_t 
     case kPbStepSegOffsets:
       pb_segoff_kernel<<<1, 512, 0, s>>>(a);
       break;
+    case kPbStepEqualCount: {
+      const unsigned grid = static_cast<unsigned>((a.ns + kPbThreads - 1) / kPbThreads);
+      pb_equal_count_kernel<K><<<grid, kPbThreads, 0, s>>>(a);
+      break;
+    }
     default:
       return cudaErrorInvalidValue;
   }

@@ -63,11 +63,13 @@ extern "C" bcf_status bcf_sort_keys_static(void* keys_out, const void* keys_in, 
   if (n > kMaxKeys) return BCF_EUNSUPPORTED;
   // 16-bit keys need widened copies the static array has no room for
   if (kt == BCF_U16 || kt == BCF_I16) return BCF_EUNSUPPORTED;
-  // the static array is sized for the merge path: pivot buckets take it too;
-  // any other algorithm value reaches bcf_sort_keys and is rejected there
+  // the static array is sized for the merge path: pivot buckets and the
+  // automatic choice take it too; any other algorithm value reaches
+  // bcf_sort_keys and is rejected there
   bcf_opts o{};
   if (opts) o = *opts;
-  if (o.algorithm == BCF_ALGO_PIVOT_BUCKETS) o.algorithm = BCF_ALGO_MERGE;
+  if (o.algorithm == BCF_ALGO_PIVOT_BUCKETS || o.algorithm == BCF_ALGO_AUTO)
+    o.algorithm = BCF_ALGO_MERGE;
   if (n == 0) return bcf_sort_keys(keys_out, keys_in, 0, kt, &o, nullptr, 0, stream);
   void* ws = static_workspace();
   if (!ws) return BCF_ECUDA;

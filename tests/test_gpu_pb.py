@@ -124,3 +124,40 @@ def test_large_duplicate_heavy_against_oracle(bcf):
     gk, gv = pb_sort(bcf, keys, vals)
     ek, ev = oracle.sort(keys, vals, nthreads=os.cpu_count() or 8)
     assert np.array_equal(gk, ek) and np.array_equal(gv, ev)
+
+
+@pytest.mark.parametrize("dist,expect_pb", [("distinct16", True), ("uniform", False),
+                                            ("sorted", False)])
+@pytest.mark.parametrize("pairs", [False, True])
+def test_auto_chooses_by_duplication_and_matches_the_oracle(bcf, dist, expect_pb, pairs):
+    """algorithm="auto": pivot buckets when most sampled keys equal a splitter
+    (16 distinct values), the merge path otherwise; the result is the oracle's
+    either way.  The choice shows in the library's launch records: the
+    decision itself launches three distribution-kind kernels (sample,
+    splitters, count), the pivot-bucket sort five more."""
+    n = (1 << 21) + 777
+    keys = workloads.keys(dist, "u32", n)
+    vals = workloads.row_index(n) if pairs else None
+    bcf.bcf_profile_collect()
+    bcf.bcf_profile_enable(True)
+    try:
+        got_k, got_v = pb_sort(bcf, keys, vals, algorithm="auto")
+    finally:
+        bcf.bcf_profile_enable(False)
+    prof = bcf.bcf_profile_collect()
+    ek, ev = oracle.sort(keys, vals)
+    assert np.array_equal(bits(got_k), bits(ek))
+    if pairs:
+        assert np.array_equal(got_v, ev)
+    distribution_launches = prof["pivot_buckets"]["launches"]
+    assert distribution_launches == (8 if expect_pb else 3), prof
+
+
+def test_auto_with_16_bit_and_descending_keys(bcf):
+    n = (1 << 20) + 3
+    for dtype, dist in (("i16", "distinct16"), ("u16", "uniform"), ("f32", "distinct16")):
+        keys = workloads.keys(dist, dtype, n)
+        for desc in (False, True):
+            got, _ = pb_sort(bcf, keys, descending=desc, algorithm="auto")
+            exp, _ = oracle.sort(keys, descending=desc)
+            assert np.array_equal(bits(got), bits(exp)), (dtype, dist, desc)

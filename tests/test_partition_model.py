@@ -113,3 +113,4 @@ def test_irregular_merge_writes_every_sample_once():
         hi = int(offs[-1])
         expect = list(range((lo + S - 1) // S * S, hi, S))
         assert sorted(written) == expect, trial
+
