@@ -308,7 +308,18 @@ __global__ void __launch_bounds__(NT) merge_kernel(const MergeArgs a,
   const uint64_t item = first_item<IRREG>(pl) + blockIdx.x;
   const Piece p = piece_of<IRREG>(a, pl, item, Tm);
   const uint64_t i0 = a.splits[item];
-  const uint64_t i1 = p.last ? p.na_tot : a.splits[item + 1];
+  // For sorted runs the splits grow with the diagonal and nothing below
+  // changes i1.  Runs that are not sorted (a broken precondition of
+  // bcf_merge_runs) can make neighbouring searches disagree; clamping i1 into
+  // the windows i0 allows keeps every staged window inside its run and within
+  // the tile's shared memory, so such input gives an undefined order but
+  // never an out-of-bounds access.
+  uint64_t i1 = p.last ? p.na_tot : a.splits[item + 1];
+  {
+    const uint64_t lo1 = p.d1 > p.nb_tot && p.d1 - p.nb_tot > i0 ? p.d1 - p.nb_tot : i0;
+    const uint64_t hi1 = i0 + (p.d1 - p.d0) < p.na_tot ? i0 + (p.d1 - p.d0) : p.na_tot;
+    i1 = i1 < lo1 ? lo1 : (i1 > hi1 ? hi1 : i1);
+  }
   const uint64_t j0 = p.d0 - i0, j1 = p.d1 - i1;
   const uint32_t na = static_cast<uint32_t>(i1 - i0), nb = static_cast<uint32_t>(j1 - j0);
   const uint32_t front = p.front;

@@ -389,17 +389,34 @@ __device__ __forceinline__ void merge_piece_item(const SegArgs& a, const SegGeo&
   const uint32_t front = static_cast<uint32_t>(ps - gt * T);
   const uint32_t endA = front + wa, begB = static_cast<uint32_t>(T) - wb;
   const uint64_t ja = A0 + i0, jb = A1 + (d0 - i0);  // first A / B window element
+  // Per-thread bases, so that slot k = e*NT + tid of the sequence is read at a
+  // base plus the compile-time offset e*NT: A[k - front] from pA[e*NT],
+  // reversed B[T-1-k] from pB[-e*NT].  (Integer arithmetic: a base may lie
+  // outside the arrays; only slots of the windows are dereferenced.)
+  const auto at = [](const void* base, uint64_t idx, uint64_t bytes) {
+    return reinterpret_cast<uintptr_t>(base) + idx * bytes;
+  };
+  const uint64_t ia = ja + tid - front, ib = jb + (T - 1) - tid;
+  const K* pA = reinterpret_cast<const K*>(at(src, ia, sizeof(K)));
+  const K* pB = reinterpret_cast<const K*>(at(src, ib, sizeof(K)));
+  const uint32_t* qA = PAIRS ? reinterpret_cast<const uint32_t*>(at(vsrc, ia, 4)) : nullptr;
+  const uint32_t* qB = PAIRS ? reinterpret_cast<const uint32_t*>(at(vsrc, ib, 4)) : nullptr;
+  const uint32_t rel0 = tid - front;  // k - front at e = 0 (wraps for k < front)
   Frag<K, PAIRS, E> f;
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const uint32_t k = e * NT + tid;
-    const bool isA = k >= front && k < endA, isB = k >= begB;
-    const uint64_t pos = isA ? ja + (k - front) : jb + (T - 1 - k);
+    const bool isA = rel0 + static_cast<uint32_t>(e * NT) < wa;  // front <= k < endA
+    const bool isB = k >= begB;
     K x = k < front ? KeyLimits<K>::kMin : KeyLimits<K>::kMax;
-    if (isA || isB) x = __ldcg(src + pos);
+    if (isA) x = __ldcg(pA + e * NT);
+    else if (isB) x = __ldcg(pB - e * NT);
     f.k[e] = x;
     if constexpr (PAIRS) {
-      f.v[e] = (isA || isB) ? __ldcg(vsrc + pos) : 0u;
+      uint32_t v = 0u;
+      if (isA) v = __ldcg(qA + e * NT);
+      else if (isB) v = __ldcg(qB - e * NT);
+      f.v[e] = v;
       f.ix[e] = isB ? endA + (static_cast<uint32_t>(T) - 1 - k) : (k < endA ? k : T + k);
     }
   }

@@ -118,3 +118,30 @@ def test_runs_not_starting_at_zero(bcf):
     gk, gv = from_dev(ko, np.uint32), from_dev(vo, np.uint32)
     assert np.array_equal(gk[3:], ek[3:]) and np.array_equal(gv[3:], ev[3:])
     assert np.all(gk[:3] == 0) and np.all(gv[:3] == 0)  # outside the runs: untouched
+
+
+def test_unsorted_runs_stay_in_bounds(bcf):
+    """Runs that are not sorted break bcf_merge_runs' precondition: the order
+    of the output is then undefined, but every access stays inside the runs
+    and the tiles' shared memory (the merge kernel clamps each tile's end
+    split into what its start split allows).  The call completes, reports no
+    device error, and the context sorts exactly afterwards."""
+    r = np.random.default_rng(99)
+    for k, total in ((2, 50_000), (5, 300_001), (64, (1 << 20) + 3)):
+        keys = workloads.keys("uniform", "u32", total, seed=int(r.integers(1 << 30)))
+        cuts = np.sort(r.choice(np.arange(1, total), size=k - 1, replace=False))
+        offs = np.concatenate([[0], cuts, [total]]).astype(np.uint64)
+        vals = workloads.row_index(total)
+        kd, vd = to_dev(keys), to_dev(vals)
+        ko, vo = torch.empty_like(kd), torch.empty_like(vd)
+        bcf.bcf_merge_runs(ko, vo, kd, vd, [int(x) for x in offs], kt=0)
+        bcf.bcf_merge_runs(ko, None, kd, None, [int(x) for x in offs], kt=0)
+        torch.cuda.synchronize()
+        assert bcf.bcf_last_device_error() == 0
+    keys = workloads.keys("uniform", "u32", 100_000, seed=3)
+    kd = to_dev(keys)
+    ko = torch.empty_like(kd)
+    bcf.bcf_sort_keys(ko, kd, kt=0)
+    torch.cuda.synchronize()
+    exp, _ = oracle.sort(keys)
+    assert np.array_equal(from_dev(ko, np.uint32), exp)
