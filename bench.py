@@ -506,8 +506,8 @@ def cps_bench(torch, dev, bcf, peak, log2n=29, colors=(1, 2, 4, 8, 16, 32, 64)):
 
 def pb_bench(torch, dev, bcf, log2n=LOG2N):
     """Pivot buckets (BCFMergesortPB) against the merge passes on the paper's
-    duplicate-heavy inputs and on distinct keys: whole-sort time, 2^log2n u32
-    keys, keys only and pairs."""
+    duplicate-heavy inputs and on distinct keys, and the automatic choice
+    between them: whole-sort time, 2^log2n u32 keys, keys only and pairs."""
     import numpy as np
 
     import workloads
@@ -526,7 +526,7 @@ def pb_bench(torch, dev, bcf, log2n=LOG2N):
             ws = torch.empty(bcf.bcf_workspace_bytes(bcf.BCF_OP_SORT_PB, n, 0, bcf.BCF_U32, pairs),
                              dtype=torch.uint8, device=dev)
             row = {}
-            for algo in ("merge", "pivot_buckets"):
+            for algo in ("merge", "pivot_buckets", "auto"):
                 if pairs:
                     fn = lambda: bcf.bcf_sort_pairs(ko, vo, kd, vd, kt=bcf.BCF_U32, ws=ws,  # noqa: E731
                                                     stream=stream, algorithm=algo)
@@ -536,6 +536,8 @@ def pb_bench(torch, dev, bcf, log2n=LOG2N):
                 ms = timed_ms(torch, stream, fn, warmup=2, reps=5)
                 row[algo] = {"ms": ms, "keys_per_s": n / (ms * 1e-3)}
             row["speedup"] = row["merge"]["ms"] / row["pivot_buckets"]["ms"]
+            # the automatic choice against the faster of the two (1.0 = as fast)
+            row["auto_vs_best"] = min(row["merge"]["ms"], row["pivot_buckets"]["ms"]) / row["auto"]["ms"]
             out[name + ("+u32" if pairs else "")] = row
             del vd, vo, ws
             torch.cuda.empty_cache()
@@ -963,6 +965,7 @@ def summary_of(line, peak):
     pb = line.get("pivot_buckets")
     if pb:
         s["pivot_bucket_speedup"] = {k: r3(v["speedup"]) for k, v in pb["results"].items()}
+        s["auto_vs_best"] = {k: r3(v["auto_vs_best"]) for k, v in pb["results"].items()}
     cps = line.get("colored_prefix_sums")
     if cps:
         s["cps_frac_banked"] = {d: r3(v["frac"]) for d, v in cps["banked"].items()}

@@ -453,7 +453,7 @@ bcf_status run_merge(void* ko, uint32_t* vo, const void* ki, const uint32_t* vi,
   }
   uint64_t* splits = reinterpret_cast<uint64_t*>(wsb + wl.splits);
   // Samples (the keys at array positions that are multiples of
-  // kSampleStride, in mapped order) narrow every merge-path search to a
+  // kRunSampleStride, in mapped order) narrow every merge-path search to a
   // window: pass i reads samp[i & 1], its merge kernel writes the next pass's
   // into samp[(i + 1) & 1], and pass 1's are taken from the input first.
   void* samp[2] = {wsb + wl.samples0, wsb + wl.samples1};

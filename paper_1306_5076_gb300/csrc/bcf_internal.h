@@ -44,6 +44,13 @@ struct PairList {
 // measured at 2^28 u32 keys, 64 takes the partition from 40 to 29 us per
 // pass (the sort 7.05 -> 6.90 ms) for 1.6 % more sample writes.
 constexpr uint32_t kSampleStride = 64;
+// Merges of given runs (bcf_merge_runs) sample their input with a kernel of
+// its own, reading one sector per sample: there a 256-key stride keeps that
+// read at 3 % of the data (64 keys cost 12 % and took the one-pass merge of
+// two runs from 0.21 to 0.24 ms).  The workspace's sample arrays are sized
+// for the smaller stride.
+constexpr uint32_t kRunSampleStride = 256;
+static_assert(kRunSampleStride % kSampleStride == 0, "sample arrays sized by kSampleStride");
 
 struct BlockSortArgs {
   const void* kin;
@@ -174,8 +181,9 @@ cudaError_t launch_block_sort(int key_bytes, bool pairs, int cfg, const BlockSor
                               cudaStream_t s);
 cudaError_t launch_partition(int key_bytes, int cfg, const MergeArgs& a, const PairList* pl,
                              cudaStream_t s);
-// Samples of keys [lo, hi): samples[g / kSampleStride] = (mapped) keys[g] for
-// every g in [lo, hi) that is a multiple of kSampleStride.
+// Samples of keys [lo, hi): samples[g / kRunSampleStride] = (mapped) keys[g]
+// for every g in [lo, hi) that is a multiple of kRunSampleStride (merges of
+// given runs).
 cudaError_t launch_sample_span(int key_bytes, const void* keys, void* samples, int mode,
                                uint64_t lo, uint64_t hi, cudaStream_t s);
 cudaError_t launch_merge(int key_bytes, bool pairs, int cfg, const MergeArgs& a,

@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(256) partition_kernel(const MergeArgs a, int T
       // cA + S * (A-samples taken) (checked exhaustively on small runs by the
       // host model of this search); the result is then checked against the
       // split's defining inequalities, with the full search as the fallback.
-      constexpr uint64_t S = kSampleStride;
+      constexpr uint64_t S = kRunSampleStride;
       const uint64_t offA = p.src, offB = p.src + p.na_tot;
       const uint64_t gA = (offA + S - 1) / S, gB = (offB + S - 1) / S;
       const uint64_t cA = gA * S - offA, cB = gB * S - offB;
@@ -408,9 +408,9 @@ __global__ void __launch_bounds__(NT) merge_kernel(const MergeArgs a,
     if (a.samples_out && ((p.out0 + tid * E) % kSampleStride) == 0 && tid * E < p.d1 - p.d0)
       static_cast<K*>(a.samples_out)[(p.out0 + tid * E) / kSampleStride] = f.k[0];
   } else if constexpr (SMP) {
-    if (((p.out0 + tid * E) % kSampleStride) == 0 && tid * E >= front &&
+    if (((p.out0 + tid * E) % kRunSampleStride) == 0 && tid * E >= front &&
         tid * E < front + (p.d1 - p.d0))
-      static_cast<K*>(a.samples_out)[(p.out0 + tid * E) / kSampleStride] = f.k[0];
+      static_cast<K*>(a.samples_out)[(p.out0 + tid * E) / kRunSampleStride] = f.k[0];
   }
 
   // outputs: BLK layout, thread holds tile slots tid*E .. tid*E+E-1
@@ -447,14 +447,14 @@ __global__ void __launch_bounds__(256) sample_span_kernel(const K* keys, K* samp
   const uint64_t t = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= count) return;
   const uint64_t g = g0 + t;
-  const K k = keys[g * kSampleStride];
+  const K k = keys[g * kRunSampleStride];
   samples[g] = MAP ? map_key(k, mode) : k;
 }
 
 template <typename K>
 static cudaError_t launch_ss(const void* keys, void* samples, int mode, uint64_t lo, uint64_t hi,
                              cudaStream_t s) {
-  constexpr uint64_t S = kSampleStride;
+  constexpr uint64_t S = kRunSampleStride;
   const uint64_t g0 = (lo + S - 1) / S, g1 = (hi + S - 1) / S;
   if (g1 <= g0) return cudaSuccess;
   const uint64_t count = g1 - g0;
