@@ -63,6 +63,7 @@ def source_digest(files):
 
 
 MERGE_SOURCES = ["paper_1306_5076_gb300/csrc/bcf_merge.cu",
+                 "paper_1306_5076_gb300/csrc/bcf_merge.cuh",
                  "paper_1306_5076_gb300/csrc/bcf_device.cuh",
                  "paper_1306_5076_gb300/csrc/bcf_internal.h"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "merge_kernel_u32_traffic.json.txt")
@@ -545,6 +546,48 @@ def pb_bench(torch, dev, bcf, log2n=LOG2N):
     return {"n": n, "key": "u32", "results": out}
 
 
+def check_segmented(torch, kin, kout, vout, od, chunk=1 << 27):
+    """Exact device checks of a segmented sort of u32 keys (int32 bits) whose
+    payloads, if any, are the input positions: every segment in order; with
+    payloads, each payload lies in its output's segment, its input key equals
+    the output key, and equal keys keep input order (together: the payloads
+    are a permutation of the segment's positions); keys only, each segment
+    keeps its multiset (two modular fingerprints per segment)."""
+    n = kin.numel()
+    nseg = od.numel() - 1
+    P = 1000000007
+    ends = od[1:].contiguous()
+    fp = [torch.zeros(nseg, dtype=torch.int64, device=kin.device) for _ in range(4)]
+    ok = True
+    for c0 in range(0, n, chunk):
+        c1 = min(n, c0 + chunk)
+        e1 = min(n, c1 + 1)  # one element of overlap joins the chunks
+        pos = torch.arange(c0, e1, dtype=torch.int64, device=kin.device)
+        seg = torch.searchsorted(ends, pos, right=True)
+        o = kout[c0:e1].to(torch.int64) & 0xFFFFFFFF
+        same = seg[1:] == seg[:-1]
+        ok = ok and bool((~same | (o[1:] >= o[:-1])).all().item())
+        if vout is not None:
+            v = vout[c0:e1].to(torch.int64) & 0xFFFFFFFF
+            ok = ok and bool((v < n).all().item())
+            vs = torch.searchsorted(ends, v.clamp(max=n - 1), right=True)
+            ok = ok and bool((vs == seg).all().item())
+            ok = ok and bool((kin[v.clamp(max=n - 1)] == kout[c0:e1]).all().item())
+            ties = same & (o[1:] == o[:-1])
+            ok = ok and bool((~ties | (v[1:] > v[:-1])).all().item())
+        else:
+            m = c1 - c0
+            i = kin[c0:c1].to(torch.int64) & 0xFFFFFFFF
+            for x, a, b in ((i, 0, 1), (o[:m], 2, 3)):
+                xm = x % P
+                fp[a].index_add_(0, seg[:m], xm)
+                fp[b].index_add_(0, seg[:m], xm * xm % P)
+    if vout is None:
+        ok = ok and bool((fp[0] == fp[2]).all().item()) and bool(
+            ((fp[1] % P) == (fp[3] % P)).all().item())
+    return ok
+
+
 def segmented_bench(torch, dev, bcf):
     """Row A6 on its workload: 100,000 segments of log-uniform size in [1, 2^18]
     (about 2.1e9 keys; seed 4000) and the 1 GiB variant ([1, 2^14]), uniform u32
@@ -578,13 +621,14 @@ def segmented_bench(torch, dev, bcf):
             with torch.cuda.stream(side):
                 call()
             side.synchronize()
+            exact = check_segmented(torch, kd, ko, vo, od)
             graph = torch.cuda.CUDAGraph()
             with torch.cuda.graph(graph, stream=side):
                 call()
             ms = timed_ms(torch, torch.cuda.current_stream(dev), graph.replay, warmup=2, reps=5)
             out[f"{label}{' +u32' if pairs else ''}"] = {
                 "segments": int(sizes.size), "keys": n, "ms": ms, "keys_per_s": n / (ms * 1e-3),
-                "payload": "u32" if pairs else None}
+                "payload": "u32" if pairs else None, "exact": exact}
             del vd, vo, ws, graph
             torch.cuda.empty_cache()
         del kd, ko, od

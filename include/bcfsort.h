@@ -174,9 +174,15 @@ bcf_status bcf_merge_runs(void* keys_out, uint32_t* vals_out, const void* keys_i
  * device; a decreasing offset is not detected on the host and yields an
  * unspecified (but memory-safe) result.  n_total may exceed 2^32 (and one
  * segment may be that long); nseg must be below 2^32 (BCF_EUNSUPPORTED
- * otherwise).  The call makes two launches (a plan and one persistent wave)
- * and can be captured in a CUDA graph; ws is sized by
- * bcf_workspace_bytes(BCF_OP_SEGMENTED, n_total, nseg, kt, has_vals).
+ * otherwise).  The call makes two launches: a plan and one persistent wave
+ * that sorts tiny segments and tiles and, by default, also runs the merge
+ * passes.  Where the tuning table's segmented row for the size band names a
+ * merge configuration, the wave only sorts, and the merge passes of segments
+ * of two or more tiles follow as one partition and one merge launch per
+ * possible pass count, ceil(log2((n_total - 1) / T + 2)) pairs for sort tile
+ * T; a pair with no segment that long finds no work.  The launch sequence is
+ * fixed by the arguments, so the call can be captured in a CUDA graph; ws is
+ * sized by bcf_workspace_bytes(BCF_OP_SEGMENTED, n_total, nseg, kt, has_vals).
  */
 bcf_status bcf_segmented_sort(void* keys_out, uint32_t* vals_out, const void* keys_in,
                               const uint32_t* vals_in, const uint64_t* seg_offsets_dev,
@@ -375,8 +381,11 @@ bcf_status bcf_colored_prefix_sums(uint32_t* out, const uint32_t* values, const 
  * configuration on the GPU and writes the table.  Without a call to
  * bcf_tuning_set the library reads tuning/gb300.tsv of its package (rows "op
  * key_bytes has_vals n_min n_max block_cfg merge_cfg seg_cfg"); configurations
- * are indices into the lists that bcf_tuning_config enumerates.  Results never
- * depend on the tuning.
+ * are indices into the lists that bcf_tuning_config enumerates.  In a
+ * BCF_OP_SEGMENTED row, block_cfg is unused and merge_cfg says who runs the
+ * merge passes: -1 the persistent worker, else launches of that merge
+ * configuration, whose tile must not exceed the seg_cfg tile (BCF_EINVAL
+ * otherwise).  Results never depend on the tuning.
  */
 typedef struct {
     int op;              /* BCF_OP_SORT, BCF_OP_MERGE or BCF_OP_SEGMENTED */

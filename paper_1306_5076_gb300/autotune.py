@@ -98,30 +98,49 @@ def tune_sort(torch, kb, pairs, reps, log):
     return rows
 
 
-def tune_segmented(torch, kb, pairs, reps, log, nseg=5000, hi=1 << 18):
+# (n_min, n_max, segments, largest segment) of the segmented sort's size bands:
+# small batches (as the request server coalesces them) and large ones
+SEG_BANDS = [(0, 1 << 24, 2000, 1 << 14), (1 << 24, 1 << 48, 5000, 1 << 18)]
+
+
+def tune_segmented(torch, kb, pairs, reps, log):
+    """Per size band: the worker configuration and who runs the merge passes
+    (merge_cfg -1: the worker; else launches of that merge configuration,
+    whose tile must not exceed the sort tile)."""
     import numpy as np
 
     import workloads
 
     kt = bcf.BCF_U32 if kb == 4 else bcf.BCF_U64
-    sizes = workloads.segment_sizes(nseg, hi, seed=4000)
-    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
-    n = int(offs[-1])
-    k, v = _inputs(torch, n, kb, pairs)
-    ko = torch.empty_like(k)
-    vo = torch.empty_like(v) if pairs else None
-    od = torch.from_numpy(offs).to("cuda")
-    ws = torch.empty(bcf.bcf_workspace_bytes(bcf.BCF_OP_SEGMENTED, n, nseg, kt, pairs),
-                     dtype=torch.uint8, device="cuda")
-    best = None
-    for si, (se, snt) in _configs(2, kb, pairs):
-        bcf.bcf_tuning_set([dict(op=bcf.BCF_OP_SEGMENTED, key_bytes=kb, has_vals=int(pairs),
-                                 n_min=0, n_max=1 << 48, block_cfg=0, merge_cfg=0, seg_cfg=si)])
-        ms = _time(torch, lambda: bcf.bcf_segmented_sort(ko, vo, k, v, od, kt=kt, ws=ws), reps)
-        log(f"segmented kb={kb} pairs={int(pairs)} n={n} cfg={se}x{snt}: {ms:.3f} ms")
-        if best is None or ms < best[0]:
-            best = (ms, si)
-    return [(bcf.BCF_OP_SEGMENTED, kb, int(pairs), 0, 1 << 48, 0, 0, best[1])]
+    merges = _configs(1, kb, pairs)
+    rows = []
+    for n_min, n_max, nseg, hi in SEG_BANDS:
+        sizes = workloads.segment_sizes(nseg, hi, seed=4000)
+        offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+        n = int(offs[-1])
+        k, v = _inputs(torch, n, kb, pairs)
+        ko = torch.empty_like(k)
+        vo = torch.empty_like(v) if pairs else None
+        od = torch.from_numpy(offs).to("cuda")
+        ws = torch.empty(bcf.bcf_workspace_bytes(bcf.BCF_OP_SEGMENTED, n, nseg, kt, pairs),
+                         dtype=torch.uint8, device="cuda")
+        best = None
+        for si, (se, snt) in _configs(2, kb, pairs):
+            for mi, mt in [(-1, None)] + [(mi, me * mnt) for mi, (me, mnt) in merges
+                                          if me * mnt <= se * snt]:
+                bcf.bcf_tuning_set([dict(op=bcf.BCF_OP_SEGMENTED, key_bytes=kb,
+                                         has_vals=int(pairs), n_min=0, n_max=1 << 48,
+                                         block_cfg=0, merge_cfg=mi, seg_cfg=si)])
+                ms = _time(torch, lambda: bcf.bcf_segmented_sort(ko, vo, k, v, od, kt=kt, ws=ws),
+                           reps)
+                who = "worker" if mi < 0 else f"launches, {mt}-key tiles"
+                log(f"segmented kb={kb} pairs={int(pairs)} n={n} cfg={se}x{snt} merges: {who}: "
+                    f"{ms:.3f} ms")
+                if best is None or ms < best[0]:
+                    best = (ms, si, mi)
+        rows.append((bcf.BCF_OP_SEGMENTED, kb, int(pairs), n_min, n_max, 0, best[2], best[1]))
+        del k, v, ko, vo, od, ws
+    return rows
 
 
 def main(argv=None):

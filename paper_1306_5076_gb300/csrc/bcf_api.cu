@@ -86,7 +86,15 @@ bool entry_ok(const bcf_tuning_entry& e) {
     if (!merge_cfg_supported(e.key_bytes, pairs, e.merge_cfg)) return false;
     return kMergeCfgs[e.merge_cfg].tile() <= 2 * kBlockCfgs[e.block_cfg].tile();
   }
-  if (e.op == BCF_OP_SEGMENTED) return seg_cfg_supported(e.key_bytes, pairs, e.seg_cfg);
+  if (e.op == BCF_OP_SEGMENTED) {
+    // merge_cfg -1: the worker merges; else the merge passes of multi-tile
+    // segments are launches of that merge configuration, whose tile must
+    // divide the segmented sort's tile
+    if (!seg_cfg_supported(e.key_bytes, pairs, e.seg_cfg)) return false;
+    if (e.merge_cfg == -1) return true;
+    return merge_cfg_supported(e.key_bytes, pairs, e.merge_cfg) &&
+           kMergeCfgs[e.merge_cfg].tile() <= kSegCfgs[e.seg_cfg].tile();
+  }
   return false;
 }
 
@@ -162,7 +170,8 @@ Plan make_plan(uint64_t n, int kb, bool pairs, int op = BCF_OP_SORT) {
 // sizes: a segment touches at most size/T + 2 tiles, and each of its passes
 // has one item per tile.
 struct SegLayout {
-  size_t ctl, items, tiny, tbase, splits, queue, keys, vals, total;
+  size_t ctl, items, tiny, tbase, splits, queue, order, pend, count_ge, pitems, chunks, pnext,
+      samp0, samp1, keys, vals, total;
   uint64_t capacity;
 };
 
@@ -178,15 +187,34 @@ SegLayout seg_layout(uint64_t n, uint64_t nseg, int kb, bool pairs) {
   w.tbase = align_up(w.tiny + nseg * 4, kAlign);
   w.splits = align_up(w.tbase + nseg * 8, kAlign);
   w.queue = align_up(w.splits + tiles * 8, kAlign);
-  w.keys = align_up(w.queue + w.capacity * seg_work_bytes(), kAlign);
+  // merge passes outside the worker: the segment list, and one record per
+  // merge tile (at most `tiles` of them; the splits above serve them too)
+  w.order = align_up(w.queue + w.capacity * seg_work_bytes(), kAlign);
+  w.pend = align_up(w.order + nseg * 4, kAlign);
+  w.count_ge = align_up(w.pend + nseg * 8, kAlign);
+  w.pitems = align_up(w.count_ge + (kSegMaxPasses + 2) * 4, kAlign);
+  // samples of the output and of the keys copy for the launches' partitions
+  const uint64_t nsamp = n / kRunSampleStride + 2;
+  w.chunks = align_up(w.pitems + tiles * sizeof(SegItem), kAlign);
+  w.pnext = align_up(w.chunks + (tiles / 32 + 2) * 4, kAlign);
+  w.samp0 = align_up(w.pnext + (kSegMaxPasses + 2) * 8, kAlign);
+  w.samp1 = align_up(w.samp0 + nsamp * kb, kAlign);
+  w.keys = align_up(w.samp1 + nsamp * kb, kAlign);
   w.vals = align_up(w.keys + n * kb, kAlign);
   w.total = align_up(w.vals + (pairs ? n * 4 : 0), kAlign);
   return w;
 }
 
-int seg_cfg_for(int kb, bool pairs, uint64_t n) {
-  if (const bcf_tuning_entry* e = find_entry(BCF_OP_SEGMENTED, kb, pairs, n)) return e->seg_cfg;
-  return 0;  // 16 x 256: 4096-key tiles
+// Segmented sort: the worker's configuration and who merges (merge_cfg -1:
+// the worker; else launches of that merge configuration).  Built-in default:
+// 4096-key tiles (16 x 256), merges in the worker.
+struct SegTuning {
+  int seg_cfg, merge_cfg;
+};
+SegTuning seg_tuning_for(int kb, bool pairs, uint64_t n) {
+  if (const bcf_tuning_entry* e = find_entry(BCF_OP_SEGMENTED, kb, pairs, n))
+    return {e->seg_cfg, e->merge_cfg};
+  return {0, -1};
 }
 
 // ---------------------------------------------------------------- device error word
@@ -551,12 +579,64 @@ bcf_status run_segmented(void* ko, uint32_t* vo, const void* ki, const uint32_t*
   L.piece_split = reinterpret_cast<uint64_t*>(wsb + wl.splits);
   L.ctl = wsb + wl.ctl;
   L.err = err;
+  const SegTuning tu = seg_tuning_for(kb, pairs, n);
+  const int cfg = tu.seg_cfg;
+  L.merge_cfg = tu.merge_cfg;
+  L.order = reinterpret_cast<uint32_t*>(wsb + wl.order);
+  L.piece_end = reinterpret_cast<uint64_t*>(wsb + wl.pend);
+  L.count_ge = reinterpret_cast<uint32_t*>(wsb + wl.count_ge);
+  L.samples_out = wsb + wl.samp0;
+  L.samples_buf = wsb + wl.samp1;
   // unpublished queue slots must read "not ready"
   if (cudaMemsetAsync(L.queue, 0, wl.capacity * seg_work_bytes(), s) != cudaSuccess)
     return BCF_ECUDA;
-  const int cfg = seg_cfg_for(kb, pairs, n);
-  const cudaError_t e = timed(3, s, [&] { return launch_segmented(kb, pairs, cfg, L, s); });
-  return from_cuda(e);
+  cudaError_t e = timed(3, s, [&] { return launch_segmented(kb, pairs, cfg, L, s); });
+  if (e != cudaSuccess || L.merge_cfg < 0) return from_cuda(e);
+  // Merge passes of the listed (multi-tile) segments, by passes to go q: the
+  // launch for q does the pass of every segment that has q or more left.
+  // The host does not know the longest segment, so q starts at the pass
+  // count of a segment of all n keys; launches with no segment that long
+  // find no work items and return at once.
+  const uint64_t T = static_cast<uint64_t>(kSegCfgs[cfg].tile());
+  const uint64_t max_tiles = (n - 1) / T + 2;
+  uint32_t qmax = 0;
+  while ((1ull << qmax) < max_tiles) ++qmax;
+  SegPassList pl{};
+  pl.off = off;
+  pl.order = L.order;
+  pl.piece_end = L.piece_end;
+  pl.count_ge = L.count_ge;
+  pl.items = reinterpret_cast<SegItem*>(wsb + wl.pitems);
+  pl.chunk_seg = reinterpret_cast<uint32_t*>(wsb + wl.chunks);
+  pl.next = reinterpret_cast<unsigned long long*>(wsb + wl.pnext);
+  pl.n = n;
+  pl.T = static_cast<uint32_t>(T);
+  e = timed(1, s, [&] { return launch_seg_chunks(pl, s); });
+  if (e != cudaSuccess) return BCF_ECUDA;
+  for (uint32_t q = qmax; q >= 1; --q) {
+    // the last pass (q = 1) writes the output: pass q writes it when q is odd
+    const bool to_out = (q & 1u) != 0;
+    MergeArgs ma{};
+    ma.kin = to_out ? L.kbuf : ko;
+    ma.vin = pairs ? (to_out ? L.vbuf : vo) : nullptr;
+    ma.kout = to_out ? ko : L.kbuf;
+    ma.vout = pairs ? (to_out ? vo : L.vbuf) : nullptr;
+    ma.n = n;
+    ma.splits = L.piece_split;
+    ma.mode_in = 0;  // the block sort left the listed segments' keys mapped
+    ma.mode_out = q == 1 ? L.mode : 0;
+    // samples of the buffer read (written by the tile sorts or the pass
+    // before) and, for a pass with a successor, of the buffer written
+    ma.samples_in = to_out ? L.samples_buf : L.samples_out;
+    ma.samples_out = q > 1 ? (to_out ? L.samples_out : L.samples_buf) : nullptr;
+    ma.err = err;
+    pl.q = q;
+    e = timed(1, s, [&] { return launch_seg_partition(kb, L.merge_cfg, ma, pl, s); });
+    if (e != cudaSuccess) return BCF_ECUDA;
+    e = timed(2, s, [&] { return launch_seg_merge(kb, pairs, L.merge_cfg, ma, pl, s); });
+    if (e != cudaSuccess) return BCF_ECUDA;
+  }
+  return BCF_OK;
 }
 
 // ---------------------------------------------------------------- pivot buckets

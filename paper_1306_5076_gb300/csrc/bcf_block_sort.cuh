@@ -33,13 +33,6 @@
 
 namespace bcf {
 
-template <typename K, int V> struct VecOf;
-template <> struct VecOf<uint32_t, 4> { using T = uint4; };
-template <> struct VecOf<uint64_t, 2> { using T = ulonglong2; };
-template <int V> struct ValVec;
-template <> struct ValVec<4> { using T = uint4; };
-template <> struct ValVec<2> { using T = uint2; };
-
 // MAP: the key map is applied on load / undone on store (runtime mode); when
 // false the kernel carries no map code at all (intermediate passes).
 template <typename K, bool PAIRS, int E, int NT, bool MAP>

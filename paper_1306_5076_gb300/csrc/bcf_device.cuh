@@ -184,6 +184,14 @@ __device__ __forceinline__ void st_global_32B(uint64_t* p, const uint64_t* x) {
                : "memory");
 }
 
+// 16-byte vectors of V keys, and of the V payloads that go with them.
+template <typename K, int V> struct VecOf;
+template <> struct VecOf<uint32_t, 4> { using T = uint4; };
+template <> struct VecOf<uint64_t, 2> { using T = ulonglong2; };
+template <int V> struct ValVec;
+template <> struct ValVec<4> { using T = uint4; };
+template <> struct ValVec<2> { using T = uint2; };
+
 // Stores E consecutive elements x[0..E) of one thread at p (E * sizeof(K) a
 // multiple of 32): 32-byte stores when p is 32-byte aligned, else 16-byte.
 template <int E, typename K>

@@ -164,6 +164,15 @@ struct SegLaunch {
   uint64_t* piece_split; // one per tile of all segments: merge-path split of its next piece
   void* ctl;             // queue counters
   uint32_t* err;
+  // Merge passes outside the worker (merge_cfg >= 0): segments of two or more
+  // tiles are only block-sorted by the worker; their merge passes run as
+  // launches of the merge kernel over a device list (SegPassList).
+  int merge_cfg;           // -1: the worker merges; else the merge kernel configuration
+  uint32_t* order;         // nseg: multi-tile segments, most passes first
+  uint64_t* piece_end;     // nseg: inclusive prefix sums of their merge tiles in that order
+  uint32_t* count_ge;      // kSegMaxPasses + 2: count_ge[q] = listed segments with >= q passes
+  void* samples_out;       // keys at positions that are multiples of kRunSampleStride in
+  void* samples_buf;       // the output / in the workspace copy (listed segments)
 };
 bool seg_cfg_supported(int key_bytes, bool pairs, int cfg);
 cudaError_t launch_segmented(int key_bytes, bool pairs, int cfg, const SegLaunch& L,
@@ -188,6 +197,41 @@ cudaError_t launch_sample_span(int key_bytes, const void* keys, void* samples, i
                                uint64_t lo, uint64_t hi, cudaStream_t s);
 cudaError_t launch_merge(int key_bytes, bool pairs, int cfg, const MergeArgs& a,
                          const PairList* pl, cudaStream_t s);
+
+// Merge passes of a segmented sort's multi-tile segments, outside the worker.
+// Segment s, block-sorted in tiles of T keys (T-aligned, clipped to the
+// segment), needs P_s = ceil(log2 tiles) pairwise passes; its pass j merges
+// runs of 2^(j-1) tiles.  The list holds the segments with P_s >= 1, most
+// passes first, so the segments that still have q or more passes to go are
+// a prefix of it; one launch does, for every one of those, the pass that
+// leaves q - 1 to go (its pass P_s - q + 1).  All of them read the same
+// buffer and write the same one in that launch.  Work items are the
+// Tm-aligned output tiles of the listed segments (Tm divides T, so an item
+// lies in one pair); the partition writes each item's pair and split, the
+// merge kernel reads them.
+constexpr uint32_t kSegMaxPasses = 40;
+struct SegItem {
+  uint64_t src, na, nb, out0;  // pair A = [src, src + na), B = next nb; tile start
+};
+struct SegPassList {
+  const uint64_t* off;
+  const uint32_t* order;
+  const uint64_t* piece_end;
+  const uint32_t* count_ge;
+  SegItem* items;
+  uint32_t* chunk_seg;         // list position of work item 32 c (launch_seg_chunks)
+  unsigned long long* next;    // per q: work items taken by the merge launch's CTAs
+  uint64_t n;
+  uint32_t T;   // block-sort tile of the segmented sort
+  uint32_t q;   // passes to go, this one included
+};
+// Once per sort, before its merge launches: the chunk table of the list (the
+// list position of every 32nd work item) and the merge launches' counters.
+cudaError_t launch_seg_chunks(const SegPassList& L, cudaStream_t s);
+cudaError_t launch_seg_partition(int key_bytes, int cfg, const MergeArgs& a,
+                                 const SegPassList& L, cudaStream_t s);
+cudaError_t launch_seg_merge(int key_bytes, bool pairs, int cfg, const MergeArgs& a,
+                             const SegPassList& L, cudaStream_t s);
 
 // Colored prefix sums (Appendix A).  One tile of kCpsTile elements per CTA,
 // tiles taken in order from `counter`; `status` holds one word per (tile,

@@ -63,9 +63,52 @@ __device__ __forceinline__ T block_scan_incl(T v, T* warp_sums, T& total) {
   return v;
 }
 
+// The list of segments whose merge passes run outside the worker: a counting
+// sort by pass count (most passes first; within a count, in no particular
+// order), then the inclusive prefix sums of their Tm-tiles in list order.
+// hist[P] holds the number of listed segments with P passes.
+__device__ __forceinline__ void plan_list(const SegArgs& a, uint32_t T, uint32_t* hist) {
+  __shared__ unsigned long long ws[32];
+  __shared__ uint32_t cursor[kSegMaxPasses + 2];
+  __syncthreads();  // every count is in hist
+  if (threadIdx.x == 0) {
+    uint32_t ge = 0;
+    a.count_ge[kSegMaxPasses + 1] = 0;
+    for (int q = kSegMaxPasses; q >= 0; --q) {
+      cursor[q] = ge;  // the segments with more passes come first
+      ge += q > 0 ? hist[q] : 0u;
+      a.count_ge[q] = ge;
+    }
+  }
+  __syncthreads();
+  for (uint64_t s = threadIdx.x; s < a.nseg; s += blockDim.x) {
+    const SegGeo g = seg_geo(a.off, s, a.n, T, a.skip_odd != 0);
+    if (g.passes == 0) continue;
+    const uint32_t pos =
+        atomicAdd(&cursor[g.passes < kSegMaxPasses ? g.passes : kSegMaxPasses], 1u);
+    a.order[pos] = static_cast<uint32_t>(s);
+    a.piece_end[pos] = (g.hi - 1) / a.Tm - g.lo / a.Tm + 1;
+  }
+  __syncthreads();
+  const uint32_t listed = a.count_ge[1];
+  unsigned long long carry = 0;
+  for (uint32_t c = 0; c < listed; c += blockDim.x) {
+    const uint32_t i = c + threadIdx.x;
+    const unsigned long long v = i < listed ? a.piece_end[i] : 0ull;
+    unsigned long long sum;
+    const unsigned long long incl = block_scan_incl(v, ws, sum);
+    if (i < listed) a.piece_end[i] = carry + incl;
+    carry += sum;
+  }
+}
+
 __global__ void __launch_bounds__(1024) plan_kernel(const SegArgs a, uint32_t T,
                                                     uint32_t per_group) {
   __shared__ unsigned long long ws[32];
+  __shared__ uint32_t s_hist[kSegMaxPasses + 2];
+  for (uint32_t q = threadIdx.x; q < kSegMaxPasses + 2; q += blockDim.x) s_hist[q] = 0;
+  __syncthreads();
+  const bool defer = a.Tm != 0;
   unsigned long long carry_tiles = 0, carry_tiny = 0, carry_total = 0;
   for (uint64_t c = 0; c < a.nseg; c += 1024) {
     const uint64_t s = c + threadIdx.x;
@@ -73,7 +116,11 @@ __global__ void __launch_bounds__(1024) plan_kernel(const SegArgs a, uint32_t T,
     if (s < a.nseg) g = seg_geo(a.off, s, a.n, T, a.skip_odd != 0);
     const unsigned long long tiles = g.tiles;
     const unsigned long long tiny = g.tiny ? 1 : 0;
-    const unsigned long long tot = tiles + static_cast<unsigned long long>(g.passes) * g.pieces;
+    // a listed segment's merge passes are not queue items
+    const bool listed = defer && g.passes > 0;
+    const unsigned long long tot =
+        tiles + (listed ? 0ull : static_cast<unsigned long long>(g.passes) * g.pieces);
+    if (listed) atomicAdd(&s_hist[g.passes < kSegMaxPasses ? g.passes : kSegMaxPasses], 1u);
     unsigned long long sum;
     const unsigned long long t_incl = block_scan_incl(tiles, ws, sum);
     const unsigned long long t_excl = t_incl - tiles;
@@ -87,16 +134,6 @@ __global__ void __launch_bounds__(1024) plan_kernel(const SegArgs a, uint32_t T,
       a.items_left[s] = g.tiles;
       a.tile_base[s] = carry_tiles + t_excl;
       if (g.tiny) a.tiny_list[carry_tiny + y_incl - 1] = static_cast<uint32_t>(s);
-      const unsigned long long base = carry_tiles + t_excl;
-      for (uint32_t q = 0; q < g.tiles; ++q) {
-        if (base + q < a.capacity) {
-          SegWork w;
-          w.meta = kReady | kWTile;
-          w.seg = static_cast<uint32_t>(s);
-          w.arg = q;
-          a.queue[base + q] = w;
-        }
-      }
     }
     carry_tiles += sum_tiles;
     carry_tiny += sum_tiny;
@@ -112,18 +149,49 @@ __global__ void __launch_bounds__(1024) plan_kernel(const SegArgs a, uint32_t T,
       a.queue[carry_tiles + q] = w;
     }
   }
+  if (defer) plan_list(a, T, s_hist);
   if (threadIdx.x == 0) {
     const unsigned long long total = carry_total + groups;
     a.ctl->head = 0;
     a.ctl->reserve = carry_tiles + groups;
     a.ctl->total = total <= a.capacity ? total : 0;  // overflow: nothing runs
     a.ctl->n_tiny = carry_tiny;
+    a.ctl->tiles = total <= a.capacity ? carry_tiles : 0;
     if (total > a.capacity) atomicOr(a.err, kErrQueueOverflow);
+  }
+}
+
+// The tile-sort slots [0, tiles) of the queue, in parallel: slot idx belongs
+// to the last segment whose first tile index (tile_base, non-decreasing) is
+// at most idx.  (A single thread per segment would write a segment of 2^31
+// keys' 2^19 slots alone.)
+__global__ void __launch_bounds__(256) fill_tiles_kernel(const SegArgs a) {
+  const uint64_t tiles = __ldcg(&a.ctl->tiles);
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  for (uint64_t idx = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+       idx < tiles; idx += stride) {
+    uint64_t lo = 0, hi = a.nseg;  // first segment whose tile_base exceeds idx
+    while (lo < hi) {
+      const uint64_t mid = (lo + hi) >> 1;
+      if (__ldcg(a.tile_base + mid) > idx) hi = mid; else lo = mid + 1;
+    }
+    const uint64_t s = lo - 1;
+    SegWork w;
+    w.meta = kReady | kWTile;
+    w.seg = static_cast<uint32_t>(s);
+    w.arg = idx - __ldcg(a.tile_base + s);
+    a.queue[idx] = w;
   }
 }
 
 cudaError_t launch_plan(const SegArgs& a, uint32_t T, uint32_t tiny_per_group, cudaStream_t s) {
   plan_kernel<<<1, 1024, 0, s>>>(a, T, tiny_per_group);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // a segment touches at most size / T + 2 tiles
+  const uint64_t bound = a.n / T + 2 * a.nseg + 2;
+  const uint64_t blocks = (bound + 255) / 256;
+  fill_tiles_kernel<<<static_cast<unsigned>(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -159,8 +227,17 @@ cudaError_t launch_segmented(int key_bytes, bool pairs, int cfg, const SegLaunch
   a.ctl = static_cast<SegCtl*>(L.ctl);
   a.err = L.err;
   a.wait_ns = wait_limit_ns();
-  return key_bytes == 4 ? launch_segmented_typed<uint32_t>(pairs, cfg, a, s)
-                         : launch_segmented_typed<uint64_t>(pairs, cfg, a, s);
+  a.Tm = L.merge_cfg >= 0 ? static_cast<uint32_t>(kMergeCfgs[L.merge_cfg].tile()) : 0u;
+  a.order = L.order;
+  a.piece_end = L.piece_end;
+  a.count_ge = L.count_ge;
+  a.samples_out = a.Tm ? L.samples_out : nullptr;
+  a.samples_buf = a.Tm ? L.samples_buf : nullptr;
+  if (key_bytes == 4)
+    return pairs ? launch_segmented_kp<uint32_t, true>(cfg, a, s)
+                 : launch_segmented_kp<uint32_t, false>(cfg, a, s);
+  return pairs ? launch_segmented_kp<uint64_t, true>(cfg, a, s)
+               : launch_segmented_kp<uint64_t, false>(cfg, a, s);
 }
 
 size_t seg_work_bytes() { return sizeof(SegWork); }

@@ -27,6 +27,7 @@ struct SegCtl {
   unsigned long long reserve;  // slots published or being published
   unsigned long long total;    // work items that will ever exist
   unsigned long long n_tiny;
+  unsigned long long tiles;    // tile sorts: queue slots [0, tiles)
 };
 
 __host__ __device__ constexpr uint32_t ceil_log2(uint64_t x) {
@@ -83,6 +84,14 @@ struct SegArgs {
   SegCtl* ctl;
   uint32_t* err;
   uint64_t wait_ns;       // limit of every wait for a queue slot
+  // Merge passes outside the worker (Tm != 0): segments of two or more tiles
+  // are block-sorted here and listed for launches of the merge kernel.
+  uint32_t Tm;            // their merge tile, or 0: the worker merges
+  uint32_t* order;        // listed segments, most passes first
+  uint64_t* piece_end;    // inclusive prefix sums of their Tm-tiles in list order
+  uint32_t* count_ge;     // [q]: listed segments with q or more passes
+  void* samples_out;      // listed segments: tile samples of the output buffer ...
+  void* samples_buf;      // ... and of the workspace copy (or nullptr: none)
 };
 
 // The plan kernel lives in bcf_segmented.cu.
@@ -215,40 +224,76 @@ template <typename K, bool PAIRS, int E, int NT, bool MAP>
 __device__ __forceinline__ void sort_tile_item(const SegArgs& a, const SegGeo& g, uint64_t q,
                                                uint32_t* sm) {
   constexpr uint32_t T = E * NT;
+  constexpr int V = 16 / sizeof(K);  // keys per 16-byte vector
+  using KV = typename VecOf<K, V>::T;
+  using VV = typename ValVec<V>::T;
+  Frag<K, PAIRS, E> f;
+  f.one = g_unit_multiplier;
   const uint32_t tid = threadIdx.x;
   const uint64_t base = (g.lo / T + q) * T;
   const uint64_t s0 = g.lo > base ? g.lo : base;
   const uint64_t s1 = g.hi < base + T ? g.hi : base + T;
   const uint32_t front = static_cast<uint32_t>(s0 - base), cnt = static_cast<uint32_t>(s1 - s0);
   const K* kin = static_cast<const K*>(a.kin) + base;
-  Frag<K, PAIRS, E> f;
-  // striped loads (coalesced); slot k is the element's tile position, which is
-  // also its rank in the stable input order; -inf pads before, +inf after
+  const uint32_t* vin = PAIRS ? a.vin + base : nullptr;
+  // Thread tid loads the V-element vectors at tile positions
+  // pos = q * V * NT + V * tid (coalesced 16-byte loads, as the block sort
+  // kernel reads); the position is also the element's rank in the stable
+  // input order.  A tile clipped by the segment reads element by element:
+  // -inf pads before the segment, +inf pads after it.
+  if (front == 0 && cnt == T) {  // kin and vin are 16-byte aligned, base a multiple of T
 #pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const uint32_t k = e * NT + tid;
-    const bool real = k >= front && k < front + cnt;
-    K x = k < front ? KeyLimits<K>::kMin : KeyLimits<K>::kMax;
-    if (real) x = MAP ? map_key(__ldcg(kin + k), a.mode) : __ldcg(kin + k);
-    f.k[e] = x;
-    if constexpr (PAIRS) {
-      f.v[e] = real ? __ldcg(a.vin + base + k) : 0u;
-      f.ix[e] = k;
+    for (int r = 0; r < E / V; ++r) {
+      const uint32_t pos = r * V * NT + V * tid;
+      const KV kv = __ldcg(reinterpret_cast<const KV*>(kin + pos));
+      const K* kp = reinterpret_cast<const K*>(&kv);
+#pragma unroll
+      for (int c = 0; c < V; ++c) f.k[r * V + c] = MAP ? map_key(kp[c], a.mode) : kp[c];
+      if constexpr (PAIRS) {
+        const VV vv = __ldcg(reinterpret_cast<const VV*>(vin + pos));
+        const uint32_t* vp = reinterpret_cast<const uint32_t*>(&vv);
+#pragma unroll
+        for (int c = 0; c < V; ++c) {
+          f.v[r * V + c] = vp[c];
+          f.ix[r * V + c] = pos + c;
+        }
+      }
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const uint32_t pos = (e / V) * V * NT + V * tid + (e % V);
+      const bool real = pos >= front && pos < front + cnt;
+      K x = pos < front ? KeyLimits<K>::kMin : KeyLimits<K>::kMax;
+      if (real) x = MAP ? map_key(__ldcg(kin + pos), a.mode) : __ldcg(kin + pos);
+      f.k[e] = x;
+      if constexpr (PAIRS) {
+        f.v[e] = real ? __ldcg(vin + pos) : 0u;
+        f.ix[e] = pos;
+      }
     }
   }
-  block_sort_tile<NT>(f, sm);
+  block_sort_tile<NT, CeForms<K, PAIRS>::kBlockBlk, CeForms<K, PAIRS>::kBlockOth>(f, sm);
   // the segment's passes alternate buffers so that its last one writes the output
   const bool to_out = (g.passes % 2) == 0;
   K* kout = static_cast<K*>(to_out ? a.kout : a.kbuf) + base;
   uint32_t* vout = PAIRS ? (to_out ? a.vout : a.vbuf) + base : nullptr;
   const bool last = g.passes == 0;
+  // samples for the first merge pass's partition when the passes run as
+  // launches: the key at every array position that is a multiple of
+  // kRunSampleStride, in the buffer this tile is written to (mapped keys)
+  void* samples = to_out ? a.samples_out : a.samples_buf;
+  const uint32_t p0 = tid * E;
+  if (samples && !last && ((base + p0) % kRunSampleStride) == 0 && p0 >= front &&
+      p0 < front + cnt)
+    static_cast<K*>(samples)[(base + p0) / kRunSampleStride] = f.k[0];
   if constexpr (MAP) {
     if (last) {
 #pragma unroll
       for (int e = 0; e < E; ++e) f.k[e] = unmap_key(f.k[e], a.mode);  // last use of f.k
     }
   }
-  store_slots<E>(kout, vout, f, tid * E, front, cnt, to_out ? a.kout : a.kbuf,
+  store_slots<E>(kout, vout, f, p0, front, cnt, to_out ? a.kout : a.kbuf,
                  PAIRS ? (to_out ? a.vout : a.vbuf) : nullptr);
 }
 
@@ -420,7 +465,8 @@ __device__ __forceinline__ void merge_piece_item(const SegArgs& a, const SegGeo&
       f.ix[e] = isB ? endA + (static_cast<uint32_t>(T) - 1 - k) : (k < endA ? k : T + k);
     }
   }
-  bitonic_merge_str<NT>(f, sm);
+  f.one = g_unit_multiplier;
+  bitonic_merge_str<NT, CeForms<K, PAIRS>::kMergeBlk, CeForms<K, PAIRS>::kMergeOth>(f, sm);
   K* dst = static_cast<K*>(dst_out ? a.kout : a.kbuf) + gt * T;
   uint32_t* vdst = PAIRS ? (dst_out ? a.vout : a.vbuf) + gt * T : nullptr;
   const bool last = pass == g.passes;
@@ -502,7 +548,7 @@ __device__ __forceinline__ void seg_worker_body(const SegArgs& a) {
     if (tid == 0) {
       __threadfence();  // ... and visible before the completion is counted
       const uint32_t left = atomicSub(a.items_left + w.seg, 1u);
-      s_publish = left == 1 && pass < g.passes;
+      s_publish = left == 1 && pass < g.passes && a.Tm == 0;
     }
     __syncthreads();
     if (s_publish) {
@@ -563,17 +609,63 @@ constexpr auto seg_kernel() {
     return &seg_worker<K, PAIRS, E, NT, MAP>;
 }
 
+// Listed segments (merge passes outside the worker): nothing is published
+// during the sort, every tile sort and tiny segment is known from the plan,
+// so they run as two plain launches instead of the persistent worker.
+// Tile sorts: one CTA per queue slot [0, tiles) -- the block sort kernel's
+// shape and register budget (the worker's budget also covers its merge
+// pieces and the warp sorts, which halved the CTAs per SM).
+template <typename K, bool PAIRS, int E, int NT, bool MAP>
+__global__ void __launch_bounds__(NT) seg_tile_kernel(const SegArgs a) {
+  extern __shared__ __align__(16) uint32_t sm[];
+  const uint64_t idx = blockIdx.x;
+  if (idx >= __ldcg(&a.ctl->tiles)) return;
+  const uint32_t seg = __ldcg(&a.queue[idx].seg);
+  const uint64_t q = __ldcg(&a.queue[idx].arg);
+  const SegGeo g = seg_geo(a.off, seg, a.n, E * NT, a.skip_odd != 0);
+  sort_tile_item<K, PAIRS, E, NT, MAP>(a, g, q, sm);
+}
+// Tiny segments: one warp each, over the plan's list of them.
+template <typename K, bool PAIRS, bool MAP>
+__global__ void __launch_bounds__(256) seg_tiny_kernel(const SegArgs a, uint32_t T) {
+  const uint64_t ntiny = __ldcg(&a.ctl->n_tiny);
+  const uint64_t warps = static_cast<uint64_t>(gridDim.x) * (blockDim.x / 32);
+  for (uint64_t t = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) / 32;
+       t < ntiny; t += warps) {
+    const SegGeo g = seg_geo(a.off, __ldcg(a.tiny_list + t), a.n, T, a.skip_odd != 0);
+    warp_sort_segment<K, PAIRS, MAP>(a, g.lo, g.hi);
+  }
+}
+
 template <typename K, bool PAIRS, int E, int NT, bool MAP>
 cudaError_t launch_seg(const SegArgs& a, cudaStream_t s) {
   constexpr int W = Frag<K, PAIRS, E>::W;
   const size_t smem = static_cast<size_t>(W) * Geo<E, NT>::kPlane * sizeof(uint32_t);
-  auto kern = seg_kernel<K, PAIRS, E, NT, MAP>();
-  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
-  if (err != cudaSuccess) return err;
   int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t err;
   if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
   if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    return err;
+  if (a.Tm) {
+    // listed segments: plan, tile sorts, tiny segments
+    auto tk = seg_tile_kernel<K, PAIRS, E, NT, MAP>;
+    if ((err = cudaFuncSetAttribute(tk, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    static_cast<int>(smem))) != cudaSuccess)
+      return err;
+    if ((err = launch_plan(a, E * NT, NT / 32, s)) != cudaSuccess) return err;
+    // a segment touches at most size / T + 2 tiles
+    const uint64_t tiles_bound = a.n / (E * NT) + 2 * a.nseg + 2;
+    tk<<<static_cast<unsigned>(tiles_bound), NT, smem, s>>>(a);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    auto yk = seg_tiny_kernel<K, PAIRS, MAP>;
+    if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, yk, 256, 0)) != cudaSuccess)
+      return err;
+    yk<<<sms * (per_sm > 0 ? per_sm : 1), 256, 0, s>>>(a, E * NT);
+    return cudaGetLastError();
+  }
+  auto kern = seg_kernel<K, PAIRS, E, NT, MAP>();
+  if ((err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(smem))) != cudaSuccess)
     return err;
   if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem)) !=
       cudaSuccess)
@@ -603,16 +695,22 @@ cudaError_t dispatch_seg(int cfg, const SegArgs& a, cudaStream_t s) {
   return cudaErrorInvalidValue;
 }
 
-// Launch of the persistent sort for key type K (instantiated per key type in
-// bcf_segmented_u32.cu / bcf_segmented_u64.cu so the two compile in parallel).
-template <typename K>
-cudaError_t launch_segmented_typed(bool pairs, int cfg, const SegArgs& a, cudaStream_t s) {
-  const bool map = a.mode != 0;
-  if (pairs) return map ? dispatch_seg<K, true, true>(cfg, a, s) : dispatch_seg<K, true, false>(cfg, a, s);
-  return map ? dispatch_seg<K, false, true>(cfg, a, s) : dispatch_seg<K, false, false>(cfg, a, s);
+// 32-bit keys without payloads in mapped order (f32, i32, descending) are
+// instantiated in bcf_segmented_u32m.cu, in parallel with the rest.
+extern template cudaError_t dispatch_seg<uint32_t, false, true>(int, const SegArgs&, cudaStream_t);
+
+// Launch of the persistent sort for key type K and payload flag PAIRS
+// (instantiated in bcf_segmented_u32.cu, _u32p.cu, _u64.cu and _u64p.cu so
+// that the four compile in parallel).
+template <typename K, bool PAIRS>
+cudaError_t launch_segmented_kp(int cfg, const SegArgs& a, cudaStream_t s) {
+  return a.mode != 0 ? dispatch_seg<K, PAIRS, true>(cfg, a, s)
+                     : dispatch_seg<K, PAIRS, false>(cfg, a, s);
 }
 
-extern template cudaError_t launch_segmented_typed<uint32_t>(bool, int, const SegArgs&, cudaStream_t);
-extern template cudaError_t launch_segmented_typed<uint64_t>(bool, int, const SegArgs&, cudaStream_t);
+extern template cudaError_t launch_segmented_kp<uint32_t, false>(int, const SegArgs&, cudaStream_t);
+extern template cudaError_t launch_segmented_kp<uint32_t, true>(int, const SegArgs&, cudaStream_t);
+extern template cudaError_t launch_segmented_kp<uint64_t, false>(int, const SegArgs&, cudaStream_t);
+extern template cudaError_t launch_segmented_kp<uint64_t, true>(int, const SegArgs&, cudaStream_t);
 
 }  // namespace bcf

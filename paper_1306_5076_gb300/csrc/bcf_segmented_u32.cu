@@ -1,9 +1,10 @@
-// bcf_segmented_u32.cu -- the persistent segmented sort instantiated for uint32_t keys.
+// bcf_segmented_u32.cu -- the persistent segmented sort instantiated for uint32_t keys
+// without payloads, and the worker's wait self-test.
 #include "bcf_segmented.cuh"
 
 namespace bcf {
 
-template cudaError_t launch_segmented_typed<uint32_t>(bool, int, const SegArgs&, cudaStream_t);
+template cudaError_t launch_segmented_kp<uint32_t, false>(int, const SegArgs&, cudaStream_t);
 
 // Failure-path self-test of the worker's wait for a queue slot: the queue
 // announces one work item (total = 1) whose slot is never published (its

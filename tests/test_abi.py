@@ -195,6 +195,32 @@ def test_committed_tuning_table_rows_are_valid(lib):
                                  merge_cfg=0, seg_cfg=0)])  # no E = 32 for 64-bit pairs
 
 
+def test_segmented_tuning_rows_name_who_merges(lib):
+    """Segmented rows: merge_cfg -1 (the worker merges) or a built merge
+    configuration whose tile is at most the sort tile (it must divide it)."""
+    import paper_1306_5076_gb300 as bcf
+
+    def row(merge_cfg, seg_cfg, kb=4, hv=0):
+        return dict(op=2, key_bytes=kb, has_vals=hv, n_min=0, n_max=1 << 40, block_cfg=0,
+                    merge_cfg=merge_cfg, seg_cfg=seg_cfg)
+
+    tile = lambda kind, i: bcf.bcf_tuning_config(kind, i)[0] * bcf.bcf_tuning_config(kind, i)[1]
+    for si in range(5):
+        bcf.bcf_tuning_set([row(-1, si)])
+        for mi in range(4):
+            if tile(1, mi) <= tile(2, si):
+                bcf.bcf_tuning_set([row(mi, si)])
+            else:
+                with pytest.raises(bcf.BcfError):
+                    bcf.bcf_tuning_set([row(mi, si)])
+    for bad in (-2, 4):
+        with pytest.raises(bcf.BcfError):
+            bcf.bcf_tuning_set([row(bad, 0)])
+    with pytest.raises(bcf.BcfError):
+        bcf.bcf_tuning_set([row(1, 0, kb=8)])  # no E = 32 merge for 64-bit keys
+    bcf.bcf_tuning_set(None)
+
+
 def test_profile_collect_launches_without_records(lib):
     """Host-side only: nothing recorded gives zero launches; missing output
     pointers are BCF_EINVAL."""

@@ -88,3 +88,55 @@ def test_check_accepts_a_stable_sort_and_rejects_planted_mistakes(key):
     kc[0] = kc[1]
     if not torch.equal(kc, ko1):
         assert not bench.check_sorted_pairs(torch, k, kc, None, key)
+
+
+def segmented_reference(k, offs, pairs):
+    """Stable per-segment sort by unsigned key order (test reference only)."""
+    o = (k.to(torch.int64) & 0xFFFFFFFF).numpy()
+    perm = np.concatenate([a + np.argsort(o[a:b], kind="stable")
+                           for a, b in zip(offs[:-1], offs[1:])]).astype(np.int64)
+    ko = k[torch.from_numpy(perm)]
+    return ko, (torch.from_numpy(perm.astype(np.int32)) if pairs else None)
+
+
+def test_segmented_check_accepts_a_stable_segmented_sort_and_rejects_mistakes():
+    r = np.random.default_rng(3)
+    sizes = np.array([0, 1, 5, 0, 300, 1000, 2, 4000, 17, 0])
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    n = int(offs[-1])
+    k = torch.from_numpy(r.integers(-2**31, 2**31, size=n).astype(np.int32))
+    k[100:400] = 7  # ties inside one segment
+    od = torch.from_numpy(offs)
+    ko, vo = segmented_reference(k, offs, True)
+    ko1, _ = segmented_reference(k, offs, False)
+    assert bench.check_segmented(torch, k, ko, vo, od, chunk=1000)
+    assert bench.check_segmented(torch, k, ko1, None, od, chunk=1000)
+    # one sort of everything: order across segment borders is not required,
+    # but keys must stay in their segments
+    glob = k[torch.from_numpy(np.argsort((k.to(torch.int64) & 0xFFFFFFFF).numpy(),
+                                         kind="stable"))]
+    assert not bench.check_segmented(torch, k, glob, None, od, chunk=1000)
+    # an unstable tie
+    o = ko.to(torch.int64) & 0xFFFFFFFF
+    i = int(torch.nonzero(o[1:] == o[:-1])[0])
+    bad = vo.clone()
+    bad[i], bad[i + 1] = vo[i + 1], vo[i]
+    assert not bench.check_segmented(torch, k, ko, bad, od, chunk=1000)
+    # two keys of one segment out of order (payloads move with them)
+    j = int(torch.nonzero((o[1:] != o[:-1]))[5])
+    kb, vb = ko.clone(), vo.clone()
+    kb[j], kb[j + 1] = ko[j + 1], ko[j]
+    vb[j], vb[j + 1] = vo[j + 1], vo[j]
+    assert not bench.check_segmented(torch, k, kb, vb, od, chunk=1000)
+    assert not bench.check_segmented(torch, k, kb, None, od, chunk=1000)
+    # a key that moved to the neighbouring segment (each segment stays sorted)
+    s = 5  # [306, 1306)
+    a, b = int(offs[s]), int(offs[s + 1])
+    kc = ko1.clone()
+    kc[a] = ko1[a - 1]
+    kc[a:b] = torch.from_numpy(np.sort(kc[a:b].numpy().view(np.uint32)).view(np.int32))
+    assert not bench.check_segmented(torch, k, kc, None, od, chunk=1000)
+    # a payload that points into another segment, with its key
+    vc, kd2 = vo.clone(), ko.clone()
+    vc[a], kd2[a] = vo[a - 1], ko[a - 1]
+    assert not bench.check_segmented(torch, k, kd2, vc, od, chunk=1000)

@@ -5,6 +5,12 @@ Segment sizes cover every class of the plan: empty, 1, tiny (<= 512 keys, one
 warp), one tile, a few tiles (one or two merge passes) and many tiles (several
 passes), at arbitrary (unaligned) offsets; keys and stable pairs, every key
 type, both directions, in place, repeated, and replayed from a CUDA graph.
+
+Every test runs with each of the two ways the merge passes can run (chosen by
+the tuning table's merge_cfg for the segmented sort): in the persistent worker
+("worker"), and as launches of the merge kernel over the list of multi-tile
+segments with 2048-key merge tiles in 4096-key sort tiles ("passes") or with
+merge tiles as large as the sort tiles ("passes_eq").
 """
 from __future__ import annotations
 
@@ -20,8 +26,14 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-@pytest.fixture(scope="module")
-def bcf():
+# (seg_cfg, merge_cfg) of the segmented rows: 16 x 256 sort tiles (4096 keys);
+# merge_cfg -1: the worker merges; 3: 16 x 128 merge tiles (2048 keys); 0:
+# 16 x 256 (4096 keys)
+MODES = {"worker": (0, -1), "passes": (0, 3), "passes_eq": (0, 0)}
+
+
+@pytest.fixture(scope="module", params=list(MODES))
+def bcf(request):
     import paper_1306_5076_gb300 as m
     from paper_1306_5076_gb300 import build
 
@@ -29,7 +41,12 @@ def bcf():
         pytest.skip("no CUDA device")
     build.build()
     m._native.load()
-    return m
+    seg_cfg, merge_cfg = MODES[request.param]
+    m.bcf_tuning_set([dict(op=m.BCF_OP_SEGMENTED, key_bytes=kb, has_vals=hv, n_min=0,
+                           n_max=1 << 48, block_cfg=0, merge_cfg=merge_cfg, seg_cfg=seg_cfg)
+                      for kb in (4, 8) for hv in (0, 1)])
+    yield m
+    m.bcf_tuning_set(None)
 
 
 def mixed_sizes(r, count):

@@ -75,16 +75,22 @@ def test_segmented_invariant_to_tuning(bcf, pairs):
     vals = workloads.row_index(keys.size) if pairs else None
     ek, ev = oracle.segmented_sort(keys, vals, offs)
     od = torch.from_numpy(offs.astype(np.int64)).to("cuda")
+    choices = []
     for si in configs(bcf, 2, 4, pairs):
+        tile = np.prod(bcf.bcf_tuning_config(2, si))
+        choices.append((si, -1))  # the worker merges
+        choices += [(si, mi) for mi in configs(bcf, 1, 4, pairs)
+                    if np.prod(bcf.bcf_tuning_config(1, mi)) <= tile]
+    for si, mi in choices:
         bcf.bcf_tuning_set([dict(op=2, key_bytes=4, has_vals=int(pairs), n_min=0, n_max=1 << 40,
-                                 block_cfg=0, merge_cfg=0, seg_cfg=si)])
+                                 block_cfg=0, merge_cfg=mi, seg_cfg=si)])
         kd = to_dev(keys)
         ko = torch.empty_like(kd)
         vd = to_dev(vals) if pairs else None
         vo = torch.empty_like(vd) if pairs else None
         bcf.bcf_segmented_sort(ko, vo, kd, vd, od, kt=0)
         torch.cuda.synchronize()
-        assert np.array_equal(from_dev(ko, np.uint32), ek), si
+        assert np.array_equal(from_dev(ko, np.uint32), ek), (si, mi)
         if pairs:
-            assert np.array_equal(from_dev(vo, np.uint32), ev), si
+            assert np.array_equal(from_dev(vo, np.uint32), ev), (si, mi)
     bcf.bcf_tuning_set(None)
