@@ -626,9 +626,20 @@ def segmented_bench(torch, dev, bcf):
             with torch.cuda.graph(graph, stream=side):
                 call()
             ms = timed_ms(torch, torch.cuda.current_stream(dev), graph.replay, warmup=2, reps=5)
+            # where the time goes: one direct call with the library's launch records
+            bcf.bcf_profile_collect()
+            bcf.bcf_profile_enable(True)
+            with torch.cuda.stream(side):
+                call()
+            side.synchronize()
+            bcf.bcf_profile_enable(False)
+            prof = bcf.bcf_profile_collect()
+            parts = {k: round(v["total_ms"], 3) for k, v in prof.items() if v["launches"]}
             out[f"{label}{' +u32' if pairs else ''}"] = {
                 "segments": int(sizes.size), "keys": n, "ms": ms, "keys_per_s": n / (ms * 1e-3),
-                "payload": "u32" if pairs else None, "exact": exact}
+                "payload": "u32" if pairs else None, "exact": exact,
+                "merges": "launches" if "merge" in parts else "worker",
+                "parts_ms": parts}
             del vd, vo, ws, graph
             torch.cuda.empty_cache()
         del kd, ko, od
@@ -1006,6 +1017,7 @@ def summary_of(line, peak):
     sg = line.get("segmented")
     if sg:
         s["segmented_ms"] = {k: r3(v["ms"]) for k, v in sg["results"].items()}
+        s["segmented_exact"] = all(v.get("exact", False) for v in sg["results"].values())
     pb = line.get("pivot_buckets")
     if pb:
         s["pivot_bucket_speedup"] = {k: r3(v["speedup"]) for k, v in pb["results"].items()}
@@ -1109,13 +1121,14 @@ def run_gpu(args, world, rank, local, pg):
         e2e_step(i)
     torch.cuda.synchronize()
     barrier()
-    # three timed regions of e2e_steps steps each; the median is reported (a
-    # host-side stall in one region -- the host loop issues every step -- does
-    # not decide the number), and all three are listed
+    # five timed regions of e2e_steps steps each; the median is reported (a
+    # host-side stall in one or two regions -- the host loop issues every step,
+    # and an nvidia-smi query on the host can hold the driver for tens of ms --
+    # does not decide the number), and all five are listed
     regions = []
     gc.collect()
     gc.disable()
-    for _ in range(3):
+    for _ in range(5):
         h0 = torch.cuda.Event(enable_timing=True)
         h1 = torch.cuda.Event(enable_timing=True)
         h0.record(stream)

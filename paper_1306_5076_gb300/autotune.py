@@ -98,9 +98,13 @@ def tune_sort(torch, kb, pairs, reps, log):
     return rows
 
 
-# (n_min, n_max, segments, largest segment) of the segmented sort's size bands:
-# small batches (as the request server coalesces them) and large ones
-SEG_BANDS = [(0, 1 << 24, 2000, 1 << 14), (1 << 24, 1 << 48, 5000, 1 << 18)]
+# (n_min, n_max, probes) of the segmented sort's size bands: small batches (as
+# the request server coalesces them) and large ones; each probe is (segments,
+# largest segment) of a log-uniform size law, and a band's candidates are
+# ranked by their summed time over its probes (large batches of short and of
+# long segments)
+SEG_BANDS = [(0, 1 << 24, [(2000, 1 << 14)]),
+             (1 << 24, 1 << 48, [(5000, 1 << 18), (50000, 1 << 14)])]
 
 
 def tune_segmented(torch, kb, pairs, reps, log):
@@ -113,33 +117,37 @@ def tune_segmented(torch, kb, pairs, reps, log):
 
     kt = bcf.BCF_U32 if kb == 4 else bcf.BCF_U64
     merges = _configs(1, kb, pairs)
+    cands = []
+    for si, (se, snt) in _configs(2, kb, pairs):
+        cands.append((si, -1, f"{se}x{snt}", "worker"))
+        cands += [(si, mi, f"{se}x{snt}", f"launches, {me * mnt}-key tiles")
+                  for mi, (me, mnt) in merges if me * mnt <= se * snt]
     rows = []
-    for n_min, n_max, nseg, hi in SEG_BANDS:
-        sizes = workloads.segment_sizes(nseg, hi, seed=4000)
-        offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
-        n = int(offs[-1])
-        k, v = _inputs(torch, n, kb, pairs)
-        ko = torch.empty_like(k)
-        vo = torch.empty_like(v) if pairs else None
-        od = torch.from_numpy(offs).to("cuda")
-        ws = torch.empty(bcf.bcf_workspace_bytes(bcf.BCF_OP_SEGMENTED, n, nseg, kt, pairs),
-                         dtype=torch.uint8, device="cuda")
-        best = None
-        for si, (se, snt) in _configs(2, kb, pairs):
-            for mi, mt in [(-1, None)] + [(mi, me * mnt) for mi, (me, mnt) in merges
-                                          if me * mnt <= se * snt]:
+    for n_min, n_max, probes in SEG_BANDS:
+        total = {c: 0.0 for c in cands}
+        for nseg, hi in probes:
+            sizes = workloads.segment_sizes(nseg, hi, seed=4000)
+            offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+            n = int(offs[-1])
+            k, v = _inputs(torch, n, kb, pairs)
+            ko = torch.empty_like(k)
+            vo = torch.empty_like(v) if pairs else None
+            od = torch.from_numpy(offs).to("cuda")
+            ws = torch.empty(bcf.bcf_workspace_bytes(bcf.BCF_OP_SEGMENTED, n, nseg, kt, pairs),
+                             dtype=torch.uint8, device="cuda")
+            for c in cands:
+                si, mi, shape, who = c
                 bcf.bcf_tuning_set([dict(op=bcf.BCF_OP_SEGMENTED, key_bytes=kb,
                                          has_vals=int(pairs), n_min=0, n_max=1 << 48,
                                          block_cfg=0, merge_cfg=mi, seg_cfg=si)])
                 ms = _time(torch, lambda: bcf.bcf_segmented_sort(ko, vo, k, v, od, kt=kt, ws=ws),
                            reps)
-                who = "worker" if mi < 0 else f"launches, {mt}-key tiles"
-                log(f"segmented kb={kb} pairs={int(pairs)} n={n} cfg={se}x{snt} merges: {who}: "
+                log(f"segmented kb={kb} pairs={int(pairs)} n={n} cfg={shape} merges: {who}: "
                     f"{ms:.3f} ms")
-                if best is None or ms < best[0]:
-                    best = (ms, si, mi)
-        rows.append((bcf.BCF_OP_SEGMENTED, kb, int(pairs), n_min, n_max, 0, best[2], best[1]))
-        del k, v, ko, vo, od, ws
+                total[c] += ms
+            del k, v, ko, vo, od, ws
+        best = min(cands, key=lambda c: total[c])
+        rows.append((bcf.BCF_OP_SEGMENTED, kb, int(pairs), n_min, n_max, 0, best[1], best[0]))
     return rows
 
 
@@ -147,6 +155,8 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--quick", action="store_true", help="fewer repetitions")
     ap.add_argument("--out", default=TABLE)
+    ap.add_argument("--only", choices=("sort", "segmented"), default=None,
+                    help="tune one operation; the other's rows are kept from --out")
     args = ap.parse_args(argv)
     import torch
 
@@ -154,9 +164,19 @@ def main(argv=None):
     reps = 3 if args.quick else 7
     log = lambda m: print(m, flush=True)  # noqa: E731
     rows = []
+    if args.only and os.path.exists(args.out):
+        keep = {"sort": {bcf.BCF_OP_SEGMENTED}, "segmented": {bcf.BCF_OP_SORT, bcf.BCF_OP_MERGE}}
+        for line in open(args.out):
+            if line.strip() and not line.startswith("#"):
+                r = tuple(int(x) for x in line.split())
+                if r[0] in keep[args.only]:
+                    rows.append(r)
     for kb, pairs in KINDS:
-        rows += tune_sort(torch, kb, pairs, reps, log)
-        rows += tune_segmented(torch, kb, pairs, reps, log)
+        if args.only in (None, "sort"):
+            rows += tune_sort(torch, kb, pairs, reps, log)
+        if args.only in (None, "segmented"):
+            rows += tune_segmented(torch, kb, pairs, reps, log)
+    rows.sort(key=lambda r: (r[1], r[2], r[0], r[3]))
     bcf.bcf_tuning_set(None)
     name = torch.cuda.get_device_name()
     with open(args.out, "w") as f:
