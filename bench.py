@@ -915,6 +915,9 @@ def profile_case(args):
     both layouts, two launches each; 'pb' = pivot-bucket sort of 2^26
     16-distinct u32 keys, twice; 'seg' = segmented sort of 5,000 segments
     with sizes log-uniform over [1, 2^18] (about 1.05e8 u32 keys), twice;
+    'seg_c4' = the segmented workload itself (100,000 segments, about 2.1e9
+    u32 keys drawn on the device as the bench draws them), twice -- for a
+    launch list only (one ncu pass per launch);
     'pairs' / 'u64' / 'u64p' = sort of 2^26 uniform keys, twice: u32 keys
     with u32 payloads, u64 keys, u64 keys with u32 payloads."""
     import numpy as np
@@ -955,6 +958,17 @@ def profile_case(args):
         ko = torch.empty_like(kd)
         for _ in range(2):
             bcf.bcf_sort_keys(ko, kd, kt=bcf.BCF_U32, algorithm="pivot_buckets")
+    elif args.profile_case == "seg_c4":
+        sizes = workloads.segment_sizes(100_000, 1 << 18, seed=4000)
+        offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+        n = int(offs[-1])
+        g = torch.Generator(device=dev)
+        g.manual_seed(4001)
+        kd = torch.randint(-2**31, 2**31 - 1, (n,), dtype=torch.int32, device=dev, generator=g)
+        ko = torch.empty_like(kd)
+        od = torch.from_numpy(offs).to(dev)
+        for _ in range(2):
+            bcf.bcf_segmented_sort(ko, None, kd, None, od, kt=bcf.BCF_U32)
     else:
         keys, offs = workloads.segments(5_000, 1 << 18, "u32", seed=4000)
         n = keys.size
@@ -1267,7 +1281,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile-case", choices=["cps", "pb", "seg", "pairs", "u64", "u64p"],
+    ap.add_argument("--profile-case", choices=["cps", "pb", "seg", "seg_c4", "pairs", "u64", "u64p"],
                     help="run only a small case of one path (for ncu captures) and exit")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the other key types, the colored prefix sums and the "
