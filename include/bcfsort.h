@@ -86,14 +86,16 @@ enum {
                                 * the segmented sort.  Fastest on duplicate-heavy keys;
                                 * needs bcf_workspace_bytes(BCF_OP_SORT_PB, ...) and
                                 * n < 2^32 (larger n takes the merge path). */
-    BCF_ALGO_AUTO = 2          /* one of the two, chosen per call: every 4096th key is
-                                * sampled and sorted, splitters are picked from it as
-                                * pivot buckets would, and pivot buckets are taken when
-                                * at least 2/3 of the sample equals a splitter (most keys
-                                * would be final after one distribution), else the merge
-                                * path.  Needs the BCF_OP_SORT_PB workspace.  The decision
-                                * reads one word back to the host, so the call
-                                * synchronises `stream` once (not for graph capture). */
+    BCF_ALGO_AUTO = 2          /* one of the two, chosen per call: a sample of at least
+                                * 16384 keys (every 256th to every 4096th key) is sorted,
+                                * splitters are picked from it as pivot buckets would,
+                                * and pivot buckets are taken when at least 1/3 of the
+                                * sample keys, not counting the splitters' own
+                                * occurrences, equal a splitter (those keys would be
+                                * final after one distribution), else the merge path.
+                                * Needs the BCF_OP_SORT_PB workspace.  The decision reads
+                                * two words back to the host, so the call synchronises
+                                * `stream` once (not for graph capture). */
 };
 
 typedef struct {

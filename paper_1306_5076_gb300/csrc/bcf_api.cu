@@ -759,14 +759,23 @@ bcf_status run_sort_pb(void* ko, uint32_t* vo, const void* ki, const uint32_t* v
                        wl.seg_bytes, s, true);
 }
 
-// BCF_ALGO_AUTO: sample every kAutoProbeStride-th key, sort the sample, pick
-// splitters from it as pivot buckets would, and count the sample keys equal to
-// a splitter -- an estimate of the share of keys pivot buckets would leave in
-// final position after one distribution.  Pivot buckets when that share
-// reaches kAutoEqualNum / kAutoEqualDen (measured on GB300: pivot buckets win
-// 2.6x on 16 distinct values and lose 30 % on distinct keys; Zipf(1.1), with
-// about 60 % of the keys in equal buckets, is the break-even), else the merge
-// path.  The count is read back to the host: the call synchronises `s` once.
+// BCF_ALGO_AUTO: sample every S-th key, S = n / kAutoMinSamples clamped to
+// [kPbSampleStride, kAutoMaxStride], sort the sample, pick splitters from it as
+// pivot buckets would, and count the sample keys equal to a splitter beyond
+// the splitters' own occurrences (each splitter is a sample key, which alone
+// would count 255 of a few hundred samples of distinct keys as equal) -- an
+// estimate of the share of keys pivot buckets would leave in final position
+// after one distribution.  Pivot buckets when that share reaches
+// kAutoEqualNum / kAutoEqualDen, else the merge path.  Measured on GB300 at
+// 2^28 keys, with the open buckets on the segmented sort's merge launches:
+// pivot buckets take 8.3 ms on distinct keys, 2.9 ms with 16 distinct values
+// and 5.9 ms on Zipf(1.1) keys (share 0.5) against 6.7 ms on the merge path,
+// a break-even near a share of 0.3 (0.2 with payloads).  The counts are read
+// back to the host: the call synchronises `s` once.
+constexpr uint32_t kAutoMaxStride = 4096;
+constexpr uint64_t kAutoMinSamples = 16384;
+constexpr uint32_t kAutoEqualNum = 1, kAutoEqualDen = 3;
+
 bcf_status choose_auto(const void* ki, uint64_t n, bcf_dtype kt, const bcf_opts* o, void* ws,
                        size_t ws_bytes, cudaStream_t s, bool pairs, bool* use_pb) {
   *use_pb = false;
@@ -779,8 +788,10 @@ bcf_status choose_auto(const void* ki, uint64_t n, bcf_dtype kt, const bcf_opts*
   a.kin = ki;
   a.n = n;
   a.mode = mode_of(kt, o);
-  a.sample_stride = kAutoProbeStride;
-  a.ns = (n + kAutoProbeStride - 1) / kAutoProbeStride;
+  const uint64_t want = n / kAutoMinSamples;
+  const uint64_t stride = want > kAutoMaxStride ? kAutoMaxStride : want;
+  a.sample_stride = static_cast<uint32_t>(stride < kPbSampleStride ? kPbSampleStride : stride);
+  a.ns = (n + a.sample_stride - 1) / a.sample_stride;
   a.samples = wsb + wl.samples;
   a.sorted_samples = wsb + wl.ssorted;
   a.splitters = wsb + wl.splitters;
@@ -800,12 +811,17 @@ bcf_status choose_auto(const void* ki, uint64_t n, bcf_dtype kt, const bcf_opts*
   if ((st = step(kPbStepSplitters)) != BCF_OK) return st;
   if (cudaMemsetAsync(a.equal_count, 0, sizeof(uint32_t), s) != cudaSuccess) return BCF_ECUDA;
   if ((st = step(kPbStepEqualCount)) != BCF_OK) return st;
-  uint32_t equal = 0;
+  uint32_t equal = 0, nsplit = 0;
   if (cudaMemcpyAsync(&equal, a.equal_count, sizeof(equal), cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(&nsplit, a.nsplit, sizeof(nsplit), cudaMemcpyDeviceToHost, s) !=
           cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return BCF_ECUDA;
-  *use_pb = static_cast<uint64_t>(equal) * kAutoEqualDen >= a.ns * kAutoEqualNum;
+  // the splitters' own occurrences in the sample do not count
+  const uint64_t extra = equal > nsplit ? equal - nsplit : 0;
+  const uint64_t rest = a.ns > nsplit ? a.ns - nsplit : 0;
+  *use_pb = rest > 0 && extra * kAutoEqualDen >= rest * kAutoEqualNum;
   return BCF_OK;
 }
 

@@ -270,11 +270,6 @@ constexpr uint32_t kPbSplitters = kPbP - 1;
 constexpr uint32_t kPbBuckets = 2 * kPbSplitters + 1;
 enum { kPbStepSample, kPbStepSplitters, kPbStepCount, kPbStepScatter, kPbStepSegOffsets,
        kPbStepEqualCount };
-// The automatic choice between the merge path and pivot buckets samples every
-// kAutoProbeStride-th key and takes pivot buckets when at least
-// kAutoEqualNum / kAutoEqualDen of the sample equals a splitter.
-constexpr uint32_t kAutoProbeStride = 4096;
-constexpr uint32_t kAutoEqualNum = 2, kAutoEqualDen = 3;
 struct PbArgs {
   const void* kin;            // user keys (original bits)
   uint64_t n;

@@ -126,12 +126,13 @@ def test_large_duplicate_heavy_against_oracle(bcf):
     assert np.array_equal(gk, ek) and np.array_equal(gv, ev)
 
 
-@pytest.mark.parametrize("dist,expect_pb", [("distinct16", True), ("uniform", False),
-                                            ("sorted", False)])
+@pytest.mark.parametrize("dist,expect_pb", [("distinct16", True), ("zipf", True),
+                                            ("uniform", False), ("sorted", False)])
 @pytest.mark.parametrize("pairs", [False, True])
 def test_auto_chooses_by_duplication_and_matches_the_oracle(bcf, dist, expect_pb, pairs):
-    """algorithm="auto": pivot buckets when most sampled keys equal a splitter
-    (16 distinct values), the merge path otherwise; the result is the oracle's
+    """algorithm="auto": pivot buckets when at least a third of the sampled keys
+    (the splitters' own occurrences aside) equal a splitter (16 distinct values;
+    Zipf(1.1) keys, about half), the merge path otherwise; the result is the oracle's
     either way.  The choice shows in the library's launch records: the
     decision itself launches three distribution-kind kernels (sample,
     splitters, count), the pivot-bucket sort five more."""
