@@ -1,7 +1,6 @@
-// bcf_segmented.cu -- sorting many independent segments in one persistent
-// launch (the batching extension of the paper's method; the paper's own
-// "segmented ShearSort" sorts segments inside one tile, Sec. 3.1 and
-// Algorithm 5).
+// bcf_segmented.cu -- sorting many independent segments (the batching
+// extension of the paper's method; the paper's own "segmented ShearSort"
+// sorts segments inside one tile, Sec. 3.1 and Algorithm 5).
 //
 // Plan (plan_kernel, one CTA): every segment is classified --
 //   tiny   : 1..512 keys, sorted by one warp entirely in registers (Batcher's
@@ -9,25 +8,32 @@
 //   others : block-sorted in T-key tiles (T-aligned in the array, clipped to
 //            the segment, ragged ends padded), then merged pairwise with
 //            ceil(log2 tiles) segment-local merge passes (Sec. 3.2; Lemma 2).
-// The plan publishes the first-phase work items in a device queue: all tile
-// sorts, then groups of tiny segments (one per warp of the worker CTA).
+// The plan queues groups of tiny segments (one per warp of a worker CTA);
+// fill_tiles_kernel queues the tile sorts, one thread per slot.
 //
-// Execution (seg_worker, persistent: one wave of co-resident CTAs): each CTA
-// repeatedly takes the next queue slot.  When the last item of a segment's
-// pass completes, the CTA that completed it enqueues the segment's next pass
-// (one item per T-aligned output tile of the segment), so every segment
-// advances as soon as its own data is ready and no grid-wide barrier exists.
-// Waiting for a slot to be published is bounded (global timer); on expiry the
-// device error word is set and the CTA exits.
+// The merge passes run in one of two forms, chosen by the tuning table:
 //
-// The CTA that publishes a segment's merge pass first finds the exact
-// splitters of all its pieces (merge path, one warp per piece, 32-ary
-// search), so a piece starts with its two splits in hand -- for passes of up
-// to 16 pieces per warp; a longer segment's pieces search their own, so that
-// one huge segment does not wait on a single CTA.  Pieces read their
-// windows straight from global memory (.cg loads: data written by other SMs
-// earlier in the same launch must not be served from a stale L1 line), then
-// run the same conflict-free bitonic merge as the merge pass kernel.
+// 1. In the persistent worker (seg_worker, one wave of co-resident CTAs):
+// each CTA repeatedly takes the next queue slot.  When the last item of a
+// segment's pass completes, the CTA that completed it enqueues the segment's
+// next pass (one item per T-aligned output tile of the segment), so every
+// segment advances as soon as its own data is ready and no grid-wide barrier
+// exists.  Waiting for a slot to be published is bounded (global timer); on
+// expiry the device error word is set and the CTA exits.  The CTA that
+// publishes a segment's merge pass first finds the exact splitters of all its
+// pieces (merge path, one warp per piece, 32-ary search), so a piece starts
+// with its two splits in hand -- for passes of up to 16 pieces per warp; a
+// longer segment's pieces search their own, so that one huge segment does not
+// wait on a single CTA.  Pieces read their windows straight from global
+// memory (.cg loads: data written by other SMs earlier in the same launch
+// must not be served from a stale L1 line), then run the same conflict-free
+// bitonic merge as the merge pass kernel.
+//
+// 2. As launches of the merge kernel (bcf_seg_merge.cu): the plan also lists
+// the segments of two or more tiles, most passes first; the tile sorts run
+// one CTA per tile (seg_tile_kernel) and the tiny segments one warp each
+// (seg_tiny_kernel); the host then launches a partition and a merge per
+// number of passes to go.
 #include <cuda_runtime.h>
 
 #include "bcf_segmented.cuh"
@@ -61,6 +67,43 @@ __device__ __forceinline__ T block_scan_incl(T v, T* warp_sums, T& total) {
   total = warp_sums[31];
   __syncthreads();
   return v;
+}
+
+// Inclusive block scan of three values per thread at once (blockDim.x ==
+// 1024): one set of barriers for the plan's three running sums.
+__device__ __forceinline__ void block_scan3_incl(unsigned long long (&v)[3],
+                                                 unsigned long long (*warp_sums)[32],
+                                                 unsigned long long (&total)[3]) {
+  const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const unsigned long long u = __shfl_up_sync(0xFFFFFFFFu, v[i], d);
+      if (lane >= static_cast<uint32_t>(d)) v[i] += u;
+    }
+  }
+  if (lane == 31) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) warp_sums[i][w] = v[i];
+  }
+  __syncthreads();
+  if (w < 3) {  // warp i scans the warp sums of value i
+    unsigned long long x = warp_sums[w][lane];
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const unsigned long long u = __shfl_up_sync(0xFFFFFFFFu, x, d);
+      if (lane >= static_cast<uint32_t>(d)) x += u;
+    }
+    warp_sums[w][lane] = x;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    if (w > 0) v[i] += warp_sums[i][w - 1];
+    total[i] = warp_sums[i][31];
+  }
+  __syncthreads();
 }
 
 // The list of segments whose merge passes run outside the worker: a counting
@@ -104,7 +147,7 @@ __device__ __forceinline__ void plan_list(const SegArgs& a, uint32_t T, uint32_t
 
 __global__ void __launch_bounds__(1024) plan_kernel(const SegArgs a, uint32_t T,
                                                     uint32_t per_group) {
-  __shared__ unsigned long long ws[32];
+  __shared__ unsigned long long ws[3][32];
   __shared__ uint32_t s_hist[kSegMaxPasses + 2];
   for (uint32_t q = threadIdx.x; q < kSegMaxPasses + 2; q += blockDim.x) s_hist[q] = 0;
   __syncthreads();
@@ -121,15 +164,11 @@ __global__ void __launch_bounds__(1024) plan_kernel(const SegArgs a, uint32_t T,
     const unsigned long long tot =
         tiles + (listed ? 0ull : static_cast<unsigned long long>(g.passes) * g.pieces);
     if (listed) atomicAdd(&s_hist[g.passes < kSegMaxPasses ? g.passes : kSegMaxPasses], 1u);
-    unsigned long long sum;
-    const unsigned long long t_incl = block_scan_incl(tiles, ws, sum);
-    const unsigned long long t_excl = t_incl - tiles;
-    const unsigned long long sum_tiles = sum;
-    const unsigned long long y_incl = block_scan_incl(tiny, ws, sum);
-    const unsigned long long sum_tiny = sum;
-    const unsigned long long tot_incl = block_scan_incl(tot, ws, sum);
-    (void)tot_incl;
-    const unsigned long long sum_tot = sum;
+    unsigned long long v[3] = {tiles, tiny, tot}, sum[3];
+    block_scan3_incl(v, ws, sum);
+    const unsigned long long t_excl = v[0] - tiles;
+    const unsigned long long y_incl = v[1];
+    const unsigned long long sum_tiles = sum[0], sum_tiny = sum[1], sum_tot = sum[2];
     if (s < a.nseg) {
       a.items_left[s] = g.tiles;
       a.tile_base[s] = carry_tiles + t_excl;
