@@ -17,7 +17,7 @@ steps.
   cpu_baseline the CPU oracle (test infrastructure) on a bounded sample, all
                host cores
 Multi-GPU: each rank sorts its own 2^28 keys (independent replicas; sorting
-does not shard without an exchange step, which this build does not have).
+does not shard without an exchange step, which this library does not have).
 
 --impl reference times the oracle itself on the host cores (bounded sample per
 step) and prints the same line with "impl": "reference".

@@ -72,7 +72,7 @@ typedef enum {
     BCF_ENOMEM = 2,       /* workspace smaller than bcf_workspace_bytes() */
     BCF_ECUDA = 3,        /* a CUDA launch or runtime call failed */
     BCF_ETIMEOUT = 4,     /* a device-side bounded wait ran out (see bcf_last_device_error) */
-    BCF_EUNSUPPORTED = 5  /* valid request this build does not handle (e.g. too many segments) */
+    BCF_EUNSUPPORTED = 5  /* valid request this library does not handle (e.g. too many segments) */
 } bcf_status;
 
 /* Sorting algorithms (bcf_opts.algorithm).  Both give the identical, stable

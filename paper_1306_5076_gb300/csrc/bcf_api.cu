@@ -1277,7 +1277,7 @@ const char* bcf_status_string(bcf_status s) {
     case BCF_ENOMEM: return "BCF_ENOMEM: workspace too small";
     case BCF_ECUDA: return "BCF_ECUDA: CUDA error";
     case BCF_ETIMEOUT: return "BCF_ETIMEOUT: device-side wait ran out";
-    case BCF_EUNSUPPORTED: return "BCF_EUNSUPPORTED: not supported by this build";
+    case BCF_EUNSUPPORTED: return "BCF_EUNSUPPORTED: not supported by this library";
     default: return "BCF: unknown status";
   }
 }
