@@ -170,6 +170,212 @@ __device__ __forceinline__ T read_seq(const T* sa, const T* sb, uint32_t k, uint
   return lds_pred(sb + (Tm1 - k), isB, v);
 }
 
+// The two windows of one output tile -- the piece p of a pair whose A-window
+// starts at split i0 and ends at split i1 -- and where they are staged in a
+// tile's shared memory, with the tile's output start and count.  For sorted
+// runs the splits grow with the diagonal and the clamp below changes
+// nothing.  Runs that are not sorted (a broken precondition of
+// bcf_merge_runs) can make neighbouring searches disagree; clamping i1 into
+// the windows i0 allows keeps every staged window inside its run and within
+// the tile's shared memory, so such input gives an undefined order but never
+// an out-of-bounds access.
+struct TileWindows {
+  uint64_t ga0, ga1, gb0, gb1;  // absolute source index ranges of the A and B windows
+  uint64_t out0;                // first index of the Tm-aligned output tile
+  uint32_t na, nb, front, cnt;  // window lengths; real output slots [front, front + cnt)
+  uint32_t offA, lenA, offB, offvA, offvB;
+};
+template <typename K>
+__device__ __forceinline__ TileWindows tile_windows(const Piece& p, uint64_t i0, uint64_t i1) {
+  constexpr uint64_t VK = 16 / sizeof(K);
+  {
+    const uint64_t lo1 = p.d1 > p.nb_tot && p.d1 - p.nb_tot > i0 ? p.d1 - p.nb_tot : i0;
+    const uint64_t hi1 = i0 + (p.d1 - p.d0) < p.na_tot ? i0 + (p.d1 - p.d0) : p.na_tot;
+    i1 = i1 < lo1 ? lo1 : (i1 > hi1 ? hi1 : i1);
+  }
+  TileWindows w;
+  const uint64_t j0 = p.d0 - i0, j1 = p.d1 - i1;
+  w.na = static_cast<uint32_t>(i1 - i0);
+  w.nb = static_cast<uint32_t>(j1 - j0);
+  w.front = p.front;
+  w.cnt = static_cast<uint32_t>(p.d1 - p.d0);
+  w.out0 = p.out0;
+  w.ga0 = p.src + i0;
+  w.ga1 = p.src + i1;
+  w.gb0 = p.src + p.na_tot + j0;
+  w.gb1 = p.src + p.na_tot + j1;
+  w.offA = static_cast<uint32_t>(w.ga0 & (VK - 1));
+  w.lenA = static_cast<uint32_t>((w.offA + w.na + VK - 1) & ~(VK - 1));  // 16B multiple
+  w.offB = static_cast<uint32_t>(w.gb0 & (VK - 1));
+  w.offvA = static_cast<uint32_t>(w.ga0 & 3);
+  w.offvB = static_cast<uint32_t>(w.gb0 & 3);
+  return w;
+}
+
+// Staged layout in a tile's shared memory `body`: A keys, B keys, then (with
+// payloads) A values and B values, each 16-byte aligned.
+template <typename K, bool PAIRS, int E, int NT>
+struct StagedTile {
+  K* smA;
+  K* smB;
+  uint32_t* svA;
+  uint32_t* svB;
+  __device__ __forceinline__ StagedTile(const TileWindows& w, unsigned char* body) {
+    smA = reinterpret_cast<K*>(body);
+    smB = smA + w.lenA;
+    svA = reinterpret_cast<uint32_t*>(body + MergeSmem<K, PAIRS, E, NT>::kKeyBytes);
+    svB = svA + ((w.offvA + w.na + 3) & ~3u);
+  }
+};
+
+// Thread 0: announce the tile's byte count on `bar`, then issue its bulk copies.
+template <typename K, bool PAIRS, int E, int NT>
+__device__ __forceinline__ void stage_issue(const MergeArgs& a, const TileWindows& w,
+                                            unsigned char* body, uint64_t* bar) {
+  const StagedTile<K, PAIRS, E, NT> t(w, body);
+  const K* kin = static_cast<const K*>(a.kin);
+  const uint64_t n = a.n;
+  // the total byte count is announced before any copy can complete
+  uint32_t total = body_bytes<K>(w.ga0, w.ga1, n) + body_bytes<K>(w.gb0, w.gb1, n);
+  if constexpr (PAIRS)
+    total += body_bytes<uint32_t>(w.ga0, w.ga1, n) + body_bytes<uint32_t>(w.gb0, w.gb1, n);
+  mbar_arrive_expect_tx(bar, total);
+  stage_bulk(t.smA, kin, w.ga0, w.ga1, n, bar);
+  stage_bulk(t.smB, kin, w.gb0, w.gb1, n, bar);
+  if constexpr (PAIRS) {
+    stage_bulk(t.svA, a.vin, w.ga0, w.ga1, n, bar);
+    stage_bulk(t.svB, a.vin, w.gb0, w.gb1, n, bar);
+  }
+}
+
+// Warp 1 (lane = threadIdx.x - 32): the windows' ragged tails at the array's
+// end.  Lanes 0-7: A keys, 8-15: B keys, 16-23: A values, 24-31: B values,
+// one store instruction per window.
+template <typename K, bool PAIRS, int E, int NT>
+__device__ __forceinline__ void stage_tails(const MergeArgs& a, const TileWindows& w,
+                                            unsigned char* body, uint32_t lane) {
+  const StagedTile<K, PAIRS, E, NT> t(w, body);
+  const K* kin = static_cast<const K*>(a.kin);
+  stage_tail(t.smA, kin, w.ga0, w.ga1, a.n, lane, 0);
+  stage_tail(t.smB, kin, w.gb0, w.gb1, a.n, lane, 8);
+  if constexpr (PAIRS) {
+    stage_tail(t.svA, a.vin, w.ga0, w.ga1, a.n, lane, 16);
+    stage_tail(t.svB, a.vin, w.gb0, w.gb1, a.n, lane, 24);
+  }
+}
+
+// The merge of a staged tile (its windows landed in `body`, visible to every
+// thread): the bitonic sequence read into registers, the network (whose
+// transposes reuse `body`), the samples and the stores.  SAMPLES: 0 writes
+// none, 1 writes regular-pass samples when a.samples_out is set, 2 writes
+// samples at array positions that are multiples of kRunSampleStride
+// (irregular passes with a successor).
+template <typename K, bool PAIRS, int E, int NT, bool MAP, int SAMPLES>
+__device__ __forceinline__ void merge_staged(const MergeArgs& a, const TileWindows& w,
+                                             unsigned char* body) {
+  constexpr int Tm = E * NT;
+  const uint32_t tid = threadIdx.x;
+  const StagedTile<K, PAIRS, E, NT> t(w, body);
+  const uint32_t na = w.na, nb = w.nb, front = w.front, cnt = w.cnt;
+  const uint64_t out0 = w.out0;
+
+  // Read the bitonic sequence into STR registers: k = e*NT + tid.
+  //   [0, front)            -inf pads          (rank k)
+  //   [front, front+na)     A[k - front]       (rank k)
+  //   [front+na, Tm-nb)     +inf pads          (rank Tm + k)
+  //   [Tm-nb, Tm)           B[Tm-1-k]          (rank front + na + (Tm-1-k))
+  Frag<K, PAIRS, E> f;
+  const uint32_t endA = front + na, begB = Tm - nb;
+  const uint32_t warp0 = tid & ~31u;
+  const K* sa = t.smA + w.offA;
+  const K* sb = t.smB + w.offB;
+  const int mode_in = MAP ? a.mode_in : 0;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const uint32_t k = e * NT + tid;
+    const uint32_t row0 = e * NT + warp0;
+    bool real;
+    K key = read_seq<K>(sa, sb, k, row0, front, endA, begB, Tm - 1, KeyLimits<K>::kMin,
+                        KeyLimits<K>::kMax, real);
+    if constexpr (MAP) key = real ? map_key(key, mode_in) : key;
+    f.k[e] = key;
+    if constexpr (PAIRS) {
+      bool rv;
+      f.v[e] = read_seq<uint32_t>(t.svA + w.offvA, t.svB + w.offvB, k, row0, front, endA, begB,
+                                  Tm - 1, 0u, 0u, rv);
+      f.ix[e] = k >= begB ? endA + (Tm - 1 - k) : (k < endA ? k : Tm + k);
+    }
+  }
+
+  f.one = g_unit_multiplier;
+  bitonic_merge_str<NT, CeForms<K, PAIRS>::kMergeBlk, CeForms<K, PAIRS>::kMergeOth>(
+      f, reinterpret_cast<uint32_t*>(body));
+  // samples of the output for the next pass's merge-path search: the keys at
+  // array positions that are multiples of S, still in mapped order (a pass
+  // with a successor writes no unmapped keys)
+  if constexpr (SAMPLES == 1) {
+    if (a.samples_out && ((out0 + tid * E) % kSampleStride) == 0 && tid * E < cnt)
+      static_cast<K*>(a.samples_out)[(out0 + tid * E) / kSampleStride] = f.k[0];
+  } else if constexpr (SAMPLES == 2) {
+    if (((out0 + tid * E) % kRunSampleStride) == 0 && tid * E >= front && tid * E < front + cnt)
+      static_cast<K*>(a.samples_out)[(out0 + tid * E) / kRunSampleStride] = f.k[0];
+  }
+
+  // outputs: BLK layout, thread holds tile slots tid*E .. tid*E+E-1
+  K* kout = static_cast<K*>(a.kout) + out0;
+  uint32_t* vout = PAIRS ? a.vout + out0 : nullptr;
+  const uint32_t s0 = tid * E;
+  const int mode_out = MAP ? a.mode_out : 0;
+  if (s0 >= front && s0 + E <= front + cnt) {
+    // out0 and s0 are multiples of 32 bytes: the base pointers decide alignment
+    if constexpr (MAP) {
+#pragma unroll
+      for (int e = 0; e < E; ++e) f.k[e] = unmap_key(f.k[e], mode_out);  // last use of f.k
+    }
+    store_run<E>(kout + s0, f.k, is_aligned32(a.kout));
+    if constexpr (PAIRS) store_run<E>(vout + s0, f.v, is_aligned32(a.vout));
+  } else {
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const uint32_t s = s0 + e;
+      if (s >= front && s < front + cnt) {
+        kout[s] = MAP ? unmap_key(f.k[e], mode_out) : f.k[e];
+        if constexpr (PAIRS) vout[s] = f.v[e];
+      }
+    }
+  }
+}
+
+// One output tile whose windows were derived beforehand (the segmented
+// sort's persistent merge: thread 0 derives them once for the CTA), staged and
+// merged by the calling CTA: thread 0 stages the windows with bulk copies
+// completing on `bar` (initialised by the caller) and waits for phase parity
+// `phase`; warp 1 stages the ragged tails.
+// Returns false when the wait for the bulk copies ran out (the error word is
+// set; the caller's CTA stops).  Thread 0 calls on_issued() once its bulk
+// copies are issued, before it waits for them.
+template <typename K, bool PAIRS, int E, int NT, bool MAP, int SAMPLES, typename OnIssued>
+__device__ __forceinline__ bool merge_windows(const MergeArgs& a, const TileWindows& w,
+                                              uint64_t* bar, uint32_t phase,
+                                              unsigned char* body, int* s_ok,
+                                              OnIssued&& on_issued) {
+  const uint32_t tid = threadIdx.x;
+  if (tid == 0) {
+    stage_issue<K, PAIRS, E, NT>(a, w, body, bar);
+    on_issued();
+    // one thread waits (bounded); the barrier below releases the others
+    bool ok = mbar_wait_bounded(bar, phase, a.err, kErrTmaTimeout, a.wait_ns);
+    if (!ok) mbar_wait_bounded(bar, phase, nullptr, 0, a.wait_ns);  // let copies in flight land
+    *s_ok = ok ? 1 : 0;
+  } else if (tid >= 32 && tid < 64) {
+    stage_tails<K, PAIRS, E, NT>(a, w, body, tid - 32);
+  }
+  __syncthreads();
+  if (!*s_ok) return false;
+  merge_staged<K, PAIRS, E, NT, MAP, SAMPLES>(a, w, body);
+  return true;
+}
+
 // One output tile: the piece p of a pair, whose A-window starts at split i0
 // and ends at split i1, merged into its Tm-aligned output tile.  Thread 0
 // stages the windows with bulk copies completing on `bar` (initialised by
@@ -179,6 +385,10 @@ __device__ __forceinline__ T read_seq(const T* sa, const T* sb, uint32_t k, uint
 // passes with a successor).  Returns false when the wait for the bulk copies
 // ran out (the error word is set; the caller's CTA stops).  Thread 0 calls
 // on_issued() once its bulk copies are issued, before it waits for them.
+// (The same steps as merge_windows, with the geometry derived by every thread
+// from the piece: kept separate because the one-shot kernels' pieces come
+// from the block index, and the 64-bit pair kernels took 96 instead of 72
+// registers when they shared merge_staged's code.)
 template <typename K, bool PAIRS, int E, int NT, bool MAP, int SAMPLES, typename OnIssued>
 __device__ __forceinline__ bool merge_tile(const MergeArgs& a, const Piece& p, uint64_t i0,
                                            uint64_t i1, uint64_t* bar, uint32_t phase,

@@ -152,21 +152,27 @@ constexpr int seg_merge_min_ctas() {
 }
 
 // Persistent form of merge_kernel over the launch's work items: CTA b takes
-// item b first, then untaken ones from an atomic counter per launch, so the
+// item b first, then untaken items from an atomic counter per launch, so the
 // items in flight stay a narrow band of the arrays as in a one-shot launch
 // (CTA b taking b, b + gridDim.x, ... lets the CTAs drift apart: 0.47 against
-// 0.39 ms per pass of 2^28 keys).  Thread 0 works two items ahead: while the
-// current item's bulk copies are in flight it reads the record and splits
-// of the item it claimed during the previous item into the other half of a
-// two-entry shared buffer, and claims the next one, whose counter value it
-// needs only an item later.  The mbarrier is initialised once and its phase
-// alternates per item.
+// 0.39 ms per pass of 2^28 keys).  Thread 0 works an item ahead: while the
+// current item's bulk copies are in flight it reads the next item's record
+// and splits into the other half of a two-entry shared buffer, and claims the
+// item after that, whose counter value it needs only an item later.  For
+// 32-bit keys without payloads thread 0 also derives that item's windows once
+// for the whole CTA (the other threads read them instead of each deriving them
+// from 64-bit positions: 0.366 against 0.393 ms per pass of 2^28 keys); with
+// payloads every thread derives them (the shared form was 8 % slower there),
+// and so do 64-bit keys (not measured in the shared form).  The mbarrier is
+// initialised once and its phase alternates per item.
 template <typename K, bool PAIRS, int E, int NT, bool MAP, bool SMP>
 __global__ void __launch_bounds__(NT, (seg_merge_min_ctas<K, PAIRS, E, NT>()))
     seg_merge_kernel(const MergeArgs a, const SegPassList L) {
+  constexpr bool kShared = !PAIRS && sizeof(K) == 4;  // windows derived by thread 0 for the CTA
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ int s_ok;
-  __shared__ SegItem s_item[2];
+  __shared__ TileWindows s_win[kShared ? 2 : 1];
+  __shared__ SegItem s_item[kShared ? 1 : 2];
   __shared__ uint64_t s_split[2][2];
   __shared__ uint64_t s_idx[2];
   __shared__ uint64_t s_claim;  // thread 0: the item after the one in the other slot
@@ -180,9 +186,14 @@ __global__ void __launch_bounds__(NT, (seg_merge_min_ctas<K, PAIRS, E, NT>()))
       const SegItem d = L.items[item];
       const uint64_t i0 = a.splits[item];
       const uint64_t i1 = item + 1 < nitems ? a.splits[item + 1] : 0;
-      s_item[slot] = d;
-      s_split[slot][0] = i0;
-      s_split[slot][1] = i1;
+      if constexpr (kShared) {
+        const Piece p = piece_of_item(d, E * NT);
+        s_win[slot] = tile_windows<K>(p, i0, p.last ? p.na_tot : i1);
+      } else {
+        s_item[slot] = d;
+        s_split[slot][0] = i0;
+        s_split[slot][1] = i1;
+      }
     }
   };
   // the record loads and the claim are independent, so their latencies overlap
@@ -203,12 +214,19 @@ __global__ void __launch_bounds__(NT, (seg_merge_min_ctas<K, PAIRS, E, NT>()))
   __syncthreads();
 #pragma unroll 1
   for (uint32_t phase = 0; s_idx[phase] < nitems; phase ^= 1u) {
-    const Piece p = piece_of_item(s_item[phase], E * NT);
-    const uint64_t i0 = s_split[phase][0];
-    const uint64_t i1 = p.last ? p.na_tot : s_split[phase][1];
-    if (!merge_tile<K, PAIRS, E, NT, MAP, SMP ? 2 : 0>(a, p, i0, i1, bar, phase, smraw + 16,
-                                                       &s_ok, [&] { ahead(phase ^ 1u); }))
-      return;
+    bool ok;
+    if constexpr (kShared) {
+      ok = merge_windows<K, PAIRS, E, NT, MAP, SMP ? 2 : 0>(a, s_win[phase], bar, phase,
+                                                            smraw + 16, &s_ok,
+                                                            [&] { ahead(phase ^ 1u); });
+    } else {
+      const Piece p = piece_of_item(s_item[phase], E * NT);
+      const uint64_t i0 = s_split[phase][0];
+      const uint64_t i1 = p.last ? p.na_tot : s_split[phase][1];
+      ok = merge_tile<K, PAIRS, E, NT, MAP, SMP ? 2 : 0>(a, p, i0, i1, bar, phase, smraw + 16,
+                                                         &s_ok, [&] { ahead(phase ^ 1u); });
+    }
+    if (!ok) return;
     __syncthreads();  // shared memory is free before the next item's copies land
   }
 }
