@@ -140,13 +140,16 @@ __global__ void __launch_bounds__(256) seg_partition_kernel(const MergeArgs a, i
   }
 }
 
-// CTAs per SM of the one-shot merge_kernel of the same configuration (its
-// register count as compiled: 32 for 32-bit keys at E = 16, 48 at E = 32 or
-// for 64-bit keys, 56-80 with payloads).  The persistent loop below is held
-// to the same residency; left to the compiler it took 80-168 registers.
+// CTAs per SM of the persistent loop below: the one-shot merge_kernel's
+// residency for the same configuration (its register count as compiled: 32
+// for 32-bit keys at E = 16, 48 at E = 32 or for 64-bit keys, 72-80 for 64-bit
+// keys with payloads), except 32-bit keys with payloads at 128 threads: 64
+// registers and 8 CTAs instead of the one-shot kernel's 56 and 9, which
+// spilled in the loop (100,000 segments with payloads: 39.6 against 41.9 ms
+// of merge launches).  Left to the compiler the loop took 80-168 registers.
 template <typename K, bool PAIRS, int E, int NT>
 constexpr int seg_merge_min_ctas() {
-  constexpr int regs = sizeof(K) == 4 ? (PAIRS ? (NT == 128 ? 56 : 64) : (E == 16 ? 32 : 48))
+  constexpr int regs = sizeof(K) == 4 ? (PAIRS ? 64 : (E == 16 ? 32 : 48))
                                       : (PAIRS ? (NT == 128 ? 72 : 80) : (NT == 128 ? 48 : 64));
   return 65536 / (regs * NT);
 }
