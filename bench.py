@@ -1135,14 +1135,13 @@ def run_gpu(args, world, rank, local, pg):
         e2e_step(i)
     torch.cuda.synchronize()
     barrier()
-    # five timed regions of e2e_steps steps each; the median is reported (a
-    # host-side stall in one or two regions -- the host loop issues every step,
-    # and an nvidia-smi query on the host can hold the driver for tens of ms --
-    # does not decide the number), and all five are listed
+    # seven timed regions of e2e_steps steps each; the median is reported (a
+    # host-side stall of 0.1-0.2 s in up to three regions -- the host loop
+    # issues every step -- does not decide the number), and all seven are listed
     regions = []
     gc.collect()
     gc.disable()
-    for _ in range(5):
+    for _ in range(7):
         h0 = torch.cuda.Event(enable_timing=True)
         h1 = torch.cuda.Event(enable_timing=True)
         h0.record(stream)
