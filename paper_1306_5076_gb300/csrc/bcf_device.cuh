@@ -224,35 +224,33 @@ __device__ __forceinline__ bool is_aligned32(const void* p) {
 __device__ __forceinline__ uint32_t pad32(uint32_t k) { return k + (k >> 5); }
 __host__ __device__ constexpr uint32_t padded_words(uint32_t n) { return n + n / 32; }
 
-// Register fragment: E elements per thread.  PAIRS carries the u32 payload
-// and a tie-break index (the element's rank in the stable input order),
-// because bitonic networks are not stable on their own.
-template <typename K, bool PAIRS, int E>
+// Register fragment: E elements per thread.  PAIRS carries a tie-break index
+// (the element's rank in the stable input order), because bitonic networks
+// are not stable on their own, and -- unless VALS is false -- the u32
+// payload.  (A merge can leave the payloads out of the network and fetch each
+// output's payload by its rank afterwards.)
+template <typename K, bool PAIRS, int E, bool VALS = PAIRS>
 struct Frag {
-  static constexpr int KW = sizeof(K) / 4;           // 32-bit words per key
-  static constexpr int W = KW + (PAIRS ? 2 : 0);     // 32-bit planes per element
+  static constexpr int KW = sizeof(K) / 4;                        // 32-bit words per key
+  static constexpr int W = KW + (PAIRS ? (VALS ? 2 : 1) : 0);     // 32-bit planes per element
   K k[E];
   uint32_t ix[PAIRS ? E : 1];
-  uint32_t v[PAIRS ? E : 1];
+  uint32_t v[PAIRS && VALS ? E : 1];
   uint32_t one;  // the multiplier of the FMA-pipe maximum (see ce()); set by kernels that use it
 
   __device__ __forceinline__ void put(uint32_t* sm, uint32_t plane, int e, uint32_t a) const {
     sm[a] = static_cast<uint32_t>(k[e]);
     if constexpr (KW == 2) sm[plane + a] = static_cast<uint32_t>(static_cast<uint64_t>(k[e]) >> 32);
-    if constexpr (PAIRS) {
-      sm[KW * plane + a] = ix[e];
-      sm[(KW + 1) * plane + a] = v[e];
-    }
+    if constexpr (PAIRS) sm[KW * plane + a] = ix[e];
+    if constexpr (PAIRS && VALS) sm[(KW + 1) * plane + a] = v[e];
   }
   __device__ __forceinline__ void get(const uint32_t* sm, uint32_t plane, int e, uint32_t a) {
     if constexpr (KW == 2)
       k[e] = static_cast<K>(sm[a]) | (static_cast<K>(sm[plane + a]) << 32);
     else
       k[e] = static_cast<K>(sm[a]);
-    if constexpr (PAIRS) {
-      ix[e] = sm[KW * plane + a];
-      v[e] = sm[(KW + 1) * plane + a];
-    }
+    if constexpr (PAIRS) ix[e] = sm[KW * plane + a];
+    if constexpr (PAIRS && VALS) v[e] = sm[(KW + 1) * plane + a];
   }
 };
 
@@ -321,8 +319,9 @@ __device__ __forceinline__ void sel_swap(uint32_t& xr, uint32_t& yr, bool sw) {
 }
 
 // Compare-exchange registers a < b: ascending puts the smaller element in a.
-template <typename K, bool PAIRS, int E>
-__device__ __forceinline__ void ce(Frag<K, PAIRS, E>& f, int a, int b, bool desc, int fma = 0) {
+template <typename K, bool PAIRS, int E, bool VALS>
+__device__ __forceinline__ void ce(Frag<K, PAIRS, E, VALS>& f, int a, int b, bool desc,
+                                   int fma = 0) {
   if constexpr (!PAIRS && sizeof(K) == 4) {
     const uint32_t x = static_cast<uint32_t>(f.k[a]), y = static_cast<uint32_t>(f.k[b]);
     const uint32_t lo = x < y ? x : y;
@@ -369,32 +368,37 @@ __device__ __forceinline__ void ce(Frag<K, PAIRS, E>& f, int a, int b, bool desc
       f.k[a] = static_cast<K>(la | (static_cast<uint64_t>(ha) << 32));
       f.k[b] = static_cast<K>(lb | (static_cast<uint64_t>(hb) << 32));
     }
-    if constexpr (PAIRS) {
-      word(f.ix[a], f.ix[b], 2);
-      word(f.v[a], f.v[b], 3);
-    }
+    if constexpr (PAIRS) word(f.ix[a], f.ix[b], 2);
+    if constexpr (PAIRS && VALS) word(f.v[a], f.v[b], 3);
   }
 }
 
 // The compare-exchange forms each kernel uses, per element kind: in the
 // BLK-layout stages (Blk) and in the other stages and the per-thread network
-// (Oth).  Measured on GB300 (sweeps over the word choices).
+// (Oth).  Block: the block sort; Merge: the merge passes, whose networks carry
+// (key, rank) only (the payloads are gathered by rank afterwards); Piece: the
+// segmented worker's merge pieces, which carry the payloads through the
+// network.  Measured on GB300 (sweeps over the word choices).
 template <typename K, bool PAIRS> struct CeForms;
 template <> struct CeForms<uint32_t, false> {
   static constexpr int kBlockBlk = kFmaKeys, kBlockOth = 0;
   static constexpr int kMergeBlk = kFmaKeys, kMergeOth = 0;
+  static constexpr int kPieceBlk = kMergeBlk, kPieceOth = kMergeOth;
 };
 template <> struct CeForms<uint32_t, true> {
   static constexpr int kBlockBlk = 0, kBlockOth = 0;
-  static constexpr int kMergeBlk = kFmaWord(3), kMergeOth = kFmaWord(3);
+  static constexpr int kMergeBlk = kFmaWord(2), kMergeOth = 0;
+  static constexpr int kPieceBlk = kFmaWord(3), kPieceOth = kFmaWord(3);
 };
 template <> struct CeForms<uint64_t, false> {
   static constexpr int kBlockBlk = kFmaWord(0) | kFmaWord(1), kBlockOth = 0;
   static constexpr int kMergeBlk = 0, kMergeOth = 0;
+  static constexpr int kPieceBlk = kMergeBlk, kPieceOth = kMergeOth;
 };
 template <> struct CeForms<uint64_t, true> {
   static constexpr int kBlockBlk = kFmaWord(1) | kFmaWord(3), kBlockOth = kFmaWord(1) | kFmaWord(3);
   static constexpr int kMergeBlk = 0, kMergeOth = 0;
+  static constexpr int kPieceBlk = 0, kPieceOth = 0;
 };
 
 // Batcher's odd-even merge sort network on N inputs (Knuth vol. 3, Sec.
@@ -492,8 +496,8 @@ struct Geo {
 // is fetched from k ^ (2^(FLIPJ-1) - 1)), turning two ascending halves into
 // one bitonic sequence -- so every compare-exchange of the sort is ascending.
 // Requires bit FLIPJ-1 to lie in TO's register window.
-template <int FROM, int TO, int FLIPJ, int NT, typename K, bool PAIRS, int E>
-__device__ __forceinline__ void relayout(Frag<K, PAIRS, E>& f, uint32_t* sm) {
+template <int FROM, int TO, int FLIPJ, int NT, typename K, bool PAIRS, int E, bool VALS>
+__device__ __forceinline__ void relayout(Frag<K, PAIRS, E, VALS>& f, uint32_t* sm) {
   using G = Geo<E, NT>;
   const uint32_t tid = threadIdx.x;
   __syncthreads();
@@ -523,8 +527,8 @@ __device__ __forceinline__ void relayout(Frag<K, PAIRS, E>& f, uint32_t* sm) {
 
 // Ascending half-cleaner stages on k bits HI down to LO, all inside layout
 // L's register window (FMA: the kFma* forms the compare-exchanges use).
-template <int L, int HI, int LO, int NT, int FMA = 0, typename K, bool PAIRS, int E>
-__device__ __forceinline__ void stages(Frag<K, PAIRS, E>& f) {
+template <int L, int HI, int LO, int NT, int FMA = 0, typename K, bool PAIRS, int E, bool VALS>
+__device__ __forceinline__ void stages(Frag<K, PAIRS, E, VALS>& f) {
   using G = Geo<E, NT>;
 #pragma unroll
   for (int b = HI; b >= LO; --b) {
@@ -541,8 +545,8 @@ __device__ __forceinline__ void stages(Frag<K, PAIRS, E>& f) {
 // barriers but halves the CTAs per SM, which was measured slower).
 // FMA_BLK / FMA_OTH: the compare-exchange forms of the BLK stages / of the
 // others (Frag::one must be set when either is non-zero).
-template <int NT, int FMA_BLK = 0, int FMA_OTH = 0, typename K, bool PAIRS, int E>
-__device__ __forceinline__ void bitonic_merge_str(Frag<K, PAIRS, E>& f, uint32_t* sm) {
+template <int NT, int FMA_BLK = 0, int FMA_OTH = 0, typename K, bool PAIRS, int E, bool VALS>
+__device__ __forceinline__ void bitonic_merge_str(Frag<K, PAIRS, E, VALS>& f, uint32_t* sm) {
   using G = Geo<E, NT>;
   constexpr int r = G::r, t = G::t;
   stages<kSTR, t - 1, t - r, NT, FMA_OTH>(f);

@@ -9,10 +9,10 @@
 // exact number i of A-keys among the first d outputs -- an exact splitter,
 // so every CTA does the same amount of work in every pass, which is what the
 // paper's distribution step is for.  The CTA then
-//   1. stages its A-window and B-window into shared memory with bulk copies
-//      (cp.async.bulk, completion on an mbarrier), each rounded out to whole
-//      16-byte blocks (only the array's last partial block is read with plain
-//      loads);
+//   1. stages the keys of its A-window and B-window into shared memory with
+//      bulk copies (cp.async.bulk, completion on an mbarrier), each rounded
+//      out to whole 16-byte blocks (only the array's last partial block is
+//      read with plain loads);
 //   2. reads the bitonic sequence [pads_min, A, pads_max, reversed B] into
 //      registers in STR layout (a warp reads 32 consecutive shared words;
 //      rows that contain both A- and B-lanes issue two predicated loads so
@@ -20,9 +20,14 @@
 //   3. runs the bitonic merge: log2 Tm ascending register stages in the STR,
 //      MID and BLK layouts joined by two padded, conflict-free transposes --
 //      data-oblivious like the paper's ShearSort merge;
-//   4. writes its Tm outputs with 128-bit stores.
+//   4. writes its Tm output keys with 32-byte stores, and with payloads reads
+//      each output's payload from global memory by its rank and writes those
+//      the same way.
 // Stability: each element carries its rank in the stable merged order (A
-// before B on equal keys); the network compares (key, rank).
+// before B on equal keys); the network compares (key, rank).  The rank also
+// names the element's source position, so the payloads need not travel
+// through the network.  The tile code lives in bcf_merge.cuh (shared with the
+// segmented sort's merge launches).
 #include <cuda_runtime.h>
 
 #include <type_traits>

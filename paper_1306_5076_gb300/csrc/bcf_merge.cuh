@@ -135,15 +135,19 @@ __device__ __forceinline__ void stage_tail(T* dst, const T* src, uint64_t g0, ui
   sts_pred(dst + (mine ? x - a0 : 0), mine, v);
 }
 
+// Shared memory of one merge tile.  Only keys are staged: with payloads the
+// network carries (key, rank), and each output's payload is read from global
+// memory by its rank once the tile is merged (moving the payload through the
+// network took 0.918 against 0.850 ms per pass of 2^28 u32 pairs).
 template <typename K, bool PAIRS, int E, int NT>
 struct MergeSmem {
   static constexpr int Tm = E * NT;
   static constexpr int VK = 16 / sizeof(K);
   // staged keys: A and B windows back to back, each 16-byte aligned
   static constexpr uint32_t kKeyBytes = ((Tm + 3 * VK) * sizeof(K) + 15) / 16 * 16;
-  static constexpr uint32_t kValBytes = PAIRS ? ((Tm + 12) * 4 + 15) / 16 * 16 : 0;
-  static constexpr uint32_t kStageBytes = kKeyBytes + kValBytes;
-  static constexpr uint32_t kPlaneBytes = Frag<K, PAIRS, E>::W * Geo<E, NT>::kPlane * 4;
+  static constexpr uint32_t kStageBytes = kKeyBytes;
+  static constexpr uint32_t kPlaneBytes =
+      Frag<K, PAIRS, E, /*VALS=*/false>::W * Geo<E, NT>::kPlane * 4;
   // the transposes reuse the staging area once it has been read
   static constexpr uint32_t kBody = kStageBytes > kPlaneBytes ? kStageBytes : kPlaneBytes;
   static constexpr uint32_t kTotal = 16 + kBody;  // + mbarrier
@@ -171,9 +175,9 @@ __device__ __forceinline__ T read_seq(const T* sa, const T* sb, uint32_t k, uint
 }
 
 // The two windows of one output tile -- the piece p of a pair whose A-window
-// starts at split i0 and ends at split i1 -- and where they are staged in a
-// tile's shared memory, with the tile's output start and count.  For sorted
-// runs the splits grow with the diagonal and the clamp below changes
+// starts at split i0 and ends at split i1 -- and where their keys are staged
+// in the tile's shared memory, with the tile's output start and count.  For
+// sorted runs the splits grow with the diagonal and the clamp below changes
 // nothing.  Runs that are not sorted (a broken precondition of
 // bcf_merge_runs) can make neighbouring searches disagree; clamping i1 into
 // the windows i0 allows keeps every staged window inside its run and within
@@ -183,7 +187,7 @@ struct TileWindows {
   uint64_t ga0, ga1, gb0, gb1;  // absolute source index ranges of the A and B windows
   uint64_t out0;                // first index of the Tm-aligned output tile
   uint32_t na, nb, front, cnt;  // window lengths; real output slots [front, front + cnt)
-  uint32_t offA, lenA, offB, offvA, offvB;
+  uint32_t offA, lenA, offB;    // staged layout: A at offA, B at lenA + offB (elements)
 };
 template <typename K>
 __device__ __forceinline__ TileWindows tile_windows(const Piece& p, uint64_t i0, uint64_t i1) {
@@ -207,88 +211,61 @@ __device__ __forceinline__ TileWindows tile_windows(const Piece& p, uint64_t i0,
   w.offA = static_cast<uint32_t>(w.ga0 & (VK - 1));
   w.lenA = static_cast<uint32_t>((w.offA + w.na + VK - 1) & ~(VK - 1));  // 16B multiple
   w.offB = static_cast<uint32_t>(w.gb0 & (VK - 1));
-  w.offvA = static_cast<uint32_t>(w.ga0 & 3);
-  w.offvB = static_cast<uint32_t>(w.gb0 & 3);
   return w;
 }
 
-// Staged layout in a tile's shared memory `body`: A keys, B keys, then (with
-// payloads) A values and B values, each 16-byte aligned.
-template <typename K, bool PAIRS, int E, int NT>
-struct StagedTile {
-  K* smA;
-  K* smB;
-  uint32_t* svA;
-  uint32_t* svB;
-  __device__ __forceinline__ StagedTile(const TileWindows& w, unsigned char* body) {
-    smA = reinterpret_cast<K*>(body);
-    smB = smA + w.lenA;
-    svA = reinterpret_cast<uint32_t*>(body + MergeSmem<K, PAIRS, E, NT>::kKeyBytes);
-    svB = svA + ((w.offvA + w.na + 3) & ~3u);
-  }
-};
-
-// Thread 0: announce the tile's byte count on `bar`, then issue its bulk copies.
-template <typename K, bool PAIRS, int E, int NT>
+// Thread 0: announce the tile's byte count on `bar`, then bulk-copy its two
+// key windows (A at body, B right after A's 16-byte-rounded span).
+template <typename K>
 __device__ __forceinline__ void stage_issue(const MergeArgs& a, const TileWindows& w,
                                             unsigned char* body, uint64_t* bar) {
-  const StagedTile<K, PAIRS, E, NT> t(w, body);
+  K* smA = reinterpret_cast<K*>(body);
   const K* kin = static_cast<const K*>(a.kin);
   const uint64_t n = a.n;
   // the total byte count is announced before any copy can complete
-  uint32_t total = body_bytes<K>(w.ga0, w.ga1, n) + body_bytes<K>(w.gb0, w.gb1, n);
-  if constexpr (PAIRS)
-    total += body_bytes<uint32_t>(w.ga0, w.ga1, n) + body_bytes<uint32_t>(w.gb0, w.gb1, n);
-  mbar_arrive_expect_tx(bar, total);
-  stage_bulk(t.smA, kin, w.ga0, w.ga1, n, bar);
-  stage_bulk(t.smB, kin, w.gb0, w.gb1, n, bar);
-  if constexpr (PAIRS) {
-    stage_bulk(t.svA, a.vin, w.ga0, w.ga1, n, bar);
-    stage_bulk(t.svB, a.vin, w.gb0, w.gb1, n, bar);
-  }
+  mbar_arrive_expect_tx(bar, body_bytes<K>(w.ga0, w.ga1, n) + body_bytes<K>(w.gb0, w.gb1, n));
+  stage_bulk(smA, kin, w.ga0, w.ga1, n, bar);
+  stage_bulk(smA + w.lenA, kin, w.gb0, w.gb1, n, bar);
 }
 
-// Warp 1 (lane = threadIdx.x - 32): the windows' ragged tails at the array's
-// end.  Lanes 0-7: A keys, 8-15: B keys, 16-23: A values, 24-31: B values,
-// one store instruction per window.
-template <typename K, bool PAIRS, int E, int NT>
+// Warp 1 (lane = threadIdx.x - 32): the key windows' ragged tails at the
+// array's end.  Lanes 0-7: A, 8-15: B, one store instruction per window.
+template <typename K>
 __device__ __forceinline__ void stage_tails(const MergeArgs& a, const TileWindows& w,
                                             unsigned char* body, uint32_t lane) {
-  const StagedTile<K, PAIRS, E, NT> t(w, body);
+  K* smA = reinterpret_cast<K*>(body);
   const K* kin = static_cast<const K*>(a.kin);
-  stage_tail(t.smA, kin, w.ga0, w.ga1, a.n, lane, 0);
-  stage_tail(t.smB, kin, w.gb0, w.gb1, a.n, lane, 8);
-  if constexpr (PAIRS) {
-    stage_tail(t.svA, a.vin, w.ga0, w.ga1, a.n, lane, 16);
-    stage_tail(t.svB, a.vin, w.gb0, w.gb1, a.n, lane, 24);
-  }
+  stage_tail(smA, kin, w.ga0, w.ga1, a.n, lane, 0);
+  stage_tail(smA + w.lenA, kin, w.gb0, w.gb1, a.n, lane, 8);
 }
 
-// The merge of a staged tile (its windows landed in `body`, visible to every
-// thread): the bitonic sequence read into registers, the network (whose
-// transposes reuse `body`), the samples and the stores.  SAMPLES: 0 writes
-// none, 1 writes regular-pass samples when a.samples_out is set, 2 writes
-// samples at array positions that are multiples of kRunSampleStride
-// (irregular passes with a successor).
+// The merge of a staged tile (its key windows landed in `body`, visible to
+// every thread): the bitonic sequence of (key, rank) read into registers, the
+// network (whose transposes reuse `body`), the samples and the key stores,
+// then -- with payloads -- each output's payload read by its rank and stored.
+//   sequence slot k = e*NT + tid (STR layout):
+//   [0, front)            -inf pads          (rank k)
+//   [front, front+na)     A[k - front]       (rank k)
+//   [front+na, Tm-nb)     +inf pads          (rank Tm + k)
+//   [Tm-nb, Tm)           B[Tm-1-k]          (rank front + na + (Tm-1-k))
+// A rank in [front, endA) is then A's element rank - front, a rank in
+// [endA, endA + nb) B's element rank - endA; the pads' ranks lie outside both
+// and pads never reach a real output slot.  SAMPLES: 0 writes none, 1 writes
+// regular-pass samples when a.samples_out is set, 2 writes samples at array
+// positions that are multiples of kRunSampleStride (irregular passes with a
+// successor).
 template <typename K, bool PAIRS, int E, int NT, bool MAP, int SAMPLES>
 __device__ __forceinline__ void merge_staged(const MergeArgs& a, const TileWindows& w,
                                              unsigned char* body) {
   constexpr int Tm = E * NT;
   const uint32_t tid = threadIdx.x;
-  const StagedTile<K, PAIRS, E, NT> t(w, body);
   const uint32_t na = w.na, nb = w.nb, front = w.front, cnt = w.cnt;
   const uint64_t out0 = w.out0;
-
-  // Read the bitonic sequence into STR registers: k = e*NT + tid.
-  //   [0, front)            -inf pads          (rank k)
-  //   [front, front+na)     A[k - front]       (rank k)
-  //   [front+na, Tm-nb)     +inf pads          (rank Tm + k)
-  //   [Tm-nb, Tm)           B[Tm-1-k]          (rank front + na + (Tm-1-k))
-  Frag<K, PAIRS, E> f;
+  Frag<K, PAIRS, E, /*VALS=*/false> f;
   const uint32_t endA = front + na, begB = Tm - nb;
   const uint32_t warp0 = tid & ~31u;
-  const K* sa = t.smA + w.offA;
-  const K* sb = t.smB + w.offB;
+  const K* sa = reinterpret_cast<const K*>(body) + w.offA;
+  const K* sb = reinterpret_cast<const K*>(body) + w.lenA + w.offB;
   const int mode_in = MAP ? a.mode_in : 0;
 #pragma unroll
   for (int e = 0; e < E; ++e) {
@@ -299,12 +276,7 @@ __device__ __forceinline__ void merge_staged(const MergeArgs& a, const TileWindo
                         KeyLimits<K>::kMax, real);
     if constexpr (MAP) key = real ? map_key(key, mode_in) : key;
     f.k[e] = key;
-    if constexpr (PAIRS) {
-      bool rv;
-      f.v[e] = read_seq<uint32_t>(t.svA + w.offvA, t.svB + w.offvB, k, row0, front, endA, begB,
-                                  Tm - 1, 0u, 0u, rv);
-      f.ix[e] = k >= begB ? endA + (Tm - 1 - k) : (k < endA ? k : Tm + k);
-    }
+    if constexpr (PAIRS) f.ix[e] = k >= begB ? endA + (Tm - 1 - k) : (k < endA ? k : Tm + k);
   }
 
   f.one = g_unit_multiplier;
@@ -323,37 +295,53 @@ __device__ __forceinline__ void merge_staged(const MergeArgs& a, const TileWindo
 
   // outputs: BLK layout, thread holds tile slots tid*E .. tid*E+E-1
   K* kout = static_cast<K*>(a.kout) + out0;
-  uint32_t* vout = PAIRS ? a.vout + out0 : nullptr;
   const uint32_t s0 = tid * E;
+  const bool full = s0 >= front && s0 + E <= front + cnt;
   const int mode_out = MAP ? a.mode_out : 0;
-  if (s0 >= front && s0 + E <= front + cnt) {
+  if (full) {
     // out0 and s0 are multiples of 32 bytes: the base pointers decide alignment
     if constexpr (MAP) {
 #pragma unroll
       for (int e = 0; e < E; ++e) f.k[e] = unmap_key(f.k[e], mode_out);  // last use of f.k
     }
     store_run<E>(kout + s0, f.k, is_aligned32(a.kout));
-    if constexpr (PAIRS) store_run<E>(vout + s0, f.v, is_aligned32(a.vout));
   } else {
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const uint32_t s = s0 + e;
-      if (s >= front && s < front + cnt) {
-        kout[s] = MAP ? unmap_key(f.k[e], mode_out) : f.k[e];
-        if constexpr (PAIRS) vout[s] = f.v[e];
+      if (s >= front && s < front + cnt) kout[s] = MAP ? unmap_key(f.k[e], mode_out) : f.k[e];
+    }
+  }
+  if constexpr (PAIRS) {
+    // payloads by rank, once the keys are stored (their registers are free)
+    uint32_t* vout = a.vout + out0;
+    uint32_t vg[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const uint32_t s = s0 + e, r = f.ix[e];
+      const uint64_t src = r < endA ? w.ga0 + (r - front) : w.gb0 + (r - endA);
+      vg[e] = (s >= front && s < front + cnt) ? __ldg(a.vin + src) : 0u;
+    }
+    if (full) {
+      store_run<E>(vout + s0, vg, is_aligned32(a.vout));
+    } else {
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const uint32_t s = s0 + e;
+        if (s >= front && s < front + cnt) vout[s] = vg[e];
       }
     }
   }
 }
 
-// One output tile whose windows were derived beforehand (the segmented
-// sort's persistent merge: thread 0 derives them once for the CTA), staged and
-// merged by the calling CTA: thread 0 stages the windows with bulk copies
-// completing on `bar` (initialised by the caller) and waits for phase parity
-// `phase`; warp 1 stages the ragged tails.
+// One output tile, staged and merged by the calling CTA: thread 0 stages the
+// key windows with bulk copies completing on `bar` (initialised by the
+// caller) and waits for phase parity `phase`; warp 1 stages the ragged tails.
 // Returns false when the wait for the bulk copies ran out (the error word is
 // set; the caller's CTA stops).  Thread 0 calls on_issued() once its bulk
-// copies are issued, before it waits for them.
+// copies are issued, before it waits for them.  The windows come derived
+// (the segmented sort's persistent merge: thread 0 derives them once for the
+// CTA) ...
 template <typename K, bool PAIRS, int E, int NT, bool MAP, int SAMPLES, typename OnIssued>
 __device__ __forceinline__ bool merge_windows(const MergeArgs& a, const TileWindows& w,
                                               uint64_t* bar, uint32_t phase,
@@ -361,14 +349,14 @@ __device__ __forceinline__ bool merge_windows(const MergeArgs& a, const TileWind
                                               OnIssued&& on_issued) {
   const uint32_t tid = threadIdx.x;
   if (tid == 0) {
-    stage_issue<K, PAIRS, E, NT>(a, w, body, bar);
+    stage_issue<K>(a, w, body, bar);
     on_issued();
     // one thread waits (bounded); the barrier below releases the others
     bool ok = mbar_wait_bounded(bar, phase, a.err, kErrTmaTimeout, a.wait_ns);
     if (!ok) mbar_wait_bounded(bar, phase, nullptr, 0, a.wait_ns);  // let copies in flight land
     *s_ok = ok ? 1 : 0;
   } else if (tid >= 32 && tid < 64) {
-    stage_tails<K, PAIRS, E, NT>(a, w, body, tid - 32);
+    stage_tails<K>(a, w, body, tid - 32);
   }
   __syncthreads();
   if (!*s_ok) return false;
@@ -376,155 +364,15 @@ __device__ __forceinline__ bool merge_windows(const MergeArgs& a, const TileWind
   return true;
 }
 
-// One output tile: the piece p of a pair, whose A-window starts at split i0
-// and ends at split i1, merged into its Tm-aligned output tile.  Thread 0
-// stages the windows with bulk copies completing on `bar` (initialised by
-// the caller) and waits for phase parity `phase`.  SAMPLES: 0 writes none,
-// 1 writes regular-pass samples when a.samples_out is set, 2 writes samples
-// at array positions that are multiples of kRunSampleStride (irregular
-// passes with a successor).  Returns false when the wait for the bulk copies
-// ran out (the error word is set; the caller's CTA stops).  Thread 0 calls
-// on_issued() once its bulk copies are issued, before it waits for them.
-// (The same steps as merge_windows, with the geometry derived by every thread
-// from the piece: kept separate because the one-shot kernels' pieces come
-// from the block index, and the 64-bit pair kernels took 96 instead of 72
-// registers when they shared merge_staged's code.)
+// ... or every thread derives them from the piece p of a pair whose A-window
+// starts at split i0 and ends at split i1 (the one-shot kernels, whose pieces
+// come from the block index).
 template <typename K, bool PAIRS, int E, int NT, bool MAP, int SAMPLES, typename OnIssued>
 __device__ __forceinline__ bool merge_tile(const MergeArgs& a, const Piece& p, uint64_t i0,
                                            uint64_t i1, uint64_t* bar, uint32_t phase,
                                            unsigned char* body, int* s_ok, OnIssued&& on_issued) {
-  using S = MergeSmem<K, PAIRS, E, NT>;
-  constexpr int Tm = S::Tm;
-  constexpr uint64_t VK = S::VK;
-  const uint32_t tid = threadIdx.x;
-  // For sorted runs the splits grow with the diagonal and nothing below
-  // changes i1.  Runs that are not sorted (a broken precondition of
-  // bcf_merge_runs) can make neighbouring searches disagree; clamping i1 into
-  // the windows i0 allows keeps every staged window inside its run and within
-  // the tile's shared memory, so such input gives an undefined order but
-  // never an out-of-bounds access.
-  {
-    const uint64_t lo1 = p.d1 > p.nb_tot && p.d1 - p.nb_tot > i0 ? p.d1 - p.nb_tot : i0;
-    const uint64_t hi1 = i0 + (p.d1 - p.d0) < p.na_tot ? i0 + (p.d1 - p.d0) : p.na_tot;
-    i1 = i1 < lo1 ? lo1 : (i1 > hi1 ? hi1 : i1);
-  }
-  const uint64_t j0 = p.d0 - i0, j1 = p.d1 - i1;
-  const uint32_t na = static_cast<uint32_t>(i1 - i0), nb = static_cast<uint32_t>(j1 - j0);
-  const uint32_t front = p.front;
-
-  // absolute source index ranges of the two windows
-  const uint64_t ga0 = p.src + i0, ga1 = p.src + i1;
-  const uint64_t gb0 = p.src + p.na_tot + j0, gb1 = p.src + p.na_tot + j1;
-  const uint32_t offA = static_cast<uint32_t>(ga0 & (VK - 1));
-  const uint32_t lenA = static_cast<uint32_t>((offA + na + VK - 1) & ~(VK - 1));  // 16B multiple
-  const uint32_t offB = static_cast<uint32_t>(gb0 & (VK - 1));
-  K* smA = reinterpret_cast<K*>(body);
-  K* smB = smA + lenA;
-  uint32_t* svA = reinterpret_cast<uint32_t*>(body + S::kKeyBytes);
-  const uint32_t offvA = static_cast<uint32_t>(ga0 & 3), offvB = static_cast<uint32_t>(gb0 & 3);
-  uint32_t* svB = svA + ((offvA + na + 3) & ~3u);
-
-  const K* kin = static_cast<const K*>(a.kin);
-  if (tid == 0) {
-    // the total byte count is announced before any copy can complete
-    const uint64_t n = a.n;
-    uint32_t total = body_bytes<K>(ga0, ga1, n) + body_bytes<K>(gb0, gb1, n);
-    if constexpr (PAIRS)
-      total += body_bytes<uint32_t>(ga0, ga1, n) + body_bytes<uint32_t>(gb0, gb1, n);
-    mbar_arrive_expect_tx(bar, total);
-    stage_bulk(smA, kin, ga0, ga1, n, bar);
-    stage_bulk(smB, kin, gb0, gb1, n, bar);
-    if constexpr (PAIRS) {
-      stage_bulk(svA, a.vin, ga0, ga1, n, bar);
-      stage_bulk(svB, a.vin, gb0, gb1, n, bar);
-    }
-    on_issued();
-    // one thread waits (bounded); the barrier below releases the others
-    bool ok = mbar_wait_bounded(bar, phase, a.err, kErrTmaTimeout, a.wait_ns);
-    if (!ok) mbar_wait_bounded(bar, phase, nullptr, 0, a.wait_ns);  // let copies in flight land
-    *s_ok = ok ? 1 : 0;
-  } else if (tid >= 32 && tid < 64) {
-    const uint32_t lane = tid - 32;
-    // lanes 0-7: A keys, 8-15: B keys, 16-23: A values, 24-31: B values, one
-    // store instruction per window
-    stage_tail(smA, kin, ga0, ga1, a.n, lane, 0);
-    stage_tail(smB, kin, gb0, gb1, a.n, lane, 8);
-    if constexpr (PAIRS) {
-      stage_tail(svA, a.vin, ga0, ga1, a.n, lane, 16);
-      stage_tail(svB, a.vin, gb0, gb1, a.n, lane, 24);
-    }
-  }
-  __syncthreads();
-  if (!*s_ok) return false;
-
-  // Read the bitonic sequence into STR registers: k = e*NT + tid.
-  //   [0, front)            -inf pads          (rank k)
-  //   [front, front+na)     A[k - front]       (rank k)
-  //   [front+na, Tm-nb)     +inf pads          (rank Tm + k)
-  //   [Tm-nb, Tm)           B[Tm-1-k]          (rank front + na + (Tm-1-k))
-  Frag<K, PAIRS, E> f;
-  const uint32_t endA = front + na, begB = Tm - nb;
-  const uint32_t warp0 = tid & ~31u;
-  const K* sa = smA + offA;
-  const K* sb = smB + offB;
-  const int mode_in = MAP ? a.mode_in : 0;
-#pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const uint32_t k = e * NT + tid;
-    const uint32_t row0 = e * NT + warp0;
-    bool real;
-    K key = read_seq<K>(sa, sb, k, row0, front, endA, begB, Tm - 1, KeyLimits<K>::kMin,
-                        KeyLimits<K>::kMax, real);
-    if constexpr (MAP) key = real ? map_key(key, mode_in) : key;
-    f.k[e] = key;
-    if constexpr (PAIRS) {
-      bool rv;
-      f.v[e] = read_seq<uint32_t>(svA + offvA, svB + offvB, k, row0, front, endA, begB, Tm - 1,
-                                  0u, 0u, rv);
-      f.ix[e] = k >= begB ? endA + (Tm - 1 - k) : (k < endA ? k : Tm + k);
-    }
-  }
-
-  f.one = g_unit_multiplier;
-  bitonic_merge_str<NT, CeForms<K, PAIRS>::kMergeBlk, CeForms<K, PAIRS>::kMergeOth>(
-      f, reinterpret_cast<uint32_t*>(body));
-  // samples of the output for the next pass's merge-path search: the keys at
-  // array positions that are multiples of S, still in mapped order (a pass
-  // with a successor writes no unmapped keys)
-  if constexpr (SAMPLES == 1) {
-    if (a.samples_out && ((p.out0 + tid * E) % kSampleStride) == 0 && tid * E < p.d1 - p.d0)
-      static_cast<K*>(a.samples_out)[(p.out0 + tid * E) / kSampleStride] = f.k[0];
-  } else if constexpr (SAMPLES == 2) {
-    if (((p.out0 + tid * E) % kRunSampleStride) == 0 && tid * E >= front &&
-        tid * E < front + (p.d1 - p.d0))
-      static_cast<K*>(a.samples_out)[(p.out0 + tid * E) / kRunSampleStride] = f.k[0];
-  }
-
-  // outputs: BLK layout, thread holds tile slots tid*E .. tid*E+E-1
-  K* kout = static_cast<K*>(a.kout) + p.out0;
-  uint32_t* vout = PAIRS ? a.vout + p.out0 : nullptr;
-  const uint32_t s0 = tid * E;
-  const uint32_t cnt = static_cast<uint32_t>(p.d1 - p.d0);
-  const int mode_out = MAP ? a.mode_out : 0;
-  if (s0 >= front && s0 + E <= front + cnt) {
-    // out0 and s0 are multiples of 32 bytes: the base pointers decide alignment
-    if constexpr (MAP) {
-#pragma unroll
-      for (int e = 0; e < E; ++e) f.k[e] = unmap_key(f.k[e], mode_out);  // last use of f.k
-    }
-    store_run<E>(kout + s0, f.k, is_aligned32(a.kout));
-    if constexpr (PAIRS) store_run<E>(vout + s0, f.v, is_aligned32(a.vout));
-  } else {
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-      const uint32_t s = s0 + e;
-      if (s >= front && s < front + cnt) {
-        kout[s] = MAP ? unmap_key(f.k[e], mode_out) : f.k[e];
-        if constexpr (PAIRS) vout[s] = f.v[e];
-      }
-    }
-  }
-  return true;
+  return merge_windows<K, PAIRS, E, NT, MAP, SAMPLES>(a, tile_windows<K>(p, i0, i1), bar, phase,
+                                                      body, s_ok, on_issued);
 }
 
 }  // namespace bcf

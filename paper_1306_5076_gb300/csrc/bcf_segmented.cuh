@@ -466,7 +466,7 @@ __device__ __forceinline__ void merge_piece_item(const SegArgs& a, const SegGeo&
     }
   }
   f.one = g_unit_multiplier;
-  bitonic_merge_str<NT, CeForms<K, PAIRS>::kMergeBlk, CeForms<K, PAIRS>::kMergeOth>(f, sm);
+  bitonic_merge_str<NT, CeForms<K, PAIRS>::kPieceBlk, CeForms<K, PAIRS>::kPieceOth>(f, sm);
   K* dst = static_cast<K*>(dst_out ? a.kout : a.kbuf) + gt * T;
   uint32_t* vdst = PAIRS ? (dst_out ? a.vout : a.vbuf) + gt * T : nullptr;
   const bool last = pass == g.passes;
