@@ -23,7 +23,9 @@
 // The kernel is instantiated per key type in bcf_block_sort_*.cu (separate
 // translation units, compiled in parallel); bcf_block_sort.cu dispatches.
 // Pairs carry a tie-break index (input position in the tile) so that the
-// result is the stable order.
+// result is the stable order; their payloads do not travel through the
+// network: they wait in a padded shared-memory plane, loaded with the keys,
+// and each output's payload is read from it by that position.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -43,7 +45,12 @@ __global__ void __launch_bounds__(NT) block_sort_kernel(const BlockSortArgs a) {
   using VV = typename ValVec<V>::T;
   extern __shared__ __align__(16) uint32_t sm[];
 
-  Frag<K, PAIRS, E> f;
+  // with payloads the network sorts (key, position) only: the tile's payloads
+  // wait in their own padded plane behind the network's planes, and each
+  // output's payload is read from there by its position once the tile is
+  // sorted (the network's barriers order the plane's writes before the reads)
+  Frag<K, PAIRS, E, /*VALS=*/false> f;
+  uint32_t* sv = sm + Frag<K, PAIRS, E, false>::W * padded_words(T);
   // keys-only 32-bit tiles move the BLK stages' maxima to the FMA pipe (the
   // network is bound by the ALU pipe: measured 1.87 vs 1.98 ms at 2^28 keys;
   // the multiplier is read before the tile's loads, which measured faster than
@@ -71,8 +78,8 @@ __global__ void __launch_bounds__(NT) block_sort_kernel(const BlockSortArgs a) {
         const uint32_t* vp = reinterpret_cast<const uint32_t*>(&vv);
 #pragma unroll
         for (int c = 0; c < V; ++c) {
-          f.v[q * V + c] = vp[c];
           f.ix[q * V + c] = pos + c;
+          sv[pos + c + ((pos + c) >> 5)] = vp[c];
         }
       }
     }
@@ -87,8 +94,8 @@ __global__ void __launch_bounds__(NT) block_sort_kernel(const BlockSortArgs a) {
       if (real) x = MAP ? map_key(kin[pos], mode_in) : kin[pos];
       f.k[e] = x;
       if constexpr (PAIRS) {
-        f.v[e] = real ? vin[pos] : 0u;
         f.ix[e] = pos;
+        sv[pos + (pos >> 5)] = real ? vin[pos] : 0u;
       }
     }
   }
@@ -102,6 +109,12 @@ __global__ void __launch_bounds__(NT) block_sort_kernel(const BlockSortArgs a) {
   static_assert(kSampleStride % E == 0 && T % kSampleStride == 0, "sample stride");
   if (a.samples && (p0 % kSampleStride) == 0 && p0 < cnt)
     static_cast<K*>(a.samples)[(base + p0) / kSampleStride] = f.k[0];
+  // payloads by tile position from the payload plane
+  uint32_t vg[PAIRS ? E : 1];
+  if constexpr (PAIRS) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) vg[e] = sv[f.ix[e] + (f.ix[e] >> 5)];
+  }
   if (p0 + E <= cnt) {
     // base and p0 are multiples of 32 bytes: the base pointers decide alignment
     if constexpr (MAP) {
@@ -109,13 +122,13 @@ __global__ void __launch_bounds__(NT) block_sort_kernel(const BlockSortArgs a) {
       for (int e = 0; e < E; ++e) f.k[e] = unmap_key(f.k[e], mode_out);  // last use of f.k
     }
     store_run<E>(kout + p0, f.k, is_aligned32(a.kout));
-    if constexpr (PAIRS) store_run<E>(vout + p0, f.v, is_aligned32(a.vout));
+    if constexpr (PAIRS) store_run<E>(vout + p0, vg, is_aligned32(a.vout));
   } else {
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       if (p0 + e < cnt) {
         kout[p0 + e] = MAP ? unmap_key(f.k[e], mode_out) : f.k[e];
-        if constexpr (PAIRS) vout[p0 + e] = f.v[e];
+        if constexpr (PAIRS) vout[p0 + e] = vg[e];
       }
     }
   }
@@ -126,7 +139,8 @@ __global__ void __launch_bounds__(NT) block_sort_kernel(const BlockSortArgs a) {
 template <typename K, bool PAIRS, int E, int NT>
 static cudaError_t launch_bs(const BlockSortArgs& a, cudaStream_t s) {
   constexpr int T = E * NT;
-  constexpr int W = Frag<K, PAIRS, E>::W;
+  // the network's planes, plus the payload plane with payloads
+  constexpr int W = Frag<K, PAIRS, E, /*VALS=*/false>::W + (PAIRS ? 1 : 0);
   const size_t need = static_cast<size_t>(W) * padded_words(T) * sizeof(uint32_t);
   const size_t smem = need > smem_floor_bytes() ? need : smem_floor_bytes();
   const uint64_t tiles = (a.n + T - 1) / T;

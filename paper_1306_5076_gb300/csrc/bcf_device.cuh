@@ -378,7 +378,8 @@ __device__ __forceinline__ void ce(Frag<K, PAIRS, E, VALS>& f, int a, int b, boo
 // (Oth).  Block: the block sort; Merge: the merge passes, whose networks carry
 // (key, rank) only (the payloads are gathered by rank afterwards); Piece: the
 // segmented worker's merge pieces, which carry the payloads through the
-// network.  Measured on GB300 (sweeps over the word choices).
+// network.  The block sorts with payloads carry (key, position) only as well.
+// Measured on GB300 (sweeps over the word choices).
 template <typename K, bool PAIRS> struct CeForms;
 template <> struct CeForms<uint32_t, false> {
   static constexpr int kBlockBlk = kFmaKeys, kBlockOth = 0;
@@ -396,7 +397,7 @@ template <> struct CeForms<uint64_t, false> {
   static constexpr int kPieceBlk = kMergeBlk, kPieceOth = kMergeOth;
 };
 template <> struct CeForms<uint64_t, true> {
-  static constexpr int kBlockBlk = kFmaWord(1) | kFmaWord(3), kBlockOth = kFmaWord(1) | kFmaWord(3);
+  static constexpr int kBlockBlk = 0, kBlockOth = 0;
   static constexpr int kMergeBlk = 0, kMergeOth = 0;
   static constexpr int kPieceBlk = 0, kPieceOth = 0;
 };
@@ -422,8 +423,8 @@ struct OemNetwork {
 
 // The "BATCHERS-ODD-EVEN-MERGESORT(R)" register network of Algorithms 1 and
 // 2: sorts one thread's E registers, direction chosen per thread.
-template <int FMA = 0, typename K, bool PAIRS, int E>
-__device__ __forceinline__ void thread_sort(Frag<K, PAIRS, E>& f, bool desc) {
+template <int FMA = 0, typename K, bool PAIRS, int E, bool VALS>
+__device__ __forceinline__ void thread_sort(Frag<K, PAIRS, E, VALS>& f, bool desc) {
   constexpr OemNetwork<E> net{};
 #pragma unroll
   for (int c = 0; c < net.n; ++c) ce(f, net.a[c], net.b[c], desc, FMA);
@@ -564,25 +565,23 @@ __device__ __forceinline__ void bitonic_merge_str(Frag<K, PAIRS, E, VALS>& f, ui
 // l and l ^ m of one warp: this lane's register a meets the partner lane's
 // register b; the lower lane keeps the smaller element, the upper the larger.
 // (key, tie-break index) order for pairs; the payload follows.
-template <typename K, bool PAIRS, int E>
+template <typename K, bool PAIRS, int E, bool VALS>
 struct LaneVal {
   K k;
   uint32_t ix, v;
 };
-template <typename K, bool PAIRS, int E>
-__device__ __forceinline__ LaneVal<K, PAIRS, E> lane_fetch(const Frag<K, PAIRS, E>& f, int b,
-                                                           uint32_t m) {
-  LaneVal<K, PAIRS, E> y;
+template <typename K, bool PAIRS, int E, bool VALS>
+__device__ __forceinline__ LaneVal<K, PAIRS, E, VALS> lane_fetch(const Frag<K, PAIRS, E, VALS>& f,
+                                                                 int b, uint32_t m) {
+  LaneVal<K, PAIRS, E, VALS> y;
   y.k = __shfl_xor_sync(0xFFFFFFFFu, f.k[b], m);
-  if constexpr (PAIRS) {
-    y.ix = __shfl_xor_sync(0xFFFFFFFFu, f.ix[b], m);
-    y.v = __shfl_xor_sync(0xFFFFFFFFu, f.v[b], m);
-  }
+  if constexpr (PAIRS) y.ix = __shfl_xor_sync(0xFFFFFFFFu, f.ix[b], m);
+  if constexpr (PAIRS && VALS) y.v = __shfl_xor_sync(0xFFFFFFFFu, f.v[b], m);
   return y;
 }
-template <typename K, bool PAIRS, int E>
-__device__ __forceinline__ void lane_keep(Frag<K, PAIRS, E>& f, int a,
-                                          const LaneVal<K, PAIRS, E>& y, bool upper) {
+template <typename K, bool PAIRS, int E, bool VALS>
+__device__ __forceinline__ void lane_keep(Frag<K, PAIRS, E, VALS>& f, int a,
+                                          const LaneVal<K, PAIRS, E, VALS>& y, bool upper) {
   if constexpr (!PAIRS) {
     const K x = f.k[a];
     f.k[a] = upper ? (x > y.k ? x : y.k) : (x < y.k ? x : y.k);
@@ -591,7 +590,7 @@ __device__ __forceinline__ void lane_keep(Frag<K, PAIRS, E>& f, int a,
     const bool take = upper ? y_after : !y_after;
     f.k[a] = take ? y.k : f.k[a];
     f.ix[a] = take ? y.ix : f.ix[a];
-    f.v[a] = take ? y.v : f.v[a];
+    if constexpr (VALS) f.v[a] = take ? y.v : f.v[a];
   }
 }
 
@@ -613,8 +612,8 @@ __host__ __device__ constexpr int shuffle_levels() {
 // lane l meets register E-1-e of lane l ^ (2^(J-r) - 1); the lower lane (k bit
 // J-1 clear) keeps the minimum.  Then half-cleaners on lane bits, then the
 // register stages r-1 .. 0.
-template <int J, int NT, int FMA_BLK, int FMA_OTH, typename K, bool PAIRS, int E>
-__device__ __forceinline__ void sort_level_shuffle(Frag<K, PAIRS, E>& f) {
+template <int J, int NT, int FMA_BLK, int FMA_OTH, typename K, bool PAIRS, int E, bool VALS>
+__device__ __forceinline__ void sort_level_shuffle(Frag<K, PAIRS, E, VALS>& f) {
   constexpr int r = ilog2(E);
   static_assert(J > r && J - r <= 5, "lane stages only");
   const uint32_t lane = threadIdx.x & 31u;
@@ -623,8 +622,8 @@ __device__ __forceinline__ void sort_level_shuffle(Frag<K, PAIRS, E>& f) {
     const bool upper = ((lane >> (J - 1 - r)) & 1u) != 0;
 #pragma unroll
     for (int e = 0; e < E / 2; ++e) {
-      const LaneVal<K, PAIRS, E> y1 = lane_fetch(f, E - 1 - e, m);  // meets my e
-      const LaneVal<K, PAIRS, E> y2 = lane_fetch(f, e, m);          // meets my E-1-e
+      const LaneVal<K, PAIRS, E, VALS> y1 = lane_fetch(f, E - 1 - e, m);  // meets my e
+      const LaneVal<K, PAIRS, E, VALS> y2 = lane_fetch(f, e, m);          // meets my E-1-e
       lane_keep(f, e, y1, upper);
       lane_keep(f, E - 1 - e, y2, upper);
     }
@@ -635,7 +634,7 @@ __device__ __forceinline__ void sort_level_shuffle(Frag<K, PAIRS, E>& f) {
     const bool upper = (lane & m) != 0;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-      const LaneVal<K, PAIRS, E> y = lane_fetch(f, e, m);
+      const LaneVal<K, PAIRS, E, VALS> y = lane_fetch(f, e, m);
       lane_keep(f, e, y, upper);
     }
   }
@@ -647,8 +646,8 @@ __device__ __forceinline__ void sort_level_shuffle(Frag<K, PAIRS, E>& f) {
 // leaves in BLK layout.  Low levels use lane shuffles (above).  A level whose
 // top bit lies in the MID window [r, 2r) needs two layout changes (BLK -> MID
 // -> BLK); only a level whose top bit lies above it goes through STR (three).
-template <int J, int NT, int FMA_BLK, int FMA_OTH, typename K, bool PAIRS, int E>
-__device__ __forceinline__ void sort_level(Frag<K, PAIRS, E>& f, uint32_t* sm) {
+template <int J, int NT, int FMA_BLK, int FMA_OTH, typename K, bool PAIRS, int E, bool VALS>
+__device__ __forceinline__ void sort_level(Frag<K, PAIRS, E, VALS>& f, uint32_t* sm) {
   using G = Geo<E, NT>;
   constexpr int r = G::r, t = G::t, top = J - 1;
   if constexpr (J - r <= shuffle_levels<K, PAIRS>()) {
@@ -672,17 +671,17 @@ __device__ __forceinline__ void sort_level(Frag<K, PAIRS, E>& f, uint32_t* sm) {
   stages<kBLK, r - 1, 0, NT, FMA_BLK>(f);
 }
 
-template <int J, int NT, int FMA_BLK, int FMA_OTH, typename K, bool PAIRS, int E,
+template <int J, int NT, int FMA_BLK, int FMA_OTH, typename K, bool PAIRS, int E, bool VALS,
           bool DONE = (J > ilog2(E * NT))>
 struct SortLevels {
-  __device__ static __forceinline__ void run(Frag<K, PAIRS, E>& f, uint32_t* sm) {
+  __device__ static __forceinline__ void run(Frag<K, PAIRS, E, VALS>& f, uint32_t* sm) {
     sort_level<J, NT, FMA_BLK, FMA_OTH>(f, sm);
-    SortLevels<J + 1, NT, FMA_BLK, FMA_OTH, K, PAIRS, E>::run(f, sm);
+    SortLevels<J + 1, NT, FMA_BLK, FMA_OTH, K, PAIRS, E, VALS>::run(f, sm);
   }
 };
-template <int J, int NT, int FMA_BLK, int FMA_OTH, typename K, bool PAIRS, int E>
-struct SortLevels<J, NT, FMA_BLK, FMA_OTH, K, PAIRS, E, true> {
-  __device__ static __forceinline__ void run(Frag<K, PAIRS, E>&, uint32_t*) {}
+template <int J, int NT, int FMA_BLK, int FMA_OTH, typename K, bool PAIRS, int E, bool VALS>
+struct SortLevels<J, NT, FMA_BLK, FMA_OTH, K, PAIRS, E, VALS, true> {
+  __device__ static __forceinline__ void run(Frag<K, PAIRS, E, VALS>&, uint32_t*) {}
 };
 
 // Sort of the whole CTA tile: each thread's registers with Batcher's network
@@ -690,10 +689,10 @@ struct SortLevels<J, NT, FMA_BLK, FMA_OTH, K, PAIRS, E, true> {
 // FMA_BLK / FMA_OTH: the compare-exchange forms of the BLK stages / of the
 // per-thread network and the other stages (Frag::one must be set when either
 // is non-zero).
-template <int NT, int FMA_BLK = 0, int FMA_OTH = 0, typename K, bool PAIRS, int E>
-__device__ __forceinline__ void block_sort_tile(Frag<K, PAIRS, E>& f, uint32_t* sm) {
+template <int NT, int FMA_BLK = 0, int FMA_OTH = 0, typename K, bool PAIRS, int E, bool VALS>
+__device__ __forceinline__ void block_sort_tile(Frag<K, PAIRS, E, VALS>& f, uint32_t* sm) {
   thread_sort<FMA_OTH>(f, false);
-  SortLevels<ilog2(E) + 1, NT, FMA_BLK, FMA_OTH, K, PAIRS, E>::run(f, sm);
+  SortLevels<ilog2(E) + 1, NT, FMA_BLK, FMA_OTH, K, PAIRS, E, VALS>::run(f, sm);
 }
 
 }  // namespace bcf

@@ -239,6 +239,53 @@ __device__ __forceinline__ void stage_tails(const MergeArgs& a, const TileWindow
   stage_tail(smA + w.lenA, kin, w.gb0, w.gb1, a.n, lane, 8);
 }
 
+// A tile whose B window (or A window) is empty -- every tile of sorted or
+// reversed stretches and of long runs of equal keys -- is the other window
+// itself: slot s in [front, front + cnt) is its element s - front.  Its keys
+// come from the staged window and its payloads from global memory, both in
+// rows of 32 consecutive slots per warp instruction, with no network at all
+// (in the network's BLK output order a warp's payload loads would sit E
+// words apart, on two L1 banks).  Samples as merge_staged writes them.
+template <typename K, bool PAIRS, int E, int NT, bool MAP, int SAMPLES>
+__device__ __forceinline__ void copy_staged(const MergeArgs& a, const TileWindows& w,
+                                            const unsigned char* body) {
+  const uint32_t tid = threadIdx.x;
+  const uint32_t front = w.front, cnt = w.cnt;
+  const bool from_a = w.nb == 0;
+  const K* st = reinterpret_cast<const K*>(body) + (from_a ? w.offA : w.lenA + w.offB) - front;
+  const int mode_in = MAP ? a.mode_in : 0, mode_out = MAP ? a.mode_out : 0;
+  // samples: the (mapped) key of slot tid * E, as the network's BLK output has it
+  if constexpr (SAMPLES != 0) {
+    const uint32_t p = tid * E;
+    constexpr uint32_t S = SAMPLES == 1 ? kSampleStride : kRunSampleStride;
+    const bool want = SAMPLES == 1 ? (a.samples_out != nullptr && p < cnt)
+                                   : (p >= front && p < front + cnt);
+    if (want && ((w.out0 + p) % S) == 0) {
+      const K x = st[p];
+      static_cast<K*>(a.samples_out)[(w.out0 + p) / S] = MAP ? map_key(x, mode_in) : x;
+    }
+  }
+  K* kout = static_cast<K*>(a.kout) + w.out0 + tid;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const uint32_t s = e * NT + tid;
+    if (s - front < cnt) {
+      const K x = st[s];
+      kout[e * NT] = MAP ? unmap_key(map_key(x, mode_in), mode_out) : x;
+    }
+  }
+  if constexpr (PAIRS) {
+    const uint32_t* src = a.vin + ((from_a ? w.ga0 : w.gb0) - front) + tid;
+    uint32_t* dst = a.vout + w.out0 + tid;
+    uint32_t vg[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) vg[e] = (e * NT + tid - front < cnt) ? __ldg(src + e * NT) : 0u;
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+      if (e * NT + tid - front < cnt) dst[e * NT] = vg[e];
+  }
+}
+
 // The merge of a staged tile (its key windows landed in `body`, visible to
 // every thread): the bitonic sequence of (key, rank) read into registers, the
 // network (whose transposes reuse `body`), the samples and the key stores,
@@ -360,7 +407,10 @@ __device__ __forceinline__ bool merge_windows(const MergeArgs& a, const TileWind
   }
   __syncthreads();
   if (!*s_ok) return false;
-  merge_staged<K, PAIRS, E, NT, MAP, SAMPLES>(a, w, body);
+  if (w.na == 0 || w.nb == 0)
+    copy_staged<K, PAIRS, E, NT, MAP, SAMPLES>(a, w, body);
+  else
+    merge_staged<K, PAIRS, E, NT, MAP, SAMPLES>(a, w, body);
   return true;
 }
 

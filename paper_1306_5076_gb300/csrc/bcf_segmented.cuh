@@ -196,24 +196,24 @@ __device__ __forceinline__ void warp_sort_segment(const SegArgs& a, uint64_t lo,
 // Stores a thread's E consecutive tile slots k0 .. k0+E-1 (BLK layout) of
 // which [front, front + cnt) are real: 32-byte vector stores when all E are
 // real and the buffers are 32-byte aligned (tiles start at multiples of T),
-// else one store per real slot.
-template <int E, typename K, typename F>
-__device__ __forceinline__ void store_slots(K* kdst, uint32_t* vdst, F& f, uint32_t k0,
-                                            uint32_t front, uint32_t cnt, const void* kbase,
+// else one store per real slot.  ks: the keys; vs: the payloads (PAIRS).
+template <int E, bool PAIRS, typename K>
+__device__ __forceinline__ void store_slots(K* kdst, uint32_t* vdst, const K* ks,
+                                            const uint32_t* vs, uint32_t k0, uint32_t front,
+                                            uint32_t cnt, const void* kbase,
                                             const uint32_t* vbase) {
-  constexpr bool PAIRS = F::W > F::KW;
   if (k0 >= front && k0 + E <= front + cnt && is_aligned32(kbase) &&
       (!PAIRS || is_aligned32(vbase))) {
-    store_run<E>(kdst + k0, f.k, true);
-    if constexpr (PAIRS) store_run<E>(vdst + k0, f.v, true);
+    store_run<E>(kdst + k0, ks, true);
+    if constexpr (PAIRS) store_run<E>(vdst + k0, vs, true);
     return;
   }
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const uint32_t k = k0 + e;
     if (k >= front && k < front + cnt) {
-      kdst[k] = f.k[e];
-      if constexpr (PAIRS) vdst[k] = f.v[e];
+      kdst[k] = ks[e];
+      if constexpr (PAIRS) vdst[k] = vs[e];
     }
   }
 }
@@ -227,7 +227,13 @@ __device__ __forceinline__ void sort_tile_item(const SegArgs& a, const SegGeo& g
   constexpr int V = 16 / sizeof(K);  // keys per 16-byte vector
   using KV = typename VecOf<K, V>::T;
   using VV = typename ValVec<V>::T;
-  Frag<K, PAIRS, E> f;
+  // with payloads the network sorts (key, position) only: the tile's payloads
+  // wait in a padded plane behind the network's planes (the space the
+  // payload-carrying merge pieces' third plane takes) and each output's
+  // payload is read from there by its position once the tile is sorted (the
+  // network's barriers order the plane's writes before the reads)
+  Frag<K, PAIRS, E, /*VALS=*/false> f;
+  uint32_t* sv = sm + Frag<K, PAIRS, E, false>::W * padded_words(T);
   f.one = g_unit_multiplier;
   const uint32_t tid = threadIdx.x;
   const uint64_t base = (g.lo / T + q) * T;
@@ -254,8 +260,8 @@ __device__ __forceinline__ void sort_tile_item(const SegArgs& a, const SegGeo& g
         const uint32_t* vp = reinterpret_cast<const uint32_t*>(&vv);
 #pragma unroll
         for (int c = 0; c < V; ++c) {
-          f.v[r * V + c] = vp[c];
           f.ix[r * V + c] = pos + c;
+          sv[pos + c + ((pos + c) >> 5)] = vp[c];
         }
       }
     }
@@ -268,8 +274,8 @@ __device__ __forceinline__ void sort_tile_item(const SegArgs& a, const SegGeo& g
       if (real) x = MAP ? map_key(__ldcg(kin + pos), a.mode) : __ldcg(kin + pos);
       f.k[e] = x;
       if constexpr (PAIRS) {
-        f.v[e] = real ? __ldcg(vin + pos) : 0u;
         f.ix[e] = pos;
+        sv[pos + (pos >> 5)] = real ? __ldcg(vin + pos) : 0u;
       }
     }
   }
@@ -293,8 +299,13 @@ __device__ __forceinline__ void sort_tile_item(const SegArgs& a, const SegGeo& g
       for (int e = 0; e < E; ++e) f.k[e] = unmap_key(f.k[e], a.mode);  // last use of f.k
     }
   }
-  store_slots<E>(kout, vout, f, p0, front, cnt, to_out ? a.kout : a.kbuf,
-                 PAIRS ? (to_out ? a.vout : a.vbuf) : nullptr);
+  uint32_t vg[PAIRS ? E : 1];
+  if constexpr (PAIRS) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) vg[e] = sv[f.ix[e] + (f.ix[e] >> 5)];
+  }
+  store_slots<E, PAIRS>(kout, vout, f.k, vg, p0, front, cnt, to_out ? a.kout : a.kbuf,
+                        PAIRS ? (to_out ? a.vout : a.vbuf) : nullptr);
 }
 
 // ---------------------------------------------------------------- merge piece
@@ -477,8 +488,8 @@ __device__ __forceinline__ void merge_piece_item(const SegArgs& a, const SegGeo&
       for (int e = 0; e < E; ++e) f.k[e] = unmap_key(f.k[e], a.mode);  // last use of f.k
     }
   }
-  store_slots<E>(dst, vdst, f, tid * E, front, cnt, dst_out ? a.kout : a.kbuf,
-                 PAIRS ? (dst_out ? a.vout : a.vbuf) : nullptr);
+  store_slots<E, PAIRS>(dst, vdst, f.k, PAIRS ? f.v : nullptr, tid * E, front, cnt,
+                        dst_out ? a.kout : a.kbuf, PAIRS ? (dst_out ? a.vout : a.vbuf) : nullptr);
 }
 
 // ---------------------------------------------------------------- worker
@@ -639,7 +650,10 @@ __global__ void __launch_bounds__(256) seg_tiny_kernel(const SegArgs a, uint32_t
 
 template <typename K, bool PAIRS, int E, int NT, bool MAP>
 cudaError_t launch_seg(const SegArgs& a, cudaStream_t s) {
+  // W planes: the merge pieces' (key, rank, payload) words, or the tile
+  // sorts' (key, position) words and their payload plane
   constexpr int W = Frag<K, PAIRS, E>::W;
+  static_assert(W >= Frag<K, PAIRS, E, false>::W + (PAIRS ? 1 : 0), "tile sort planes");
   const size_t smem = static_cast<size_t>(W) * Geo<E, NT>::kPlane * sizeof(uint32_t);
   int dev = 0, sms = 0, per_sm = 0;
   cudaError_t err;

@@ -94,6 +94,33 @@ def test_benchmark_family_scaled(bcf, k):
     check(bcf, keys, offs, vals, False)
 
 
+@pytest.mark.parametrize("dtype", ["u32", "f32", "u64"])
+@pytest.mark.parametrize("descending", [False, True])
+def test_runs_of_disjoint_ranges(bcf, dtype, descending):
+    """Runs that are consecutive stretches of one sorted array, in order and in
+    reverse order of the stretches: every merge then takes all of one run
+    before the other, so nearly every merge tile copies one window."""
+    from tests.pins import order_rank
+
+    r = workloads.rng(24)
+    lens = r.integers(1, 40000, size=9)
+    lens[3] = 0
+    n = int(lens.sum())
+    keys = workloads.keys("uniform", dtype, n, seed=12)
+    rank = order_rank(keys)
+    keys = keys[np.argsort(~rank if descending else rank, kind="stable")]
+    bounds = np.concatenate([[0], np.cumsum(lens)])
+    for flip in (False, True):
+        idx = range(len(lens) - 1, -1, -1) if flip else range(len(lens))
+        parts = [keys[bounds[i]:bounds[i + 1]] for i in idx]
+        ks = np.concatenate(parts)
+        offs = np.concatenate([[0], np.cumsum([p.size for p in parts])]).astype(np.uint64)
+        vals = workloads.row_index(n)
+        check(bcf, ks, offs, None, descending)
+        check(bcf, ks, offs, vals, descending)
+        check(bcf, ks, offs, vals, descending, inplace=True)
+
+
 def test_in_place_odd_and_even_pass_counts(bcf):
     r = workloads.rng(22)
     for k in (2, 3, 4, 7, 8):

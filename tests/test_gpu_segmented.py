@@ -103,6 +103,24 @@ def test_ties_and_extreme_keys(bcf):
         check(bcf, keys, offs, vals, desc)
 
 
+@pytest.mark.parametrize("dtype", ["u32", "f32", "u64", "f64"])
+def test_presorted_and_reversed_segments(bcf, dtype):
+    """Keys already in order, in reverse order, and in few values: most merge
+    tiles then draw every output from one of their two runs (the tiles that
+    copy one window instead of merging), in both directions and with the key
+    maps of the float types."""
+    r = workloads.rng(34)
+    sizes = mixed_sizes(r, 120)
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
+    n = int(offs[-1])
+    vals = workloads.row_index(n)
+    for dist in ("sorted", "reverse", "distinct16"):
+        keys = workloads.keys(dist, dtype, n, seed=10)
+        for desc in (False, True):
+            check(bcf, keys, offs, vals, desc)
+        check(bcf, keys, offs, None, False)
+
+
 def test_one_big_segment_and_empty_edges(bcf):
     n = (1 << 20) + 333
     keys = workloads.keys("uniform", "u32", n, seed=8)
