@@ -522,7 +522,7 @@ bcf_status bcf_arena_destroy(bcf_arena* a);
  *     streams, other host threads) race and give wrong results.  Serialise them.
  *     Nothing in it needs to start at zero; it keeps the last call's contents.
  *   - The first call on a device looks up the array's device address with that
- *     device current; make that first call before any stream capture.
+ *     device current.
  */
 #define BCF_STATIC_MAX_KEYS (1u << 20)
 bcf_status bcf_sort_keys_static(void* keys_out, const void* keys_in, uint64_t n, bcf_dtype kt,

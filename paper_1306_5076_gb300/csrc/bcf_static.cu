@@ -19,8 +19,7 @@
 //  - nothing in the array has to start at zero (every word is written before
 //    it is read), so calls need not clear it; it keeps the last call's data;
 //  - the first call on a device looks up the array's device address
-//    (cudaGetSymbolAddress) with that device current; make that first call
-//    before any stream capture.
+//    (cudaGetSymbolAddress) with that device current.
 #include <cuda_runtime.h>
 
 #include <mutex>
