@@ -30,8 +30,10 @@ __device__ uint32_t g_error_word;  // set by bounded waits that ran out
 // Run-time settings read by the launch wrappers (bcf_internal.h).
 static std::atomic<uint64_t> g_wait_limit_ns{kDefaultWaitLimitNs};
 static std::atomic<uint32_t> g_smem_floor{0};
+static std::atomic<bool> g_profiling{false};
 uint64_t wait_limit_ns() { return g_wait_limit_ns.load(std::memory_order_relaxed); }
 uint32_t smem_floor_bytes() { return g_smem_floor.load(std::memory_order_relaxed); }
+bool chained_launches() { return !g_profiling.load(std::memory_order_relaxed); }
 
 namespace {
 
@@ -1366,6 +1368,7 @@ bcf_status bcf_profile_enable(int on) {
   Profiler& P = prof();
   std::lock_guard<std::mutex> lk(P.mu);
   P.on = on != 0;
+  g_profiling.store(P.on, std::memory_order_relaxed);
   return BCF_OK;
 }
 

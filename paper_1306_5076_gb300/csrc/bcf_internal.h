@@ -15,9 +15,34 @@ namespace bcf {
 // (bcf_profile_set_smem_floor); 0 leaves every launch as built.
 uint64_t wait_limit_ns();
 uint32_t smem_floor_bytes();
+// chained_launches(): false while the launch profiler is on, whose events
+// between launches must see each kernel start after its predecessor ended.
+bool chained_launches();
 constexpr uint64_t kDefaultWaitLimitNs = 2000000000ull;  // 2 s
 constexpr uint32_t kMaxWaitLimitUs = 60000000u;          // 60 s
 constexpr uint32_t kMaxSmemFloor = 227u * 1024u;         // the opt-in maximum per CTA
+
+// Launch of a kernel that begins with pdl_wait() (bcf_device.cuh) as a
+// programmatic dependent of the kernel ahead of it in the stream: it is
+// scheduled once that kernel's last CTA has run, and starts work once that
+// kernel has completed.  Only kernels whose every global access follows
+// pdl_wait() may be launched this way.  While the launch profiler is on, a
+// plain launch.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_chained(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                           cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = chained_launches() ? 1 : 0;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
 
 // One adjacent pair of sorted runs to merge: A = [off, off + na), B = [off + na,
 // off + na + nb) of the source array; the merged run occupies the same index

@@ -105,6 +105,7 @@ __device__ __forceinline__ uint64_t first_item(const PairParam<IRREG>& pl) {
 template <typename K, bool IRREG, bool MAP>
 __global__ void __launch_bounds__(256) partition_kernel(const MergeArgs a, int Tm,
                                                         const __grid_constant__ PairParam<IRREG> pl) {
+  pdl_wait();
   const uint64_t local = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (local >= a.nitems) return;
   const uint64_t item = first_item<IRREG>(pl) + local;
@@ -158,6 +159,7 @@ __global__ void __launch_bounds__(NT) merge_kernel(const MergeArgs a,
                                                    const __grid_constant__ PairParam<IRREG> pl) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ int s_ok;
+  pdl_wait();
   uint64_t* bar = reinterpret_cast<uint64_t*>(smraw);
   const uint64_t item = first_item<IRREG>(pl) + blockIdx.x;
   const Piece p = piece_of<IRREG>(a, pl, item, E * NT);
@@ -227,8 +229,7 @@ static cudaError_t launch_m3(const MergeArgs& a, const PairParam<IRREG>& pl, cud
   if (err != cudaSuccess) return err;
   MergeArgs b = a;
   b.wait_ns = wait_limit_ns();
-  kern<<<static_cast<unsigned>(a.nitems), NT, smem, s>>>(b, pl);
-  return cudaGetLastError();
+  return launch_chained(kern, dim3(static_cast<unsigned>(a.nitems)), dim3(NT), smem, s, b, pl);
 }
 
 template <typename K, bool PAIRS, int E, int NT, bool IRREG, bool MAP>
@@ -275,9 +276,10 @@ cudaError_t launch_merge(int key_bytes, bool pairs, int cfg, const MergeArgs& a,
 }
 
 template <typename K, bool IRREG, bool MAP>
-static void launch_p(const MergeArgs& a, int Tm, const PairParam<IRREG>& pl, cudaStream_t s) {
+static cudaError_t launch_p(const MergeArgs& a, int Tm, const PairParam<IRREG>& pl,
+                            cudaStream_t s) {
   const unsigned grid = static_cast<unsigned>((a.nitems + 255) / 256);
-  partition_kernel<K, IRREG, MAP><<<grid, 256, 0, s>>>(a, Tm, pl);
+  return launch_chained(partition_kernel<K, IRREG, MAP>, dim3(grid), dim3(256), 0, s, a, Tm, pl);
 }
 
 cudaError_t launch_partition(int key_bytes, int cfg, const MergeArgs& a, const PairList* pl,
@@ -287,17 +289,15 @@ cudaError_t launch_partition(int key_bytes, int cfg, const MergeArgs& a, const P
   const int Tm = kMergeCfgs[cfg].tile();
   const bool map = a.mode_in != 0;
   if (key_bytes == 4) {
-    if (pl) map ? launch_p<uint32_t, true, true>(a, Tm, *pl, s)
-                : launch_p<uint32_t, true, false>(a, Tm, *pl, s);
-    else map ? launch_p<uint32_t, false, true>(a, Tm, NoPairs{0}, s)
-             : launch_p<uint32_t, false, false>(a, Tm, NoPairs{0}, s);
-  } else {
-    if (pl) map ? launch_p<uint64_t, true, true>(a, Tm, *pl, s)
-                : launch_p<uint64_t, true, false>(a, Tm, *pl, s);
-    else map ? launch_p<uint64_t, false, true>(a, Tm, NoPairs{0}, s)
-             : launch_p<uint64_t, false, false>(a, Tm, NoPairs{0}, s);
+    if (pl) return map ? launch_p<uint32_t, true, true>(a, Tm, *pl, s)
+                       : launch_p<uint32_t, true, false>(a, Tm, *pl, s);
+    return map ? launch_p<uint32_t, false, true>(a, Tm, NoPairs{0}, s)
+               : launch_p<uint32_t, false, false>(a, Tm, NoPairs{0}, s);
   }
-  return cudaGetLastError();
+  if (pl) return map ? launch_p<uint64_t, true, true>(a, Tm, *pl, s)
+                     : launch_p<uint64_t, true, false>(a, Tm, *pl, s);
+  return map ? launch_p<uint64_t, false, true>(a, Tm, NoPairs{0}, s)
+             : launch_p<uint64_t, false, false>(a, Tm, NoPairs{0}, s);
 }
 
 
