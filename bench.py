@@ -1080,9 +1080,13 @@ def run_gpu(args, world, rank, local, pg):
     # host loop enqueues every step, and a collection pause would idle the GPU)
     gc.collect()
     gc.disable()
+    # Two regions of the same steps.  The first, the headline, runs the calls
+    # as a user makes them (the library chains its launches); the second has
+    # the launch profiler on, whose CUDA events around every kernel give the
+    # per-kernel times of the roofline, and whose launches are plain (an event
+    # between two kernels ends the chaining).
     clocks = ClockSampler(local)
     bcf.bcf_profile_collect()  # drop anything pending
-    bcf.bcf_profile_enable(True)
     clocks.start()
     barrier()
     torch.cuda.synchronize()
@@ -1096,11 +1100,23 @@ def run_gpu(args, world, rank, local, pg):
     torch.cuda.synchronize()
     m1 = clocks.mark()
     barrier()
+    bcf.bcf_profile_enable(True)
+    barrier()
+    torch.cuda.synchronize()
+    p0 = torch.cuda.Event(enable_timing=True)
+    p1 = torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for _ in range(args.steps):
+        step()
+    p1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
     clk = clocks.stop(m0, m1)
     bcf.bcf_profile_enable(False)
     prof, launch_list = bcf.bcf_profile_collect_launches(64 * (args.steps + 1) + 64)
     gc.enable()
     ms = max_over_ranks(torch, pg, e0.elapsed_time(e1) / args.steps, dev)
+    ms_profiled = max_over_ranks(torch, pg, p0.elapsed_time(p1) / args.steps, dev)
     passes = per_pass_ms(launch_list)
 
     # correctness of the timed output (bit-exact order check on the device:
@@ -1243,6 +1259,10 @@ def run_gpu(args, world, rank, local, pg):
                    "block_tile": plan["block_tile"], "merge_tile": plan["merge_tile"],
                    "merge_passes": plan["merge_passes"],
                    "l2": "inputs (1 GiB) larger than L2 (129 MB); no flush",
+                   "timing": "value from a region of plain calls; roofline, per_kernel_ms, "
+                             "per_pass_ms and gpu_launches from a second region of the same "
+                             "steps with the launch profiler's CUDA events around every kernel",
+                   "ms_per_step_profiled": ms_profiled,
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
