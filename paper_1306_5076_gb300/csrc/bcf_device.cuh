@@ -404,12 +404,12 @@ template <> struct CeForms<uint32_t, true> {
 };
 template <> struct CeForms<uint64_t, false> {
   static constexpr int kBlockBlk = kFmaWord(0) | kFmaWord(1), kBlockOth = 0;
-  static constexpr int kMergeBlk = 0, kMergeOth = 0;
-  static constexpr int kPieceBlk = kMergeBlk, kPieceOth = kMergeOth;
+  static constexpr int kMergeBlk = kFmaWord(0) | kFmaWord(1), kMergeOth = kFmaWord(0) | kFmaWord(1);
+  static constexpr int kPieceBlk = 0, kPieceOth = 0;
 };
 template <> struct CeForms<uint64_t, true> {
   static constexpr int kBlockBlk = 0, kBlockOth = 0;
-  static constexpr int kMergeBlk = 0, kMergeOth = 0;
+  static constexpr int kMergeBlk = kFmaWord(1) | kFmaWord(2), kMergeOth = 0;
   static constexpr int kPieceBlk = 0, kPieceOth = 0;
 };
 
